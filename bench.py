@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the two-center multipole (TCM) hot path on GB300.
+
+Workload (one "step"): the protein-like PES scan -- systems A and B of 20,000 atoms each
+(seeded random-walk chains, bond 1.5 A, confined to r = 30 A, N(0, 0.3) net-zero charges),
+256 seeded orientations of B (uniform rotation about its centre, |R0| uniform in
+[70, 150] A), Lmax = 20, mixed precision.  One step runs the whole path through the C ABI
+(tcm_energy_batch): centre and radius of A and B on the device, the moments of A and of the
+256 rotated copies of B (5.14e6 atom-moments), the cross-tile reductions and the 256
+two-center contractions.  Inputs are resident in HBM; L2 is flushed (256 MB write, untimed)
+before every timed step.
+
+Prints one JSON line (see the design doc for every key).  ``--impl reference`` times the CPU
+oracle instead.  Under torchrun each rank runs its own copy of the workload on its GPU
+(weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-moments/s and TCM energies/s vs plain FP64 GPU path at stated error; p50/p99"
+UNIT = "atom-moments/s"
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--e2e-steps", type=int, default=100)
+    p.add_argument("--fp64-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-clocks", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- workload
+
+def workload():
+    from paper_0704_1672_gb300 import synth
+    s = synth.protein_pes_scan()
+    k = len(s.R0)
+    atoms = len(s.A) + k * len(s.B)
+    cfg = {"workload": "protein-like PES scan: 2 x 20000 random-walk atoms (r=30 A, N(0,0.3) net-zero), "
+                       "256 orientations of B, |R0| in [70,150] A, Lmax=20",
+           "n_atoms_A": len(s.A), "n_atoms_B": len(s.B), "orientations": k, "lmax": s.L,
+           "atom_moments_per_step": atoms, "energies_per_step": k, "coords": "float32 (x,y,z,q)",
+           "l2": "flushed before every timed step (256 MB write, untimed); inputs 640 KB"}
+    return s, atoms, cfg
+
+
+def moment_instr_per_atom(L):
+    """Algorithmic FP32-pipe instructions per atom-moment at order L (3 per real component + 12)."""
+    return 3 * (L + 1) ** 2 + 12
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+                pw.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle leg
+
+def oracle_rate(s, target_seconds, threads):
+    """Oracle (as it stands) on a bounded sample of the workload: Eq. (multipole) of rotated B
+    over an atom sample split across host threads, plus one Eq. (Formula) contraction."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    cB, _ = oracle.center_radius(s.B)
+    cA, _ = oracle.center_radius(s.A)
+    L = s.L
+    # calibrate on a small slice
+    t0 = time.perf_counter()
+    oracle.moments(s.B[:200], cB, L, rot=s.rotB[0])
+    per_atom = (time.perf_counter() - t0) / 200
+    n = int(max(threads * 50, min(len(s.B), target_seconds * threads / per_atom)))
+    n = min(n, len(s.B))
+    bounds = np.linspace(0, n, threads + 1).astype(int)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        t0 = time.perf_counter()
+        futs = [ex.submit(oracle.moments, s.B[bounds[i]:bounds[i + 1]], cB, L, s.rotB[1]) for i in range(threads)]
+        for f in futs:
+            f.result()
+        t_mom = time.perf_counter() - t0
+    QA = oracle.moments(s.A[:50], cA, L)
+    QB = oracle.moments(s.B[:50], cB, L)
+    t0 = time.perf_counter()
+    oracle.tcm_energy(L, QA, QB, s.R0[0])
+    t_con = time.perf_counter() - t0
+    return n, t_mom, t_con
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    s, atoms_per_step, cfg = workload()
+    threads = os.cpu_count() or 1
+    budget = min(0.5, 120.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_rate(s, budget, threads)
+    tot_atoms, tot_t, t_con = 0, 0.0, 0.0
+    times = []
+    for _ in range(args.steps):
+        n, tm, tc = oracle_rate(s, budget, threads)
+        tot_atoms += n
+        tot_t += tm
+        t_con += tc
+        times.append(tm)
+    value = tot_atoms / tot_t
+    sample = (f"per step: oracle Eq. (multipole) at L={s.L} over {n} atoms of rotated B split across {threads} host "
+              f"threads (timed), plus one Eq. (Formula) contraction timed separately "
+              f"({t_con / args.steps:.3f} s per energy, single thread)")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                             "energies_per_s_single_thread": 1.0 / max(t_con / args.steps, 1e-12)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our leg
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_0704_1672_gb300 import build, tcm
+    build.build()
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    s, atoms_per_step, cfg = workload()
+    k = len(s.R0)
+    L = s.L
+    prec = tcm.TCM_MIXED if args.precision == "mixed" else tcm.TCM_FP64
+    A = torch.tensor(s.A, dtype=torch.float32, device="cuda")
+    B = torch.tensor(s.B, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = tcm.Context(lmax_cap=L, stream=stream)
+    pb = tcm.pack_batch([(A, None, None), (B, None, None)], np.zeros(k, int), np.ones(k, int), np.full(k, L),
+                        s.R0, rotB=s.rotB)
+    E = torch.empty(k, dtype=torch.float64, device="cuda")
+    st = torch.empty(k, dtype=torch.int32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step():
+        ctx.tcm_energy_batch_packed(pb, prec, E, st)
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    assert bool(torch.all(st == 0)), "non-converged items in the benchmark workload"
+    ctx.tcm_ctx_read_profile()
+    ctx.tcm_ctx_set_profiling(True)
+
+    clocks = ClockSampler(dev)
+    if not args.no_clocks:
+        clocks.start()
+        time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop() if not args.no_clocks else {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    phase_ms, launches = ctx.tcm_ctx_read_profile()
+    ctx.tcm_ctx_set_profiling(False)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * atoms_per_step / (total_ms * 1e-3)
+    energies_per_s = world * k / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel (moment accumulation, FP32 pipe)
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tinstr = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    mom_ms = phase_ms["moments"] / args.steps
+    mom_launch_ms = phase_ms["moments"] / max(1, launches["moments"])
+    instr = atoms_per_step * moment_instr_per_atom(L) / max(1, launches["moments"] / args.steps)
+    achieved = instr / (mom_launch_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": f"k_moments<float,{L}>", "achieved": achieved, "peak": peak_tinstr,
+                "unit": "T FP32-pipe lane-instr/s", "frac": achieved / peak_tinstr, "traffic": None,
+                "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (max SM clock of measured)",
+                "algorithmic_instr_per_atom": moment_instr_per_atom(L)}
+    phases = {p: phase_ms[p] / args.steps for p in phase_ms}
+
+    # end to end through the C ABI with host buffers: H2D of the coordinates, D2H of the energies
+    A_h = torch.tensor(s.A, dtype=torch.float32).pin_memory()
+    B_h = torch.tensor(s.B, dtype=torch.float32).pin_memory()
+    E_h = torch.empty(k, dtype=torch.float64).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(args.e2e_steps + 3):
+        if i == 3:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            t_wall = time.perf_counter()
+        A.copy_(A_h, non_blocking=True)
+        B.copy_(B_h, non_blocking=True)
+        step()
+        E_h.copy_(E, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    e2e = {"value": world * atoms_per_step / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": int(A_h.numel() * 4 + B_h.numel() * 4),
+           "d2h_bytes_per_step": int(E_h.numel() * 8), "ms_per_step": e2e_ms,
+           "wall_ms_per_step": 1e3 * t_wall / args.e2e_steps}
+
+    # reference points: the plain single-request FP64 GPU path, and the CPU oracle
+    fp64_plain = None
+    if args.fp64_steps > 0 and rank == 0:
+        fp64_plain = plain_fp64(ctx, tcm, torch, A, B, s, args.fp64_steps)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        threads = os.cpu_count() or 1
+        n, tm, tc = oracle_rate(s, 2.0, threads)
+        cpu = {"value": n / tm, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"oracle Eq. (multipole) at L={L} over {n} atoms of rotated B split across {threads} host "
+                         f"threads; one Eq. (Formula) contraction took {tc:.3f} s single-threaded",
+               "energies_per_s_single_thread": 1.0 / tc}
+
+    if rank == 0:
+        p50 = float(np.percentile(step_ms, 50))
+        p99 = float(np.percentile(step_ms, 99))
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64" if prec == tcm.TCM_MIXED else "f64", "data": "synthetic",
+                "config": cfg, "energies_per_s": energies_per_s,
+                "step_latency_ms": {"p50": p50, "p99": p99},
+                "phase_ms_per_step": phases, "gpu_launches": int(sum(launches.values())),
+                "gpu_launches_per_step": {p: launches[p] / args.steps for p in launches},
+                "roofline": roofline, "clocks": ck, "e2e": e2e, "fp64_plain_gpu": fp64_plain,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def plain_fp64(ctx, tcm, torch, A, B, s, steps):
+    """The plain FP64 GPU path: one request at a time through tcm_moments + tcm_energy, no batching."""
+    k = len(s.R0)
+    L = s.L
+    qA = torch.empty((L + 1) ** 2, dtype=torch.float64, device="cuda")
+    qB = torch.empty((L + 1) ** 2, dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ma = ctx.tcm_moments(A, L, precision=tcm.TCM_FP64, out=qA)
+        for i in range(k):
+            mb = ctx.tcm_moments(B, L, precision=tcm.TCM_FP64, rot=s.rotB[i], out=qB)
+            ctx.tcm_energy(ma, mb, s.R0[i], L)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    atoms = len(s.A) + k * len(s.B)
+    return {"value": atoms / dt, "unit": UNIT, "energies_per_s": k / dt, "ms_per_step": 1e3 * dt, "steps": steps,
+            "how": "per orientation: tcm_moments(B, FP64, rotated) + tcm_energy (synchronous); A once per step"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        dist = tdist
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, dist)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * tcm.h -- C ABI of the GB300 two-center multipole (TCM) library (libtcm.so).
+ *
+ * The method (Solov'yov, Yakubovich, Solov'yov, Greiner, "Two center multipole
+ * expansion method: application to macromolecular systems") computes the Coulomb
+ * interaction energy of two separated charge systems A and B,
+ *
+ *   Eq. (Coulomb):    U = sum_i sum_j q_i q_j / |R0 + r_j^B - r_i^A|,
+ *
+ * where r^A, r^B are positions about each system's centre and R0 points from the
+ * centre of A to the centre of B, in two steps:
+ *
+ *   Eq. (multipole):  Q_lm = sum_i q_i r_i^l sqrt(4 pi / (2l+1)) Y_lm(theta_i, phi_i)
+ *                     for each system, 0 <= l <= Lmax, and
+ *   Eq. (Formula):    U_mult = sum_{l1,l2=0}^{Lmax} sum_{m1,m2} (-1)^(l1+M) R0^-(L+1)
+ *                       sqrt(4 pi (2L)! / ((2 l1)! (2 l2)!)) (l1 l2 L; m1 m2 -M)
+ *                       Q^A_{l1 m1} Q^B_{l2 m2} Y*_{LM}(R0hat),  L = l1 + l2, M = m1 + m2,
+ *
+ * valid when |R0| exceeds the sum of the two system radii (Eq. (mainCond)).
+ *
+ * Conventions
+ *   - Y_lm: orthonormal spherical harmonics with the Condon-Shortley phase.
+ *   - Moments use Y_lm (not Y*_lm) and the separation harmonic is conjugated, as the
+ *     paper prints them; l1 and l2 each run over 0..Lmax (square truncation).
+ *   - Units follow the input: charges in e and distances in Angstrom give energies in
+ *     e^2/Angstrom (multiply by 332.06 for kcal/mol).
+ *   - Packed moments: (Lmax+1)^2 doubles; degree l starts at index l*l and holds
+ *     Re Q_l0, Re Q_l1, Im Q_l1, ..., Re Q_ll, Im Q_ll.  For real charges
+ *     Q_l,-m = (-1)^m conj(Q_lm), so m < 0 is not stored.
+ *   - A rotation acts about the system's own centre: r' = rot * (x - c), rot
+ *     row-major 3x3.  Moments are reported in the frame after rotation.
+ *
+ * Memory and threads
+ *   - Coordinate records, packed moments and batch energy outputs are DEVICE
+ *     pointers owned by the caller; the context owns its scratch (grown on first
+ *     use, never freed until tcm_ctx_destroy) and its tables.
+ *   - All work is queued on the context's stream.  Calls that return a host value
+ *     (tcm_energy, tcm_direct, tcm_prepare, tcm_moments when it must compute a
+ *     centre or radius) synchronise that stream; the others are asynchronous.
+ *   - A context is used by one host thread at a time.
+ *
+ * Errors
+ *   Every call returns a tcm_status; nothing throws across the ABI.  On failure
+ *   tcm_last_error() returns a message for the calling thread.
+ */
+#ifndef TCM_H_
+#define TCM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Largest Lmax with compiled kernels.  Moments use (Lmax+1)^2 components; the
+ * contraction evaluates irregular harmonics up to order 2 Lmax. */
+#define TCM_LMAX_MAX 24
+
+typedef enum {
+  TCM_OK = 0,
+  TCM_EINVAL = 1,    /* bad argument: null pointer, Lmax out of range, misaligned buffer, bad dtype */
+  TCM_ENOTCONV = 2,  /* |R0| <= a_A + a_B: the expansion does not converge (Eq. (mainCond)) */
+  TCM_ENOMEM = 3,    /* device or pinned host allocation failed */
+  TCM_ECUDA = 4,     /* a CUDA runtime call or kernel launch failed */
+  TCM_ETIMEOUT = 5   /* reserved: a bounded device-side wait ran out */
+} tcm_status;
+
+typedef enum { TCM_F32 = 0, TCM_F64 = 1 } tcm_dtype;
+
+typedef enum {
+  TCM_FP64 = 0,  /* every step in double precision */
+  TCM_MIXED = 1  /* moment recurrence and per-atom products in float on radius-scaled
+                    coordinates; block partials, cross-block reduction, tables and the
+                    contraction in double */
+} tcm_precision;
+
+typedef struct tcm_ctx* tcm_ctx_t;
+
+/* One charge system. */
+typedef struct {
+  const void* xyzq; /* device: n records (x, y, z, q); float[4] (16-byte aligned) for
+                       TCM_F32, double[4] (16-byte aligned) for TCM_F64 */
+  int64_t n;        /* number of charges, >= 0 */
+  int32_t dtype;    /* tcm_dtype */
+  int32_t has_center; /* nonzero: center[] is the system centre; zero: the centroid of the
+                         positions (unit masses) is used */
+  double center[3];
+  double radius;    /* a = max_i |x_i - c| (any a' >= a is also accepted); < 0: computed */
+} tcm_system;
+
+/* Moments of one system (output of tcm_moments, input of tcm_energy). */
+typedef struct {
+  double* q;        /* device: (lmax+1)^2 packed doubles, caller-owned */
+  int32_t lmax;
+  int32_t pad_;
+  double center[3]; /* centre the moments are taken about */
+  double radius;    /* system radius about that centre */
+} tcm_moments_t;
+
+/* One (pair, orientation) of a batch. */
+typedef struct {
+  int32_t a, b;     /* indices into the batch's systems array */
+  int32_t lmax;     /* 0 <= lmax <= TCM_LMAX_MAX */
+  int32_t has_rot;  /* nonzero: rotB applies to B about its centre */
+  double rotB[9];
+  double R0[3];     /* centre of A -> centre of B */
+} tcm_pair_item;
+
+/* Create a context on the current CUDA device, bound to cuda_stream (a cudaStream_t;
+ * NULL = legacy default stream).  lmax_cap (0..TCM_LMAX_MAX) bounds the Lmax of every
+ * later call.  On success *ctx is set; on failure *ctx is NULL. */
+int tcm_ctx_create(tcm_ctx_t* ctx, int lmax_cap, void* cuda_stream);
+
+/* Release the context and everything it owns.  Synchronises its stream.  NULL is a no-op. */
+void tcm_ctx_destroy(tcm_ctx_t ctx);
+
+/* Rebind the context to another stream (takes effect for later calls). */
+int tcm_ctx_set_stream(tcm_ctx_t ctx, void* cuda_stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* tcm_last_error(void);
+
+/* Phases of the path, for tracing and benchmarks. */
+typedef enum {
+  TCM_PHASE_GEOM = 0,     /* a1: centre and radius */
+  TCM_PHASE_MOMENTS = 1,  /* a2: per-atom moment accumulation and per-tile CTA reduction */
+  TCM_PHASE_FINALIZE = 2, /* a3: cross-tile reduction in double and normalisation */
+  TCM_PHASE_CONTRACT = 3, /* a4 + a5: irregular harmonics at R0 and the two-center contraction */
+  TCM_PHASE_DIRECT = 4,   /* a6: exact pairwise sum */
+  TCM_NPHASES = 5
+} tcm_phase;
+
+/* Enable (1) or disable (0) phase timing: the context then records a CUDA event pair on
+ * its stream around every phase it queues.  Off by default. */
+int tcm_ctx_set_profiling(tcm_ctx_t ctx, int enable);
+
+/* Synchronise the context stream, then write the milliseconds spent in each phase
+ * (ms[TCM_NPHASES], NULL allowed; zero unless profiling was on) and the number of kernels
+ * launched per phase (launches[TCM_NPHASES], NULL allowed) since the previous read, and
+ * reset both. */
+int tcm_ctx_read_profile(tcm_ctx_t ctx, double* ms, int64_t* launches);
+
+/* Step a1 (Section II: the centres may be any point; centroid by default): compute the
+ * centroid (if !has_center) and the radius (if radius < 0) of *s on the device, write
+ * them into *s and set has_center.  Synchronous. */
+int tcm_prepare(tcm_ctx_t ctx, tcm_system* s);
+
+/* Eq. (multipole): moments Q_lm, 0 <= l <= lmax, of system s about its centre, after
+ * the optional rotation rot (row-major 3x3 host array, NULL = identity).
+ * out->q must hold (lmax+1)^2 doubles on the device; out->lmax, out->center and
+ * out->radius are written.  precision is a tcm_precision.  Asynchronous unless the
+ * centre or radius has to be computed (then it synchronises once, as tcm_prepare). */
+int tcm_moments(tcm_ctx_t ctx, const tcm_system* s, const double* rot, int lmax, int precision,
+                tcm_moments_t* out);
+
+/* Eq. (Formula): two-center energy of A and B at separation R0 (host double[3], from
+ * the centre of A to the centre of B), truncated at lmax (<= both moment sets' lmax).
+ * Returns TCM_ENOTCONV when |R0| <= A->radius + B->radius.  Writes the energy to the
+ * host double *E.  Synchronous. */
+int tcm_energy(tcm_ctx_t ctx, const tcm_moments_t* A, const tcm_moments_t* B, const double* R0,
+               int lmax, double* E);
+
+/* Batched Eq. (multipole) + Eq. (Formula): for every item, the moments of system a
+ * and of system b (rotated by rotB about its centre) at the item's lmax and their
+ * two-center energy at R0.  Moment sets shared by several items (same system, lmax
+ * and no rotation) are computed once.  Systems without a centre or radius get them
+ * on the device (step a1) without a host round trip.
+ *   E:      device, n_items doubles (NaN for an item that does not converge)
+ *   status: device, n_items int32 (TCM_OK or TCM_ENOTCONV), or NULL
+ * Returns TCM_ENOTCONV at once if a host-known radius already violates Eq. (mainCond).
+ * Asynchronous; results are ready when the context stream reaches this point.
+ * Each item's result does not depend on the other items in the batch. */
+int tcm_energy_batch(tcm_ctx_t ctx, int n_systems, const tcm_system* systems, int64_t n_items,
+                     const tcm_pair_item* items, int precision, double* E, int32_t* status);
+
+/* Eq. (Coulomb): exact pairwise energy of A and B (B rotated by rotB about its centre,
+ * NULL = identity) with the centre of B at the centre of A plus R0, in double
+ * precision.  Writes the host double *E.  Synchronous. */
+int tcm_direct(tcm_ctx_t ctx, const tcm_system* A, const tcm_system* B, const double* rotB,
+               const double* R0, double* E);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TCM_H_ */

@@ -39,7 +39,7 @@ def _load():
         lib.oracle_tcm_blocks.argtypes = [i32, P, P, P, P, P, P, P]
         lib.oracle_tcm_energy.argtypes = [i32, P, P, P, P, P, P]
         lib.oracle_tcm_energy.restype = d
-        lib.oracle_direct.argtypes = [i64, P, P, i64, P, P, P, P]
+        lib.oracle_direct.argtypes = [i64, P, P, i64, P, P, P, P, P]
         lib.oracle_direct.restype = d
         _lib = lib
     return _lib
@@ -122,15 +122,20 @@ def tcm_energy(L, QA, QB, R0, return_imag=False):
     return (e, float(im[0])) if return_imag else e
 
 
-def direct(A, cA, B, cB, R0, rotB=None):
-    """Eq. (Coulomb): exact pairwise energy with B rotated about its centre by ``rotB``."""
+def direct(A, cA, B, cB, R0, rotB=None, return_abs=False):
+    """Eq. (Coulomb): exact pairwise energy with B rotated about its centre by ``rotB``.
+
+    With ``return_abs`` also returns sum_ij |q_i q_j| / r_ij (the rounding scale of the sum).
+    """
     A = _f64(A, (-1, 4))
     B = _f64(B, (-1, 4))
     ca = _f64(cA, (3,))
     cb = _f64(cB, (3,))
     r = None if rotB is None else _f64(rotB, (9,))
     R = _f64(R0, (3,))
-    return _load().oracle_direct(A.shape[0], _ptr(A), _ptr(ca), B.shape[0], _ptr(B), _ptr(cb), _ptr(r), _ptr(R))
+    ab = np.zeros(1)
+    e = _load().oracle_direct(A.shape[0], _ptr(A), _ptr(ca), B.shape[0], _ptr(B), _ptr(cb), _ptr(r), _ptr(R), _ptr(ab))
+    return (e, float(ab[0])) if return_abs else e
 
 
 def tcm_energy_systems(A, B, L, R0, rotB=None, cA=None, cB=None):

@@ -245,24 +245,30 @@ double oracle_tcm_energy(int L, const double* qa_re, const double* qa_im, const 
 
 // Eq. (Coulomb): U = sum_i sum_j q_i q_j / |R0 + r_j^B - r_i^A|, with r^A about
 // centre cA, r^B about cB and rotated by rotB (NULL = identity).
+// *abs_out (optional) receives sum_ij |q_i q_j| / |R0 + r_j^B - r_i^A|, the scale against
+// which rounding in the signed sum is measured.
 double oracle_direct(int64_t na, const double* a, const double* ca, int64_t nb, const double* b,
-                     const double* cb, const double* rotb, const double* R0) {
+                     const double* cb, const double* rotb, const double* R0, double* abs_out) {
   std::vector<double> rb(3 * (size_t)nb);
   for (int64_t j = 0; j < nb; ++j) rel_pos(b, j, cb, rotb, &rb[3 * j]);
-  CSum s;
+  CSum s, sa;
   for (int64_t i = 0; i < na; ++i) {
     double ra[3];
     rel_pos(a, i, ca, nullptr, ra);
     double qi = a[4 * i + 3];
-    CSum row;
+    CSum row, rowa;
     for (int64_t j = 0; j < nb; ++j) {
       double dx = R0[0] + rb[3 * j + 0] - ra[0];
       double dy = R0[1] + rb[3 * j + 1] - ra[1];
       double dz = R0[2] + rb[3 * j + 2] - ra[2];
-      row.add(b[4 * j + 3] / std::sqrt(dx * dx + dy * dy + dz * dz));
+      double inv = 1.0 / std::sqrt(dx * dx + dy * dy + dz * dz);
+      row.add(b[4 * j + 3] * inv);
+      rowa.add(std::fabs(b[4 * j + 3]) * inv);
     }
     s.add(qi * row.value());
+    sa.add(std::fabs(qi) * rowa.value());
   }
+  if (abs_out) *abs_out = sa.value();
   return s.value();
 }
 

@@ -1,0 +1,9 @@
+// Explicit instantiations of the moment kernels: float, Lmax 20..22.
+// (Split across translation units so that they compile in parallel.)
+#include "moments_kernel.cuh"
+
+namespace tcm {
+template int launch_moments_t<float, 20>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<float, 21>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<float, 22>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+}  // namespace tcm

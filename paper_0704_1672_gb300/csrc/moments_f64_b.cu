@@ -1,0 +1,12 @@
+// Explicit instantiations of the moment kernels: double, Lmax 14..19.
+// (Split across translation units so that they compile in parallel.)
+#include "moments_kernel.cuh"
+
+namespace tcm {
+template int launch_moments_t<double, 14>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 15>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 16>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 17>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 18>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 19>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+}  // namespace tcm

@@ -1,0 +1,311 @@
+// Moment kernels, Eq. (multipole): persistent CTAs pull tiles (job, column chunk,
+// atom range); every thread keeps the chunk's accumulators in registers while it
+// walks its atoms, then the CTA reduces them into one double-precision partial row
+// per tile.  Included by the per-Lmax translation units, which instantiate
+// launch_moments_t<T, L> explicitly.
+//
+// Per atom (after the per-tile transform M = rot / a and the split centre
+// c = c_hi + c_lo):
+//   d   = (x - c_hi) - c_lo                       exact-ish centring in float
+//   p   = M d                                     rotation and radius scaling fused
+//   rinv = rsqrt(|p|^2), u = (p_x + i p_y) rinv, c = p_z rinv, rho = |p|
+//   column recurrences of tcm_internal.h, accumulating q rho^l G_lm.
+// No trigonometric function and no division is evaluated per atom.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tcm_internal.h"
+
+namespace tcm {
+
+template <typename T>
+struct MomTraits;
+template <>
+struct MomTraits<float> {
+  static constexpr int kmax = kKmaxF32;
+  static constexpr int stride = 36;  // row stride (floats) of the transpose buffer: 16-B rows, no LDS.128 conflicts
+};
+template <>
+struct MomTraits<double> {
+  static constexpr int kmax = kKmaxF64;
+  static constexpr int stride = 34;  // doubles
+};
+
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rsqrtT(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrtT(double x) { return rsqrt(x); }
+
+template <typename T, int L>
+struct Plan {
+  static constexpr int kmax = MomTraits<T>::kmax;
+  static constexpr int nch = plan_nch(L, kmax);
+  __host__ __device__ static constexpr int m0(int c) { return plan_m0(L, kmax, nch, c); }
+  __host__ __device__ static constexpr int nacc(int c) { return chunk_off(L, m0(c), m0(c + 1)); }
+  __host__ __device__ static constexpr int max_nacc() {
+    int mx = 0;
+    for (int c = 0; c < nch; ++c) mx = nacc(c) > mx ? nacc(c) : mx;
+    return mx;
+  }
+  __host__ __device__ static constexpr int smem_bytes() {
+    return (kThreads / 32) * max_nacc() * MomTraits<T>::stride * (int)sizeof(T);
+  }
+};
+
+// Register state of one column chunk [M0, M1).
+template <typename T, int L, int M0, int M1>
+struct Regs {
+  static constexpr int NC = M1 - M0;
+  static constexpr int NACC = chunk_off(L, M0, M1);
+  T acc[NACC];
+  T gr[NC], gi[NC];  // G_l,m   (real, imaginary)
+  T pr[NC], pi[NC];  // G_l-1,m
+  T dr, di;          // running diagonal power u^m
+};
+
+// Column m at degree l: advance its recurrence to G_lm and accumulate qr * G_lm.
+template <typename T, int L, int M0, int M1, int l, int m>
+__device__ __forceinline__ void col_step(Regs<T, L, M0, M1>& s, T ux, T uy, T c, T qr) {
+  if constexpr (m <= l) {
+    constexpr int j = m - M0;
+    if constexpr (l == m) {
+      if constexpr (m > M0) {
+        const T nr = s.dr * ux - s.di * uy;
+        const T ni = s.dr * uy + s.di * ux;
+        s.dr = nr;
+        s.di = ni;
+      }
+      s.gr[j] = s.dr;
+      s.gi[j] = s.di;
+    } else if constexpr (l == m + 1) {
+      s.pr[j] = s.gr[j];
+      s.gr[j] = c * s.pr[j];
+      if constexpr (m > 0) {
+        s.pi[j] = s.gi[j];
+        s.gi[j] = c * s.pi[j];
+      }
+    } else {
+      constexpr T k = (T)kcoef(l - 1, m);
+      const T t = k * c;
+      const T nr = fmaT(t, s.gr[j], -s.pr[j]);
+      s.pr[j] = s.gr[j];
+      s.gr[j] = nr;
+      if constexpr (m > 0) {
+        const T ni = fmaT(t, s.gi[j], -s.pi[j]);
+        s.pi[j] = s.gi[j];
+        s.gi[j] = ni;
+      }
+    }
+    constexpr int a = chunk_off(L, M0, m) + (m == 0 ? l : 2 * (l - m));
+    s.acc[a] = fmaT(qr, s.gr[j], s.acc[a]);
+    if constexpr (m > 0) s.acc[a + 1] = fmaT(qr, s.gi[j], s.acc[a + 1]);
+  }
+}
+
+template <typename T, int L, int M0, int M1, int l, int m>
+__device__ __forceinline__ void level_cols(Regs<T, L, M0, M1>& s, T ux, T uy, T c, T qr) {
+  if constexpr (m < M1) {
+    col_step<T, L, M0, M1, l, m>(s, ux, uy, c, qr);
+    level_cols<T, L, M0, M1, l, m + 1>(s, ux, uy, c, qr);
+  }
+}
+
+template <typename T, int L, int M0, int M1, int l>
+__device__ __forceinline__ void levels(Regs<T, L, M0, M1>& s, T ux, T uy, T c, T rho, T qr) {
+  level_cols<T, L, M0, M1, l, M0>(s, ux, uy, c, qr);
+  if constexpr (l < L) levels<T, L, M0, M1, l + 1>(s, ux, uy, c, rho, qr * rho);
+}
+
+// Per-tile transform of the coordinates: centring and rot / a.
+template <typename T>
+struct Xform {
+  T chi[3], clo[3];  // centre split into high and low parts (float path); clo = 0 in double
+  T M[9];
+};
+
+template <typename T>
+__device__ __forceinline__ Xform<T> make_xform(const MomJob& job, const SysGeom& g) {
+  Xform<T> x;
+  const double a = g.a > 0.0 ? g.a : 1.0;
+  const double ia = 1.0 / a;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    x.chi[k] = (T)g.c[k];
+    x.clo[k] = (T)(g.c[k] - (double)x.chi[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) x.M[k] = (T)(job.rot[k] * ia);
+  return x;
+}
+
+// Load atom i and produce (u_x, u_y, c, rho, q) in the scaled, rotated frame.
+template <typename T>
+__device__ __forceinline__ void load_setup(const void* xyzq, int dtype, long long i, const Xform<T>& xf,
+                                           const double* cd, T& ux, T& uy, T& cz, T& rho, T& q) {
+  T d0, d1, d2;
+  if (dtype == TCM_F32) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(xyzq) + i);
+    d0 = ((T)v.x - xf.chi[0]) - xf.clo[0];
+    d1 = ((T)v.y - xf.chi[1]) - xf.clo[1];
+    d2 = ((T)v.z - xf.chi[2]) - xf.clo[2];
+    q = (T)v.w;
+  } else {
+    const double2 v0 = __ldg(reinterpret_cast<const double2*>(xyzq) + 2 * i);
+    const double2 v1 = __ldg(reinterpret_cast<const double2*>(xyzq) + 2 * i + 1);
+    d0 = (T)(v0.x - cd[0]);
+    d1 = (T)(v0.y - cd[1]);
+    d2 = (T)(v1.x - cd[2]);
+    q = (T)v1.y;
+  }
+  const T px = fmaT(xf.M[0], d0, fmaT(xf.M[1], d1, xf.M[2] * d2));
+  const T py = fmaT(xf.M[3], d0, fmaT(xf.M[4], d1, xf.M[5] * d2));
+  const T pz = fmaT(xf.M[6], d0, fmaT(xf.M[7], d1, xf.M[8] * d2));
+  const T r2 = fmaT(px, px, fmaT(py, py, pz * pz));
+  const T rinv = r2 > (T)0 ? rsqrtT(r2) : (T)0;
+  ux = px * rinv;
+  uy = py * rinv;
+  cz = pz * rinv;
+  rho = r2 * rinv;
+}
+
+__device__ __forceinline__ float row_sum32(const float* p) {
+  const float4* v = reinterpret_cast<const float4*>(p);
+  float s[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float4 w = v[k];
+    s[k] = (w.x + w.y) + (w.z + w.w);
+  }
+  return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
+
+__device__ __forceinline__ double row_sum32(const double* p) {
+  const double2* v = reinterpret_cast<const double2*>(p);
+  double s[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const double2 w0 = v[2 * k], w1 = v[2 * k + 1];
+    s[k] = (w0.x + w0.y) + (w1.x + w1.y);
+  }
+  return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
+
+// CTA reduction of the per-thread accumulators into one double row `out[0..NACC)`.
+// Each warp transposes its 32 x NACC block through shared memory and every lane
+// tree-sums whole rows (fixed order); the four warp sums are then added in double.
+template <typename T, int NACC>
+__device__ __forceinline__ void cta_reduce_store(const T (&acc)[NACC], unsigned char* smem_raw, double* out) {
+  constexpr int S = MomTraits<T>::stride;
+  constexpr int NW = kThreads / 32;
+  constexpr int NR = (NACC + 31) / 32;
+  T* buf = reinterpret_cast<T*>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* wb = buf + warp * (NACC * S);
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) wb[k * S + lane] = acc[k];
+  __syncwarp();
+  T rs[NR];
+#pragma unroll
+  for (int rr = 0; rr < NR; ++rr) {
+    const int r = lane + 32 * rr;
+    rs[rr] = (r < NACC) ? row_sum32(wb + r * S) : (T)0;
+  }
+  __syncthreads();
+  T* ws = buf;  // [NW][NACC], reuses the transpose buffer
+#pragma unroll
+  for (int rr = 0; rr < NR; ++rr) {
+    const int r = lane + 32 * rr;
+    if (r < NACC) ws[warp * NACC + r] = rs[rr];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < NACC; k += kThreads) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s += (double)ws[w * NACC + k];
+    out[k] = s;
+  }
+  __syncthreads();
+}
+
+template <typename T, int L, int M0, int M1>
+__device__ __forceinline__ void run_chunk(const MomTile& tile, const MomJob* __restrict__ jobs,
+                                          const SysGeom* __restrict__ geoms, double* __restrict__ partials,
+                                          unsigned char* smem) {
+  using R = Regs<T, L, M0, M1>;
+  const MomJob& job = jobs[tile.job];
+  const SysGeom g = geoms[job.geom];
+  const Xform<T> xf = make_xform<T>(job, g);
+  const long long n = job.n;
+  const long long i0 = (long long)tile.t * job.atoms_per_tile;
+  const long long i1 = min(n, i0 + (long long)job.atoms_per_tile);
+  const void* xyzq = job.xyzq;
+  const int dtype = job.dtype;
+  R s;
+#pragma unroll
+  for (int k = 0; k < R::NACC; ++k) s.acc[k] = (T)0;
+  for (long long i = i0 + threadIdx.x; i < i1; i += kThreads) {
+    T ux, uy, cz, rho, q;
+    load_setup<T>(xyzq, dtype, i, xf, g.c, ux, uy, cz, rho, q);
+    if constexpr (M0 == 0) {
+      s.dr = (T)1;
+      s.di = (T)0;
+    } else {
+      s.dr = ux;
+      s.di = uy;
+#pragma unroll
+      for (int k = 1; k < M0; ++k) {
+        const T nr = s.dr * ux - s.di * uy;
+        const T ni = s.dr * uy + s.di * ux;
+        s.dr = nr;
+        s.di = ni;
+      }
+    }
+    levels<T, L, M0, M1, 0>(s, ux, uy, cz, rho, q);
+  }
+  cta_reduce_store<T, R::NACC>(s.acc, smem, partials + (long long)tile.id * Plan<T, L>::kmax);
+}
+
+template <typename T, int L, int C>
+__device__ __forceinline__ void run_tile(const MomTile& tile, const MomJob* __restrict__ jobs,
+                                         const SysGeom* __restrict__ geoms, double* __restrict__ partials,
+                                         unsigned char* smem) {
+  using P = Plan<T, L>;
+  if constexpr (C < P::nch) {
+    if (tile.chunk == C)
+      run_chunk<T, L, P::m0(C), P::m0(C + 1)>(tile, jobs, geoms, partials, smem);
+    else
+      run_tile<T, L, C + 1>(tile, jobs, geoms, partials, smem);
+  }
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_moments(const MomJob* __restrict__ jobs, const MomTile* __restrict__ tiles, int n_tiles,
+              int* __restrict__ counter, const SysGeom* __restrict__ geoms, double* __restrict__ partials) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_next;
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int ti = s_next;
+    __syncthreads();
+    if (ti >= n_tiles) return;
+    const MomTile tile = tiles[ti];
+    run_tile<T, L, 0>(tile, jobs, geoms, partials, smem);
+  }
+}
+
+template <typename T, int L>
+int launch_moments_t(const MomJob* jobs, const MomTile* tiles, int n_tiles, int* counter,
+                     const SysGeom* geoms, double* partials, int grid, cudaStream_t s) {
+  constexpr int smem = Plan<T, L>::smem_bytes();
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(k_moments<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      return -1;
+  }
+  k_moments<T, L><<<grid, kThreads, smem, s>>>(jobs, tiles, n_tiles, counter, geoms, partials);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace tcm

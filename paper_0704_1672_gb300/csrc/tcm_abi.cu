@@ -1,0 +1,766 @@
+// C ABI of libtcm.so (include/tcm.h): argument checks, the context (tables, scratch,
+// descriptor staging) and the host-side planning of moment jobs and tiles.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "tcm_internal.h"
+
+using namespace tcm;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int set_err(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define TRY_CUDA(expr)                                                                                   \
+  do {                                                                                                   \
+    cudaError_t e_ = (expr);                                                                             \
+    if (e_ != cudaSuccess) return set_err(TCM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));           \
+  } while (0)
+#define TRY(expr)                   \
+  do {                              \
+    int r_ = (expr);                \
+    if (r_ != TCM_OK) return r_;    \
+  } while (0)
+#define TRY_LAUNCH(expr)                                                                                 \
+  do {                                                                                                   \
+    if ((expr) != 0) {                                                                                   \
+      cudaError_t e_ = cudaGetLastError();                                                               \
+      return set_err(TCM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));                                \
+    }                                                                                                    \
+  } while (0)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+struct Stage {  // pinned host staging slot for one call's descriptors
+  void* host = nullptr;
+  size_t cap = 0;
+  cudaEvent_t ev = nullptr;
+  bool pending = false;
+};
+
+constexpr int kStages = 4;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+// Host-side builder of one call's descriptor block (uploaded with a single copy).
+struct Packer {
+  std::vector<char> buf;
+  template <typename T>
+  size_t add(const std::vector<T>& v) {
+    const size_t off = align_up(buf.size());
+    buf.resize(off + std::max<size_t>(v.size() * sizeof(T), 1));
+    if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+};
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+struct tcm_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int lmax_cap = 0;
+  cudaStream_t stream = nullptr;
+  // tables
+  double* d_ftab = nullptr;  // F_lm, [kLmaxMax+1][kLmaxMax+1]
+  double* d_isf = nullptr;   // 1/sqrt((l+m)!(l-m)!)
+  int2* d_cmap[2] = {nullptr, nullptr};
+  int* d_cmap_off = nullptr;
+  // scratch
+  DevBuf desc, partials, gpart, counters, moms, escr, dpart;
+  Stage stage[kStages];
+  int stage_next = 0;
+  void* pinned_small = nullptr;  // 256 B for small device->host reads
+  int atoms_per_thread[2] = {16, 32};  // [TCM_FP64, TCM_MIXED]
+  // phase profiling
+  bool prof = false;
+  struct Mark {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> ev_pool;
+  int64_t launches[TCM_NPHASES] = {};
+};
+
+namespace {
+
+cudaEvent_t pool_event(tcm_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Records an event pair around one phase when profiling is on, and counts launches.
+struct PhaseScope {
+  tcm_ctx* c;
+  int phase;
+  cudaEvent_t a = nullptr;
+  PhaseScope(tcm_ctx* c_, int ph, int nlaunch) : c(c_), phase(ph) {
+    c->launches[ph] += nlaunch;
+    if (c->prof && (a = pool_event(c)) != nullptr) cudaEventRecord(a, c->stream);
+  }
+  ~PhaseScope() {
+    if (!a) return;
+    cudaEvent_t b = pool_event(c);
+    if (!b) {
+      c->ev_pool.push_back(a);
+      return;
+    }
+    cudaEventRecord(b, c->stream);
+    c->marks.push_back({phase, a, b});
+  }
+};
+
+int dev_ensure(tcm_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes <= b.cap) return TCM_OK;
+  size_t nc = std::max(bytes, b.cap + b.cap / 2);
+  nc = align_up(std::max<size_t>(nc, kAlign));
+  if (b.p) {
+    TRY_CUDA(cudaStreamSynchronize(c->stream));
+    TRY_CUDA(cudaFree(b.p));
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  if (cudaMalloc(&b.p, nc) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(TCM_ENOMEM, "cudaMalloc of %zu bytes failed", nc);
+  }
+  b.cap = nc;
+  return TCM_OK;
+}
+
+// Copy the packed descriptors to the device through a pinned slot; returns the
+// device base address in *dbase.
+int upload(tcm_ctx* c, const Packer& pk, char** dbase) {
+  const size_t bytes = std::max<size_t>(pk.buf.size(), 1);
+  TRY(dev_ensure(c, c->desc, bytes));
+  Stage& st = c->stage[c->stage_next];
+  c->stage_next = (c->stage_next + 1) % kStages;
+  if (st.pending) {
+    TRY_CUDA(cudaEventSynchronize(st.ev));
+    st.pending = false;
+  }
+  if (st.cap < bytes) {
+    if (st.host) TRY_CUDA(cudaFreeHost(st.host));
+    st.host = nullptr;
+    st.cap = 0;
+    const size_t nc = align_up(std::max<size_t>(bytes * 2, 4096));
+    if (cudaHostAlloc(&st.host, nc, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(TCM_ENOMEM, "cudaHostAlloc of %zu bytes failed", nc);
+    }
+    st.cap = nc;
+  }
+  std::memcpy(st.host, pk.buf.data(), pk.buf.size());
+  TRY_CUDA(cudaMemcpyAsync(c->desc.p, st.host, bytes, cudaMemcpyHostToDevice, c->stream));
+  TRY_CUDA(cudaEventRecord(st.ev, c->stream));
+  st.pending = true;
+  *dbase = static_cast<char*>(c->desc.p);
+  return TCM_OK;
+}
+
+int check_system(const tcm_system* s, const char* what) {
+  if (!s) return set_err(TCM_EINVAL, "%s: null system", what);
+  if (s->n < 0) return set_err(TCM_EINVAL, "%s: negative atom count", what);
+  if (s->dtype != TCM_F32 && s->dtype != TCM_F64) return set_err(TCM_EINVAL, "%s: dtype must be TCM_F32 or TCM_F64", what);
+  if (s->n > 0 && !s->xyzq) return set_err(TCM_EINVAL, "%s: null coordinate pointer", what);
+  if (s->n > 0 && !aligned16(s->xyzq)) return set_err(TCM_EINVAL, "%s: coordinates must be 16-byte aligned", what);
+  if (s->has_center && !(std::isfinite(s->center[0]) && std::isfinite(s->center[1]) && std::isfinite(s->center[2])))
+    return set_err(TCM_EINVAL, "%s: non-finite centre", what);
+  return TCM_OK;
+}
+
+bool geom_known(const tcm_system& s) { return s.has_center && s.radius >= 0.0; }
+
+// Moment-job planning -------------------------------------------------------------
+
+struct JobKey {
+  int sys, L, rot_item;  // rot_item = -1 when unrotated
+  bool operator<(const JobKey& o) const { return std::tie(sys, L, rot_item) < std::tie(o.sys, o.L, o.rot_item); }
+};
+
+struct Plan {
+  std::vector<MomJob> jobs;
+  std::vector<MomTile> tiles;      // grouped by L, each group sorted by cost (largest first)
+  int tile_begin[kLmaxMax + 2] = {};  // tiles of L are [tile_begin[L], tile_begin[L+1])
+  int n_tile_ids = 0;
+  size_t moms_doubles = 0;
+};
+
+void plan_job(tcm_ctx* c, int precision, MomJob& j, int& next_id) {
+  const int nch = moments_nchunks(precision, j.L);
+  const long long per_tile = (long long)kThreads * c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1];
+  long long tpc = (j.n + per_tile - 1) / per_tile;
+  if (tpc < 1) tpc = 1;
+  j.tiles_per_chunk = (int)tpc;
+  j.atoms_per_tile = (int)((j.n + tpc - 1) / tpc);
+  j.tile_base = next_id;
+  next_id += nch * (int)tpc;
+}
+
+double chunk_cost(int precision, int L, int chunk) {
+  const int kmax = moments_kmax(precision);
+  const int nch = plan_nch(L, kmax);
+  const int m0 = plan_m0(L, kmax, nch, chunk), m1 = plan_m0(L, kmax, nch, chunk + 1);
+  return 1.25 * chunk_off(L, m0, m1) + 4.0 * m0 + 30.0;
+}
+
+void build_tiles(int precision, Plan& P) {
+  std::vector<std::vector<std::pair<double, MomTile>>> byL(kLmaxMax + 1);
+  for (int ji = 0; ji < (int)P.jobs.size(); ++ji) {
+    const MomJob& j = P.jobs[ji];
+    const int nch = moments_nchunks(precision, j.L);
+    for (int ch = 0; ch < nch; ++ch) {
+      const double cc = chunk_cost(precision, j.L, ch);
+      for (int t = 0; t < j.tiles_per_chunk; ++t) {
+        const long long i0 = (long long)t * j.atoms_per_tile;
+        const long long cnt = std::max(0LL, std::min((long long)j.atoms_per_tile, j.n - i0));
+        MomTile mt{ji, ch, t, j.tile_base + ch * j.tiles_per_chunk + t};
+        byL[j.L].push_back({cc * (double)cnt, mt});
+      }
+    }
+  }
+  P.tiles.clear();
+  for (int L = 0; L <= kLmaxMax; ++L) {
+    P.tile_begin[L] = (int)P.tiles.size();
+    auto& v = byL[L];
+    std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    for (auto& e : v) P.tiles.push_back(e.second);
+  }
+  P.tile_begin[kLmaxMax + 1] = (int)P.tiles.size();
+}
+
+// Queue the moment pass (step a2/a3) for every job of the plan.
+int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, const MomTile* d_tiles,
+                const SysGeom* d_geoms) {
+  const int kmax = moments_kmax(precision);
+  TRY(dev_ensure(c, c->partials, (size_t)std::max(P.n_tile_ids, 1) * kmax * sizeof(double)));
+  TRY(dev_ensure(c, c->counters, 64 * sizeof(int)));
+  TRY_CUDA(cudaMemsetAsync(c->counters.p, 0, 64 * sizeof(int), c->stream));
+  int* counters = static_cast<int*>(c->counters.p);
+  double* parts = static_cast<double*>(c->partials.p);
+  int ngroups = 0;
+  for (int L = 0; L <= kLmaxMax; ++L) ngroups += P.tile_begin[L + 1] > P.tile_begin[L];
+  {
+    PhaseScope ps(c, TCM_PHASE_MOMENTS, ngroups);
+    for (int L = 0; L <= kLmaxMax; ++L) {
+      const int b = P.tile_begin[L], e = P.tile_begin[L + 1];
+      if (e == b) continue;
+      const int grid = std::min(e - b, 2 * c->num_sms);
+      TRY_LAUNCH(launch_moments(precision, L, d_jobs, d_tiles + b, e - b, counters + L, d_geoms, parts, grid, c->stream));
+    }
+  }
+  {
+    PhaseScope ps(c, TCM_PHASE_FINALIZE, 1);
+    TRY_LAUNCH(launch_finalize(d_jobs, (int)P.jobs.size(), parts, d_geoms, c->d_cmap[precision == TCM_FP64 ? 0 : 1],
+                               c->d_cmap_off, c->d_ftab, kmax, c->stream));
+  }
+  return TCM_OK;
+}
+
+// Step a1 for the systems that need it (device only, no host round trip).
+int add_geom_jobs(const tcm_system* systems, int n_systems, const std::vector<char>& used,
+                  std::vector<GeomJob>& gjobs, std::vector<GeomTile>& gtiles) {
+  int base = 0;
+  for (int s = 0; s < n_systems; ++s) {
+    if (!used[s] || geom_known(systems[s])) continue;
+    GeomJob g{};
+    g.xyzq = systems[s].xyzq;
+    g.n = systems[s].n;
+    g.dtype = systems[s].dtype;
+    g.geom = s;
+    g.need_center = systems[s].has_center ? 0 : 1;
+    g.need_radius = 1;
+    g.n_tiles = (int)std::max<long long>(1, (g.n + kGeomTileAtoms - 1) / kGeomTileAtoms);
+    g.tile_base = base;
+    base += g.n_tiles;
+    for (int t = 0; t < g.n_tiles; ++t) gtiles.push_back(GeomTile{(int)gjobs.size(), t});
+    gjobs.push_back(g);
+  }
+  return base;
+}
+
+SysGeom host_geom(const tcm_system& s) {
+  SysGeom g{};
+  for (int d = 0; d < 3; ++d) g.c[d] = s.has_center ? s.center[d] : 0.0;
+  g.a = s.radius >= 0.0 ? s.radius : 0.0;
+  return g;
+}
+
+void identity(double* r) {
+  for (int k = 0; k < 9; ++k) r[k] = (k % 4 == 0) ? 1.0 : 0.0;
+}
+
+// Host tables --------------------------------------------------------------------
+
+int build_tables(tcm_ctx* c) {
+  const int N = kLmaxMax + 1;
+  std::vector<long double> fact(2 * N + 2);
+  fact[0] = 1.0L;
+  for (size_t k = 1; k < fact.size(); ++k) fact[k] = fact[k - 1] * (long double)k;
+  std::vector<double> ftab(N * N, 0.0), isf(N * N, 0.0);
+  for (int m = 0; m < N; ++m) {
+    // s_lm: normalisation of the kernel's G_lm (see tcm_internal.h)
+    long double s_prev = 0.0L, s = 1.0L;
+    for (int k = 1; k < 2 * m; k += 2) s *= (long double)k;  // (2m-1)!!
+    for (int l = m; l < N; ++l) {
+      if (l == m + 1) {
+        s_prev = s;
+        s = (long double)(2 * m + 1) * s;
+      } else if (l > m + 1) {
+        const long double sn = (long double)(l - 1 + m) * s_prev / (long double)(l - m);
+        s_prev = s;
+        s = sn;
+      }
+      const long double sgn = (m & 1) ? -1.0L : 1.0L;
+      ftab[l * N + m] = (double)(sgn * std::sqrt(fact[l - m] / fact[l + m]) * s);
+      isf[l * N + m] = (double)(1.0L / std::sqrt(fact[l + m] * fact[l - m]));
+    }
+  }
+  std::vector<int> off(N + 1, 0);
+  for (int L = 0; L < N; ++L) off[L + 1] = off[L] + (L + 1) * (L + 1);
+  std::vector<int2> cmap[2];
+  for (int pi = 0; pi < 2; ++pi) {
+    const int prec = pi == 0 ? TCM_FP64 : TCM_MIXED;
+    const int kmax = moments_kmax(prec);
+    cmap[pi].assign(off[N], make_int2(-1, -1));
+    for (int L = 0; L < N; ++L) {
+      const int nch = plan_nch(L, kmax);
+      for (int ch = 0; ch < nch; ++ch) {
+        const int m0 = plan_m0(L, kmax, nch, ch), m1 = plan_m0(L, kmax, nch, ch + 1);
+        for (int m = m0; m < m1; ++m)
+          for (int l = m; l <= L; ++l) {
+            const int slot = chunk_off(L, m0, m) + (m == 0 ? l : 2 * (l - m));
+            if (m == 0) {
+              cmap[pi][off[L] + l * l] = make_int2(ch, slot);
+            } else {
+              cmap[pi][off[L] + l * l + 2 * m - 1] = make_int2(ch, slot);
+              cmap[pi][off[L] + l * l + 2 * m] = make_int2(ch, slot + 1);
+            }
+          }
+      }
+    }
+  }
+  for (int pi = 0; pi < 2; ++pi)
+    for (const int2& e : cmap[pi])
+      if (e.x < 0 || e.y < 0 || e.y >= moments_kmax(pi == 0 ? TCM_FP64 : TCM_MIXED))
+        return set_err(TCM_ECUDA, "internal error: incomplete moment component map");
+  TRY_CUDA(cudaMalloc(&c->d_ftab, ftab.size() * sizeof(double)));
+  TRY_CUDA(cudaMalloc(&c->d_isf, isf.size() * sizeof(double)));
+  TRY_CUDA(cudaMalloc(&c->d_cmap_off, off.size() * sizeof(int)));
+  for (int pi = 0; pi < 2; ++pi) TRY_CUDA(cudaMalloc(&c->d_cmap[pi], cmap[pi].size() * sizeof(int2)));
+  TRY_CUDA(cudaMemcpy(c->d_ftab, ftab.data(), ftab.size() * sizeof(double), cudaMemcpyHostToDevice));
+  TRY_CUDA(cudaMemcpy(c->d_isf, isf.data(), isf.size() * sizeof(double), cudaMemcpyHostToDevice));
+  TRY_CUDA(cudaMemcpy(c->d_cmap_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+  for (int pi = 0; pi < 2; ++pi)
+    TRY_CUDA(cudaMemcpy(c->d_cmap[pi], cmap[pi].data(), cmap[pi].size() * sizeof(int2), cudaMemcpyHostToDevice));
+  return TCM_OK;
+}
+
+void free_ctx(tcm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->d_ftab);
+  cudaFree(c->d_isf);
+  cudaFree(c->d_cmap_off);
+  for (auto* p : c->d_cmap) cudaFree(p);
+  for (DevBuf* b : {&c->desc, &c->partials, &c->gpart, &c->counters, &c->moms, &c->escr, &c->dpart}) cudaFree(b->p);
+  for (auto& st : c->stage) {
+    if (st.host) cudaFreeHost(st.host);
+    if (st.ev) cudaEventDestroy(st.ev);
+  }
+  if (c->pinned_small) cudaFreeHost(c->pinned_small);
+  for (auto& m : c->marks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+int check_ctx(tcm_ctx* c) {
+  if (!c) return set_err(TCM_EINVAL, "null context");
+  TRY_CUDA(cudaSetDevice(c->device));
+  return TCM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tcm_last_error(void) { return g_err; }
+
+int tcm_ctx_create(tcm_ctx_t* out, int lmax_cap, void* cuda_stream) {
+  if (!out) return set_err(TCM_EINVAL, "tcm_ctx_create: null output pointer");
+  *out = nullptr;
+  if (lmax_cap < 0 || lmax_cap > TCM_LMAX_MAX)
+    return set_err(TCM_EINVAL, "tcm_ctx_create: lmax_cap %d outside [0, %d]", lmax_cap, TCM_LMAX_MAX);
+  tcm_ctx* c = new (std::nothrow) tcm_ctx();
+  if (!c) return set_err(TCM_ENOMEM, "tcm_ctx_create: host allocation failed");
+  int rc = TCM_OK;
+  do {
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+      rc = set_err(TCM_ECUDA, "tcm_ctx_create: no usable CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    c->lmax_cap = lmax_cap;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if ((rc = build_tables(c)) != TCM_OK) break;
+    for (auto& st : c->stage)
+      if (cudaEventCreateWithFlags(&st.ev, cudaEventDisableTiming) != cudaSuccess) {
+        rc = set_err(TCM_ECUDA, "tcm_ctx_create: cudaEventCreate failed");
+        break;
+      }
+    if (rc != TCM_OK) break;
+    if (cudaHostAlloc(&c->pinned_small, 256, cudaHostAllocDefault) != cudaSuccess) {
+      rc = set_err(TCM_ENOMEM, "tcm_ctx_create: cudaHostAlloc failed");
+      break;
+    }
+  } while (0);
+  if (rc != TCM_OK) {
+    free_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return TCM_OK;
+}
+
+void tcm_ctx_destroy(tcm_ctx_t c) { free_ctx(c); }
+
+int tcm_ctx_set_stream(tcm_ctx_t c, void* cuda_stream) {
+  TRY(check_ctx(c));
+  TRY_CUDA(cudaStreamSynchronize(c->stream));
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return TCM_OK;
+}
+
+int tcm_ctx_set_profiling(tcm_ctx_t c, int enable) {
+  TRY(check_ctx(c));
+  c->prof = enable != 0;
+  return TCM_OK;
+}
+
+int tcm_ctx_read_profile(tcm_ctx_t c, double* ms, int64_t* launches) {
+  TRY(check_ctx(c));
+  TRY_CUDA(cudaStreamSynchronize(c->stream));
+  double acc[TCM_NPHASES] = {};
+  for (auto& m : c->marks) {
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess) acc[m.phase] += t;
+    c->ev_pool.push_back(m.a);
+    c->ev_pool.push_back(m.b);
+  }
+  c->marks.clear();
+  for (int k = 0; k < TCM_NPHASES; ++k) {
+    if (ms) ms[k] = acc[k];
+    if (launches) launches[k] = c->launches[k];
+    c->launches[k] = 0;
+  }
+  return TCM_OK;
+}
+
+int tcm_prepare(tcm_ctx_t c, tcm_system* s) {
+  TRY(check_ctx(c));
+  TRY(check_system(s, "tcm_prepare"));
+  if (geom_known(*s)) return TCM_OK;
+  std::vector<char> used(1, 1);
+  std::vector<GeomJob> gjobs;
+  std::vector<GeomTile> gtiles;
+  const int ngt = add_geom_jobs(s, 1, used, gjobs, gtiles);
+  std::vector<SysGeom> geoms{host_geom(*s)};
+  Packer pk;
+  const size_t o_geo = pk.add(geoms), o_gj = pk.add(gjobs), o_gt = pk.add(gtiles);
+  char* base = nullptr;
+  TRY(upload(c, pk, &base));
+  TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double)));
+  SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
+  {
+    PhaseScope ps(c, TCM_PHASE_GEOM, 4);
+    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
+                           reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
+                           static_cast<double*>(c->gpart.p), d_geo, c->stream));
+  }
+  TRY_CUDA(cudaMemcpyAsync(c->pinned_small, d_geo, sizeof(SysGeom), cudaMemcpyDeviceToHost, c->stream));
+  TRY_CUDA(cudaStreamSynchronize(c->stream));
+  const SysGeom* g = static_cast<const SysGeom*>(c->pinned_small);
+  for (int d = 0; d < 3; ++d) s->center[d] = g->c[d];
+  s->has_center = 1;
+  s->radius = g->a;
+  return TCM_OK;
+}
+
+int tcm_moments(tcm_ctx_t c, const tcm_system* s, const double* rot, int lmax, int precision, tcm_moments_t* out) {
+  TRY(check_ctx(c));
+  TRY(check_system(s, "tcm_moments"));
+  if (!out || !out->q) return set_err(TCM_EINVAL, "tcm_moments: null output");
+  if (!aligned16(out->q)) return set_err(TCM_EINVAL, "tcm_moments: output must be 16-byte aligned");
+  if (lmax < 0 || lmax > c->lmax_cap)
+    return set_err(TCM_EINVAL, "tcm_moments: lmax %d outside [0, %d]", lmax, c->lmax_cap);
+  if (precision != TCM_FP64 && precision != TCM_MIXED) return set_err(TCM_EINVAL, "tcm_moments: bad precision");
+  Plan P;
+  MomJob j{};
+  j.xyzq = s->xyzq;
+  j.n = s->n;
+  j.dtype = s->dtype;
+  j.L = lmax;
+  j.geom = 0;
+  if (rot)
+    std::memcpy(j.rot, rot, 9 * sizeof(double));
+  else
+    identity(j.rot);
+  j.out = out->q;
+  int next = 0;
+  plan_job(c, precision, j, next);
+  P.jobs.push_back(j);
+  P.n_tile_ids = next;
+  build_tiles(precision, P);
+  std::vector<char> used(1, 1);
+  std::vector<GeomJob> gjobs;
+  std::vector<GeomTile> gtiles;
+  const int ngt = add_geom_jobs(s, 1, used, gjobs, gtiles);
+  std::vector<SysGeom> geoms{host_geom(*s)};
+  Packer pk;
+  const size_t o_geo = pk.add(geoms), o_job = pk.add(P.jobs), o_tile = pk.add(P.tiles), o_gj = pk.add(gjobs),
+               o_gt = pk.add(gtiles);
+  char* base = nullptr;
+  TRY(upload(c, pk, &base));
+  SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
+  if (!gjobs.empty()) {
+    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double)));
+    PhaseScope ps(c, TCM_PHASE_GEOM, 4);
+    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
+                           reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
+                           static_cast<double*>(c->gpart.p), d_geo, c->stream));
+  }
+  TRY(run_moments(c, precision, P, reinterpret_cast<MomJob*>(base + o_job), reinterpret_cast<MomTile*>(base + o_tile),
+                  d_geo));
+  out->lmax = lmax;
+  if (!gjobs.empty()) {
+    TRY_CUDA(cudaMemcpyAsync(c->pinned_small, d_geo, sizeof(SysGeom), cudaMemcpyDeviceToHost, c->stream));
+    TRY_CUDA(cudaStreamSynchronize(c->stream));
+    const SysGeom* g = static_cast<const SysGeom*>(c->pinned_small);
+    for (int d = 0; d < 3; ++d) out->center[d] = g->c[d];
+    out->radius = g->a;
+  } else {
+    for (int d = 0; d < 3; ++d) out->center[d] = s->center[d];
+    out->radius = s->radius;
+  }
+  return TCM_OK;
+}
+
+int tcm_energy(tcm_ctx_t c, const tcm_moments_t* A, const tcm_moments_t* B, const double* R0, int lmax, double* E) {
+  TRY(check_ctx(c));
+  if (!A || !B || !R0 || !E || !A->q || !B->q) return set_err(TCM_EINVAL, "tcm_energy: null argument");
+  if (lmax < 0 || lmax > c->lmax_cap || lmax > A->lmax || lmax > B->lmax)
+    return set_err(TCM_EINVAL, "tcm_energy: lmax %d exceeds the moments' lmax or the context cap", lmax);
+  const double R = std::sqrt(R0[0] * R0[0] + R0[1] * R0[1] + R0[2] * R0[2]);
+  if (!(R > A->radius + B->radius))
+    return set_err(TCM_ENOTCONV, "tcm_energy: |R0| = %.17g <= a_A + a_B = %.17g (Eq. (mainCond))", R,
+                   A->radius + B->radius);
+  std::vector<MomJob> jobs(2);
+  std::memset(jobs.data(), 0, 2 * sizeof(MomJob));
+  jobs[0].out = A->q;
+  jobs[0].L = A->lmax;
+  jobs[1].out = B->q;
+  jobs[1].L = B->lmax;
+  std::vector<SysGeom> geoms(2);
+  std::memset(geoms.data(), 0, 2 * sizeof(SysGeom));
+  geoms[0].a = A->radius;
+  geoms[1].a = B->radius;
+  std::vector<PairDesc> items(1);
+  items[0] = PairDesc{0, 1, 0, 1, lmax, 0, {R0[0], R0[1], R0[2]}};
+  Packer pk;
+  const size_t o_job = pk.add(jobs), o_geo = pk.add(geoms), o_it = pk.add(items);
+  char* base = nullptr;
+  TRY(upload(c, pk, &base));
+  TRY(dev_ensure(c, c->escr, 64));
+  double* dE = static_cast<double*>(c->escr.p);
+  {
+    PhaseScope ps(c, TCM_PHASE_CONTRACT, 1);
+    TRY_LAUNCH(launch_contract(reinterpret_cast<PairDesc*>(base + o_it), 1, lmax,
+                               reinterpret_cast<MomJob*>(base + o_job), reinterpret_cast<SysGeom*>(base + o_geo),
+                               c->d_isf, dE, nullptr, c->stream));
+  }
+  TRY_CUDA(cudaMemcpyAsync(c->pinned_small, dE, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TRY_CUDA(cudaStreamSynchronize(c->stream));
+  *E = *static_cast<const double*>(c->pinned_small);
+  return TCM_OK;
+}
+
+int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t n_items, const tcm_pair_item* items,
+                     int precision, double* E, int32_t* status) {
+  TRY(check_ctx(c));
+  if (n_items < 0 || n_systems < 0) return set_err(TCM_EINVAL, "tcm_energy_batch: negative count");
+  if (n_items == 0) return TCM_OK;
+  if (!systems || !items || !E) return set_err(TCM_EINVAL, "tcm_energy_batch: null argument");
+  if (n_items > (1LL << 30)) return set_err(TCM_EINVAL, "tcm_energy_batch: too many items");
+  if (precision != TCM_FP64 && precision != TCM_MIXED) return set_err(TCM_EINVAL, "tcm_energy_batch: bad precision");
+  std::vector<char> used(n_systems, 0);
+  for (int64_t k = 0; k < n_items; ++k) {
+    const tcm_pair_item& it = items[k];
+    if (it.a < 0 || it.a >= n_systems || it.b < 0 || it.b >= n_systems)
+      return set_err(TCM_EINVAL, "tcm_energy_batch: item %lld refers to a system outside [0, %d)", (long long)k, n_systems);
+    if (it.lmax < 0 || it.lmax > c->lmax_cap)
+      return set_err(TCM_EINVAL, "tcm_energy_batch: item %lld lmax %d outside [0, %d]", (long long)k, it.lmax, c->lmax_cap);
+    used[it.a] = used[it.b] = 1;
+  }
+  for (int s = 0; s < n_systems; ++s)
+    if (used[s]) TRY(check_system(&systems[s], "tcm_energy_batch"));
+  // host-known radii: reject non-convergent items before any work is queued
+  for (int64_t k = 0; k < n_items; ++k) {
+    const tcm_pair_item& it = items[k];
+    if (geom_known(systems[it.a]) && geom_known(systems[it.b])) {
+      const double R = std::sqrt(it.R0[0] * it.R0[0] + it.R0[1] * it.R0[1] + it.R0[2] * it.R0[2]);
+      const double aa = systems[it.a].radius + systems[it.b].radius;
+      if (!(R > aa))
+        return set_err(TCM_ENOTCONV, "tcm_energy_batch: item %lld: |R0| = %.17g <= a_A + a_B = %.17g (Eq. (mainCond))",
+                       (long long)k, R, aa);
+    }
+  }
+  // moment jobs (A sides and unrotated B sides shared)
+  Plan P;
+  std::map<JobKey, int> job_of;
+  std::vector<PairDesc> pd(n_items);
+  int next_id = 0;
+  size_t moff = 0;
+  std::vector<size_t> job_moff;
+  auto get_job = [&](int sys, int L, int rot_item, const double* rot) {
+    JobKey key{sys, L, rot_item};
+    auto itr = job_of.find(key);
+    if (itr != job_of.end()) return itr->second;
+    MomJob j{};
+    j.xyzq = systems[sys].xyzq;
+    j.n = systems[sys].n;
+    j.dtype = systems[sys].dtype;
+    j.L = L;
+    j.geom = sys;
+    if (rot)
+      std::memcpy(j.rot, rot, 9 * sizeof(double));
+    else
+      identity(j.rot);
+    plan_job(c, precision, j, next_id);
+    job_moff.push_back(moff);
+    moff += (size_t)(L + 1) * (L + 1);
+    const int id = (int)P.jobs.size();
+    P.jobs.push_back(j);
+    job_of[key] = id;
+    return id;
+  };
+  for (int64_t k = 0; k < n_items; ++k) {
+    const tcm_pair_item& it = items[k];
+    const int ja = get_job(it.a, it.lmax, -1, nullptr);
+    const int jb = it.has_rot ? get_job(it.b, it.lmax, (int)k, it.rotB) : get_job(it.b, it.lmax, -1, nullptr);
+    pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, 0, {it.R0[0], it.R0[1], it.R0[2]}};
+  }
+  P.n_tile_ids = next_id;
+  TRY(dev_ensure(c, c->moms, std::max<size_t>(moff, 1) * sizeof(double)));
+  for (size_t ji = 0; ji < P.jobs.size(); ++ji) P.jobs[ji].out = static_cast<double*>(c->moms.p) + job_moff[ji];
+  build_tiles(precision, P);
+  int Lmax_items = 0;
+  for (int64_t k = 0; k < n_items; ++k) Lmax_items = std::max(Lmax_items, (int)items[k].lmax);
+  std::vector<GeomJob> gjobs;
+  std::vector<GeomTile> gtiles;
+  const int ngt = add_geom_jobs(systems, n_systems, used, gjobs, gtiles);
+  std::vector<SysGeom> geoms(std::max(n_systems, 1));
+  for (int s = 0; s < n_systems; ++s) geoms[s] = host_geom(systems[s]);
+  Packer pk;
+  const size_t o_geo = pk.add(geoms), o_job = pk.add(P.jobs), o_tile = pk.add(P.tiles), o_gj = pk.add(gjobs),
+               o_gt = pk.add(gtiles), o_it = pk.add(pd);
+  char* base = nullptr;
+  TRY(upload(c, pk, &base));
+  SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
+  if (!gjobs.empty()) {
+    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double)));
+    PhaseScope ps(c, TCM_PHASE_GEOM, 4);
+    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
+                           reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
+                           static_cast<double*>(c->gpart.p), d_geo, c->stream));
+  }
+  const MomJob* d_jobs = reinterpret_cast<MomJob*>(base + o_job);
+  TRY(run_moments(c, precision, P, d_jobs, reinterpret_cast<MomTile*>(base + o_tile), d_geo));
+  {
+    PhaseScope ps(c, TCM_PHASE_CONTRACT, 1);
+    TRY_LAUNCH(launch_contract(reinterpret_cast<PairDesc*>(base + o_it), (int)n_items, Lmax_items, d_jobs, d_geo,
+                               c->d_isf, E, status, c->stream));
+  }
+  return TCM_OK;
+}
+
+int tcm_direct(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, const double* rotB, const double* R0, double* E) {
+  TRY(check_ctx(c));
+  TRY(check_system(A, "tcm_direct A"));
+  TRY(check_system(B, "tcm_direct B"));
+  if (!R0 || !E) return set_err(TCM_EINVAL, "tcm_direct: null argument");
+  tcm_system sys[2] = {*A, *B};
+  for (auto& s : sys)
+    if (s.has_center) s.radius = std::max(s.radius, 0.0);  // the direct sum needs centres only
+  std::vector<char> used(2, 1);
+  std::vector<GeomJob> gjobs;
+  std::vector<GeomTile> gtiles;
+  const int ngt = add_geom_jobs(sys, 2, used, gjobs, gtiles);
+  std::vector<SysGeom> geoms{host_geom(sys[0]), host_geom(sys[1])};
+  std::vector<double> xf(12);
+  if (rotB)
+    std::memcpy(xf.data(), rotB, 9 * sizeof(double));
+  else
+    identity(xf.data());
+  for (int d = 0; d < 3; ++d) xf[9 + d] = R0[d];
+  Packer pk;
+  const size_t o_geo = pk.add(geoms), o_xf = pk.add(xf), o_gj = pk.add(gjobs), o_gt = pk.add(gtiles);
+  char* base = nullptr;
+  TRY(upload(c, pk, &base));
+  SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
+  if (!gjobs.empty()) {
+    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double)));
+    PhaseScope ps(c, TCM_PHASE_GEOM, 4);
+    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
+                           reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
+                           static_cast<double*>(c->gpart.p), d_geo, c->stream));
+  }
+  const int nblk = direct_blocks(A->n);
+  TRY(dev_ensure(c, c->dpart, (size_t)std::max(nblk, 1) * sizeof(double)));
+  TRY(dev_ensure(c, c->escr, 64));
+  double* dE = static_cast<double*>(c->escr.p);
+  {
+    PhaseScope ps(c, TCM_PHASE_DIRECT, nblk > 0 ? 2 : 1);
+    TRY_LAUNCH(launch_direct(A->xyzq, A->n, A->dtype, B->xyzq, B->n, B->dtype, d_geo,
+                             reinterpret_cast<double*>(base + o_xf), static_cast<double*>(c->dpart.p), nblk, dE,
+                             c->stream));
+  }
+  TRY_CUDA(cudaMemcpyAsync(c->pinned_small, dE, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TRY_CUDA(cudaStreamSynchronize(c->stream));
+  *E = *static_cast<const double*>(c->pinned_small);
+  return TCM_OK;
+}
+
+}  // extern "C"

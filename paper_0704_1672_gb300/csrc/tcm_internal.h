@@ -1,0 +1,152 @@
+// Internal definitions shared by the CUDA translation units of libtcm.so.
+//
+// Moment kernel formulation (Eq. (multipole)).  For one charge q at r = |r| rhat
+// the regular solid harmonic is q r^l C_lm(rhat) with C_lm = sqrt(4pi/(2l+1)) Y_lm.
+// The kernels never evaluate a trigonometric function: with u = (x + iy)/r and
+// c = z/r they run, per column m, the three-term recurrence
+//     G_mm     = u^m
+//     G_m+1,m  = c G_mm
+//     G_l+1,m  = k_lm c G_lm - G_l-1,m           (l >= m+1)
+// whose normalisation is chosen so that the G_l-1 coefficient is exactly one, and
+// accumulate q (r/a)^l G_lm.  The deferred factor F_lm a^l (F_lm below) turns the
+// sums into Q_lm.  Per real component this is one FMUL shared by Re/Im, one FFMA
+// for the recurrence and one FFMA for the accumulation.
+//
+// Accumulators live in registers, so the (Lmax+1)^2 components are split into
+// column chunks [m0, m1) of at most kmax accumulators; a chunk is a separate tile
+// of work that re-reads the atoms.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/tcm.h"
+
+namespace tcm {
+
+constexpr int kLmaxMax = TCM_LMAX_MAX;
+constexpr int kThreads = 128;  // threads per moment CTA (4 warps)
+
+// Accumulator budget per thread for the float and double moment kernels.
+constexpr int kKmaxF32 = 160;
+constexpr int kKmaxF64 = 80;
+
+// ---------------------------------------------------------------------------------
+// Column-chunk plan (host and device, compile time).
+__host__ __device__ constexpr int col_acc(int L, int m) { return m == 0 ? (L + 1) : 2 * (L - m + 1); }
+
+// First column of chunk c when the columns 0..L are split greedily into nch chunks
+// of at most kmax accumulators, each filled up to the balanced target.
+__host__ __device__ constexpr int plan_m0(int L, int kmax, int nch, int c) {
+  int total = (L + 1) * (L + 1);
+  int target = (total + nch - 1) / nch;
+  int m = 0;
+  for (int cc = 0; cc < nch; ++cc) {
+    if (cc == c) return m;
+    int acc = 0;
+    while (m <= L && acc + col_acc(L, m) <= kmax && (acc < target || acc == 0)) {
+      acc += col_acc(L, m);
+      ++m;
+    }
+  }
+  return m;
+}
+__host__ __device__ constexpr int plan_nch(int L, int kmax) {
+  int n = 1;
+  while (plan_m0(L, kmax, n, n) != L + 1) ++n;
+  return n;
+}
+// Accumulator offset of column m inside the chunk that starts at m0.
+__host__ __device__ constexpr int chunk_off(int L, int m0, int m) {
+  int o = 0;
+  for (int k = m0; k < m; ++k) o += col_acc(L, k);
+  return o;
+}
+
+// Recurrence coefficient k_lm (l >= m+1), from the ratio r_l = s_l / s_l-1 of the
+// normalisations s_lm with F_lm = P_l^m e^{i m phi} = s_lm G_lm:
+//   s_mm = (2m-1)!!, s_m+1,m = (2m+1) s_mm, s_l+1 = (l+m) s_l-1 / (l-m+1).
+__host__ __device__ constexpr double kcoef(int l, int m) {
+  double r = 2.0 * m + 1.0;  // r_{m+1}
+  for (int j = m + 1; j < l; ++j) r = (double)(j + m) / ((double)(j - m + 1) * r);
+  return (2.0 * l + 1.0) * r / (double)(l + m);
+}
+
+// ---------------------------------------------------------------------------------
+// Device descriptors.
+
+struct SysGeom {   // centre and radius of one system (device)
+  double c[3];
+  double a;
+};
+
+struct MomJob {    // one moment set: a system at one Lmax under one rotation
+  const void* xyzq;
+  long long n;
+  int dtype;
+  int L;
+  int geom;        // index into the SysGeom array
+  int tiles_per_chunk;
+  int atoms_per_tile;
+  int tile_base;   // id of the job's first tile; tile id = base + chunk * tpc + t
+  double rot[9];   // row-major, identity when unrotated
+  double* out;     // packed moments, (L+1)^2 doubles
+};
+
+struct MomTile {   // one tile of moment work
+  int job;
+  int chunk;
+  int t;           // tile index inside the chunk
+  int id;          // global tile id (row of the partials buffer)
+};
+
+struct GeomJob {   // a1: centroid and/or radius of one system
+  const void* xyzq;
+  long long n;
+  int dtype;
+  int geom;
+  int need_center;
+  int need_radius;
+  int tile_base;
+  int n_tiles;
+};
+
+struct GeomTile {
+  int gjob;
+  int t;
+};
+
+struct PairDesc {  // one energy: moments of jobA and jobB at lmax L, separation R0
+  int jobA, jobB;
+  int geomA, geomB;
+  int L;
+  int pad;
+  double R0[3];
+};
+
+constexpr int kGeomTileAtoms = 16384;
+
+// ---------------------------------------------------------------------------------
+// Launchers (defined in the .cu files).
+
+// Moment kernels: one persistent launch over `n_tiles` tiles of Lmax L.
+// precision: TCM_MIXED (float kernels) or TCM_FP64 (double kernels).
+int launch_moments(int precision, int L, const MomJob* jobs, const MomTile* tiles, int n_tiles,
+                   int* counter, const SysGeom* geoms, double* partials, int grid, cudaStream_t s);
+int moments_smem_bytes(int precision, int L);
+int moments_kmax(int precision);
+int moments_nchunks(int precision, int L);
+
+int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n_gtiles, double* gpart,
+                SysGeom* geoms, cudaStream_t s);
+int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms,
+                    const int2* cmap, const int* cmap_off, const double* ftab, int kmax, cudaStream_t s);
+int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const MomJob* jobs,
+                    const SysGeom* geoms, const double* isf, double* E, int32_t* status, cudaStream_t s);
+int launch_direct(const void* a, long long na, int dta, const void* b, long long nb, int dtb,
+                  const SysGeom* geo /* device: [A, B] centres */, const double* xf /* device: rot[9], R0[3] */,
+                  double* part, int nblk, double* E, cudaStream_t s);
+int direct_blocks(long long na);
+
+}  // namespace tcm

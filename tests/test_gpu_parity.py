@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element
+on the same seeded inputs (tolerances in tcm_testlib)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_0704_1672_gb300 import synth
+from tcm_testlib import (TOL_FP64, TOL_MIX_E, TOL_MIX_MOM, degree_scales, energy_error, moment_error,
+                         oracle_direct_threaded, oracle_moments_threaded)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tcm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0704_1672_gb300 import build
+    build.build()
+    from paper_0704_1672_gb300 import tcm as t
+    torch.cuda.set_device(0)
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(tcm):
+    c = tcm.Context(lmax_cap=24)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def sphere_system(seed, n, radius=5.0, shift=(0.0, 0.0, 0.0)):
+    rng = np.random.default_rng(seed)
+    S = synth.pack(synth.uniform_ball(rng, n, radius), synth.charges_uniform_net_zero(rng, n) if n > 1 else np.ones(n))
+    S[:, :3] += shift
+    return S
+
+
+# ----------------------------------------------------------------------------- moments
+
+@pytest.mark.parametrize("n", [1, 31, 33, 1025, 4100, 9000])
+@pytest.mark.parametrize("L", [0, 1, 2, 7, 10, 13, 20, 24])
+def test_moments_fp64_vs_oracle(ctx, tcm, n, L):
+    S = sphere_system(100 + n, n, shift=(3.0, -1.0, 2.0))
+    c, a = oracle.center_radius(S)
+    m = ctx.tcm_moments(dev(S), L, precision=tcm.TCM_FP64)
+    assert np.allclose(m.center, c, rtol=0, atol=1e-12) and abs(m.radius - a) < 1e-12
+    ref = oracle_moments_threaded(S, c, L)
+    err = moment_error(tcm.unpack(m.q), ref, degree_scales(S, c, L))
+    assert err < TOL_FP64, err
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 1025, 4100, 9000])
+@pytest.mark.parametrize("L", [0, 1, 2, 7, 10, 13, 20, 24])
+def test_moments_mixed_vs_oracle(ctx, tcm, n, L):
+    S = sphere_system(200 + n, n, shift=(-2.0, 0.5, 7.0))
+    c, a = oracle.center_radius(S)
+    m = ctx.tcm_moments(dev(S), L, precision=tcm.TCM_MIXED)
+    ref = oracle_moments_threaded(S, c, L)
+    err = moment_error(tcm.unpack(m.q), ref, degree_scales(S, c, L))
+    assert err < TOL_MIX_MOM, err
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_moments_float32_coordinates_rotation_given_centre(ctx, tcm, precision):
+    rng = np.random.default_rng(5)
+    S = sphere_system(7, 3000, radius=20.0, shift=(100.0, -50.0, 25.0))
+    S32 = S.astype(np.float32).astype(np.float64)  # what the float32 input holds
+    rot = synth.random_rotations(rng, 1)[0]
+    cgiv = np.array([99.5, -50.25, 24.75])
+    L = 16
+    m = ctx.tcm_moments(dev(S32, torch.float32), L, precision=precision, rot=rot, center=cgiv, radius=25.0)
+    assert np.allclose(m.center, cgiv) and m.radius == 25.0
+    ref = oracle_moments_threaded(S32, cgiv, L, rot=rot)
+    err = moment_error(tcm.unpack(m.q), ref, degree_scales(S32, cgiv, L, rot=rot))
+    assert err < (TOL_FP64 if precision == 0 else TOL_MIX_MOM), err
+
+
+def test_moments_empty_and_single_charge_at_centre(ctx, tcm):
+    empty = torch.zeros((0, 4), dtype=torch.float64, device="cuda")
+    m = ctx.tcm_moments(empty, 6, precision=tcm.TCM_MIXED, center=(0, 0, 0), radius=1.0)
+    assert torch.all(m.q == 0)
+    one = dev(np.array([[1.0, 2.0, 3.0, 0.75]]))
+    for prec in (0, 1):
+        m = ctx.tcm_moments(one, 8, precision=prec)  # centroid = the charge itself, radius 0
+        q = m.q.cpu().numpy()
+        assert q[0] == 0.75 and np.all(q[1:] == 0.0)
+
+
+# ----------------------------------------------------------------------------- energies
+
+def test_single_pair_fp64_energy_and_direct(ctx, tcm):
+    """Single-pair workload: 2 x 200 charges in r = 10 A spheres, R0 = 40 A, Lmax = 10, FP64."""
+    s = synth.single_pair_sphere()
+    A, B = dev(s.A), dev(s.B)
+    ma = ctx.tcm_moments(A, s.L, precision=tcm.TCM_FP64)
+    mb = ctx.tcm_moments(B, s.L, precision=tcm.TCM_FP64)
+    R0 = s.R0[0]
+    E = ctx.tcm_energy(ma, mb, R0, s.L)
+    cA, _ = oracle.center_radius(s.A)
+    cB, _ = oracle.center_radius(s.B)
+    QA, QB = oracle.moments(s.A, cA, s.L), oracle.moments(s.B, cB, s.L)
+    Eo = oracle.tcm_energy(s.L, QA, QB, R0)
+    blocks = oracle.tcm_blocks(s.L, QA, QB, R0)
+    assert energy_error(E, Eo, blocks) < TOL_FP64
+    Ed = ctx.tcm_direct(A, B, R0)
+    Edo, scale = oracle.direct(s.A, cA, s.B, cB, R0, return_abs=True)
+    assert abs(Ed - Edo) / scale < TOL_FP64
+    # the batched path at FP64 gives the same energy
+    Eb, st = ctx.tcm_energy_batch([(A, None, None), (B, None, None)], [0], [1], [s.L], R0[None], precision=tcm.TCM_FP64)
+    torch.cuda.synchronize()
+    assert int(st[0]) == 0 and energy_error(float(Eb[0]), Eo, blocks) < TOL_FP64
+
+
+def _config2_check(ctx, tcm, s, E, sample):
+    cA, _ = oracle.center_radius(s.A)
+    cB, _ = oracle.center_radius(s.B)
+    QA = oracle_moments_threaded(s.A, cA, s.L)
+    worst = 0.0
+    for k in sample:
+        QB = oracle_moments_threaded(s.B, cB, s.L, rot=s.rotB[k])
+        Eo = oracle.tcm_energy(s.L, QA, QB, s.R0[k])
+        blocks = oracle.tcm_blocks(s.L, QA, QB, s.R0[k])
+        worst = max(worst, energy_error(float(E[k]), Eo, blocks))
+    return worst
+
+
+def test_protein_pes_scan_full_size_sampled(ctx, tcm):
+    """Protein-like PES scan at full size (2 x 20,000 atoms, 256 orientations, L = 20), mixed
+    precision, the launch the benchmark times; oracle on sampled orientations."""
+    s = synth.protein_pes_scan()
+    A, B = dev(s.A, torch.float32), dev(s.B, torch.float32)
+    k = len(s.R0)
+    E, st = ctx.tcm_energy_batch([(A, None, None), (B, None, None)], np.zeros(k, int), np.ones(k, int),
+                                 np.full(k, s.L), s.R0, rotB=s.rotB, precision=tcm.TCM_MIXED)
+    torch.cuda.synchronize()
+    assert torch.all(st == 0)
+    E = E.cpu().numpy()
+    s32 = synth.PairScan(s.A.astype(np.float32).astype(np.float64), s.B.astype(np.float32).astype(np.float64),
+                         s.rotB, s.R0, s.L)
+    worst = _config2_check(ctx, tcm, s32, E, [0, 97, 255])
+    assert worst < TOL_MIX_E, worst
+
+
+def test_batch_alone_vs_in_mix_and_repeatability(ctx, tcm):
+    """Each item's result is independent of the rest of the batch, and runs repeat bitwise."""
+    rng = np.random.default_rng(17)
+    systems = [sphere_system(300 + i, int(n), radius=float(r)) for i, (n, r) in
+               enumerate([(500, 6.0), (3000, 9.0), (12000, 15.0), (80, 3.0), (7000, 12.0)])]
+    T = [(dev(S, torch.float32), None, None) for S in systems]
+    rad = [oracle.center_radius(S)[1] for S in systems]
+    items = [(0, 1, 12), (2, 3, 24), (1, 4, 8), (4, 2, 16), (3, 0, 10)]
+    a = [i[0] for i in items]
+    b = [i[1] for i in items]
+    L = [i[2] for i in items]
+    R0 = np.array([synth.unit_vectors(rng, 1)[0] * 1.7 * (rad[i] + rad[j]) for i, j, _ in items])
+    rot = synth.random_rotations(rng, len(items))
+    E_mix, _ = ctx.tcm_energy_batch(T, a, b, L, R0, rotB=rot, precision=tcm.TCM_MIXED)
+    E_mix2, _ = ctx.tcm_energy_batch(T, a, b, L, R0, rotB=rot, precision=tcm.TCM_MIXED)
+    torch.cuda.synchronize()
+    assert torch.equal(E_mix, E_mix2)
+    for k in range(len(items)):
+        E1, _ = ctx.tcm_energy_batch(T, [a[k]], [b[k]], [L[k]], R0[k:k + 1], rotB=rot[k:k + 1], precision=tcm.TCM_MIXED)
+        torch.cuda.synchronize()
+        assert float(E1[0]) == float(E_mix[k])
+    # and each is right
+    for k in range(len(items)):
+        Sa, Sb = systems[a[k]].astype(np.float32).astype(np.float64), systems[b[k]].astype(np.float32).astype(np.float64)
+        ca, cb = oracle.center_radius(Sa)[0], oracle.center_radius(Sb)[0]
+        QA = oracle_moments_threaded(Sa, ca, L[k])
+        QB = oracle_moments_threaded(Sb, cb, L[k], rot=rot[k])
+        Eo = oracle.tcm_energy(L[k], QA, QB, R0[k])
+        assert energy_error(float(E_mix[k]), Eo, oracle.tcm_blocks(L[k], QA, QB, R0[k])) < TOL_MIX_E
+
+
+# ----------------------------------------------------------------------------- error paths
+
+def test_not_converged_paths(ctx, tcm):
+    S = sphere_system(11, 100, radius=5.0)
+    A = dev(S)
+    m = ctx.tcm_moments(A, 4, precision=tcm.TCM_FP64)
+    with pytest.raises(tcm.TcmError) as e:
+        ctx.tcm_energy(m, m, [0.0, 0.0, 1.5 * m.radius], 4)
+    assert e.value.code == tcm.TCM_ENOTCONV
+    # host-known radii: rejected before any work
+    with pytest.raises(tcm.TcmError) as e:
+        ctx.tcm_energy_batch([(A, m.center, m.radius)], [0], [0], [4], [[0.0, 0.0, 1.0]])
+    assert e.value.code == tcm.TCM_ENOTCONV
+    # radii computed on the device: NaN and a per-item status
+    E, st = ctx.tcm_energy_batch([(A, None, None)], [0, 0], [0, 0], [4, 4],
+                                 [[0.0, 0.0, 1.0], [0.0, 0.0, 3.0 * m.radius]])
+    torch.cuda.synchronize()
+    assert int(st[0]) == tcm.TCM_ENOTCONV and np.isnan(float(E[0]))
+    assert int(st[1]) == tcm.TCM_OK and np.isfinite(float(E[1]))
+
+
+def test_invalid_arguments(ctx, tcm):
+    S = dev(sphere_system(12, 64))
+    with pytest.raises(tcm.TcmError) as e:
+        ctx.tcm_moments(S, 25)
+    assert e.value.code == tcm.TCM_EINVAL
+    raw = torch.zeros(4 * 64 + 1, dtype=torch.float32, device="cuda")
+    mis = raw[1:].view(64, 4)  # 4-byte offset: not 16-byte aligned
+    with pytest.raises(tcm.TcmError) as e:
+        ctx.tcm_moments(mis, 4)
+    assert e.value.code == tcm.TCM_EINVAL
+    with pytest.raises(tcm.TcmError) as e:
+        ctx.tcm_energy_batch([(S, None, None)], [0], [3], [4], [[0.0, 0.0, 100.0]])
+    assert e.value.code == tcm.TCM_EINVAL
