@@ -161,8 +161,7 @@ __global__ void __launch_bounds__(256) k_finalize(const MomJob* __restrict__ job
   const MomJob& job = jobs[blockIdx.x];
   const int L = job.L;
   const int tpc = job.tiles_per_chunk;
-  double a = geoms[job.geom].a;
-  if (!(a > 0.0)) a = 1.0;
+  const double a = scale_radius(geoms[job.geom].a);  // the moment kernels scaled by 1/a
   if (threadIdx.x <= L) {
     double p = 1.0;
     for (int k = 0; k < (int)threadIdx.x; ++k) p *= a;

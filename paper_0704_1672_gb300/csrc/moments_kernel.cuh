@@ -4,11 +4,12 @@
 // per tile.  Included by the per-Lmax translation units, which instantiate
 // launch_moments_t<T, L> explicitly.
 //
-// Per atom (after the per-tile transform M = rot / a and the split centre
-// c = c_hi + c_lo):
+// Per atom (after the per-tile transform M = rot / a', a' = scale_radius(a) a power of
+// two, and the split centre c = c_hi + c_lo):
 //   d   = (x - c_hi) - c_lo                       exact-ish centring in float
 //   p   = M d                                     rotation and radius scaling fused
-//   rinv = rsqrt(|p|^2), u = (p_x + i p_y) rinv, c = p_z rinv, rho = |p|
+//   rinv = rsqrt(|p|^2) (+ one Newton step in float), u = (p_x + i p_y) rinv,
+//   c = p_z rinv, rho = |p|
 //   column recurrences of tcm_internal.h, accumulating q rho^l G_lm.
 // No trigonometric function and no division is evaluated per atom.
 #pragma once
@@ -127,8 +128,7 @@ struct Xform {
 template <typename T>
 __device__ __forceinline__ Xform<T> make_xform(const MomJob& job, const SysGeom& g) {
   Xform<T> x;
-  const double a = g.a > 0.0 ? g.a : 1.0;
-  const double ia = 1.0 / a;
+  const double ia = 1.0 / scale_radius(g.a);  // exact: a power of two
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     x.chi[k] = (T)g.c[k];
@@ -162,7 +162,11 @@ __device__ __forceinline__ void load_setup(const void* xyzq, int dtype, long lon
   const T py = fmaT(xf.M[3], d0, fmaT(xf.M[4], d1, xf.M[5] * d2));
   const T pz = fmaT(xf.M[6], d0, fmaT(xf.M[7], d1, xf.M[8] * d2));
   const T r2 = fmaT(px, px, fmaT(py, py, pz * pz));
-  const T rinv = r2 > (T)0 ? rsqrtT(r2) : (T)0;
+  T rinv = r2 > (T)0 ? rsqrtT(r2) : (T)0;
+  if constexpr (sizeof(T) == 4) {  // one Newton step: the hardware rsqrt is a few ulp off
+    const T h = r2 * rinv;
+    rinv = fmaT(fmaT(-h, rinv, (T)1), (T)0.5 * rinv, rinv);
+  }
   ux = px * rinv;
   uy = py * rinv;
   cz = pz * rinv;

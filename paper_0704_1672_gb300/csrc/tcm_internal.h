@@ -19,6 +19,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 
 #include "../../include/tcm.h"
@@ -71,6 +72,15 @@ __host__ __device__ constexpr double kcoef(int l, int m) {
   double r = 2.0 * m + 1.0;  // r_{m+1}
   for (int j = m + 1; j < l; ++j) r = (double)(j + m) / ((double)(j - m + 1) * r);
   return (2.0 * l + 1.0) * r / (double)(l + m);
+}
+
+// Scaling radius used by the moment kernels: the smallest power of two >= a, so that
+// 1/a' is exact in float and the final factor a'^l exact in double.
+__host__ __device__ inline double scale_radius(double a) {
+  if (!(a > 0.0)) return 1.0;
+  int e = 0;
+  frexp(a, &e);  // a = f 2^e, 0.5 <= f < 1
+  return ldexp(1.0, e);
 }
 
 // ---------------------------------------------------------------------------------

@@ -6,8 +6,8 @@ import torch
 
 import oracle
 from paper_0704_1672_gb300 import synth
-from tcm_testlib import (TOL_FP64, TOL_MIX_E, TOL_MIX_MOM, degree_scales, energy_error, moment_error,
-                         oracle_direct_threaded, oracle_moments_threaded)
+from tcm_testlib import (TOL_FP64, TOL_MIX_E, TOL_MIX_MOM, degree_scales, energy_error, energy_error_vs_e,
+                         moment_error, oracle_moments_threaded)
 
 pytestmark = pytest.mark.gpu
 
@@ -121,12 +121,14 @@ def _config2_check(ctx, tcm, s, E, sample):
     cA, _ = oracle.center_radius(s.A)
     cB, _ = oracle.center_radius(s.B)
     QA = oracle_moments_threaded(s.A, cA, s.L)
-    worst = 0.0
+    worst = worst_e = 0.0
     for k in sample:
         QB = oracle_moments_threaded(s.B, cB, s.L, rot=s.rotB[k])
         Eo = oracle.tcm_energy(s.L, QA, QB, s.R0[k])
         blocks = oracle.tcm_blocks(s.L, QA, QB, s.R0[k])
-        worst = max(worst, energy_error(float(E[k]), Eo, blocks))
+        worst = max(worst, energy_error(float(E[k]), Eo, blocks, mixed=True))
+        worst_e = max(worst_e, energy_error_vs_e(float(E[k]), Eo))
+    print(f"mixed energy error: {worst:.3e} of the condition scale, {worst_e:.3e} of |E|")
     return worst
 
 
@@ -175,7 +177,10 @@ def test_batch_alone_vs_in_mix_and_repeatability(ctx, tcm):
         QA = oracle_moments_threaded(Sa, ca, L[k])
         QB = oracle_moments_threaded(Sb, cb, L[k], rot=rot[k])
         Eo = oracle.tcm_energy(L[k], QA, QB, R0[k])
-        assert energy_error(float(E_mix[k]), Eo, oracle.tcm_blocks(L[k], QA, QB, R0[k])) < TOL_MIX_E
+        err = energy_error(float(E_mix[k]), Eo, oracle.tcm_blocks(L[k], QA, QB, R0[k]), mixed=True)
+        print(f"item {k}: mixed energy error {err:.3e} of the condition scale, "
+              f"{energy_error_vs_e(float(E_mix[k]), Eo):.3e} of |E|")
+        assert err < TOL_MIX_E
 
 
 # ----------------------------------------------------------------------------- error paths
