@@ -179,6 +179,37 @@ int tcm_energy_batch(tcm_ctx_t ctx, int n_systems, const tcm_system* systems, in
 int tcm_direct(tcm_ctx_t ctx, const tcm_system* A, const tcm_system* B, const double* rotB,
                const double* R0, double* E);
 
+/* Largest atom count accepted by tcm_moments_noalloc. */
+#define TCM_NOALLOC_MAX_ATOMS 262144
+
+/* The paper has no counterpart to this call; it exists for callers that cannot allocate
+ * device memory.  Examples: code that must not let cudaMalloc/cudaFree synchronise the
+ * device in the middle of its work, applications whose own allocator owns all device
+ * memory, and plug-ins that are not allowed to create allocations.  A context
+ * (tcm_ctx_create) allocates, so such callers use this instead of tcm_moments.
+ *
+ * It computes the same moments as tcm_moments (Eq. (multipole)) of system s, optionally
+ * rotated by rot (row-major host double[9], NULL = identity), into q_out (device,
+ * (lmax+1)^2 packed doubles, 16-byte aligned).  If center_radius_out is not NULL it
+ * receives (device, 4 doubles) the centre and radius used: the given ones, or the
+ * centroid and radius computed on the device when s has no centre or no radius.
+ * precision is TCM_FP64 or TCM_MIXED.  The work is queued on cuda_stream (a
+ * cudaStream_t; NULL = legacy default stream) and the call returns without waiting.
+ *
+ * Memory: instead of allocating, the call uses one fixed scratch array of about 0.5 MiB
+ * defined in the library as device memory.  Every GPU that loads the library holds its
+ * own copy until the process exits.  All calls on a GPU share that array and it keeps
+ * the last call's contents (each call rewrites what it reads), so calls whose work
+ * overlaps on the GPU race on it: serialise them (one stream, or events).
+ * Limits: 0 <= s->n <= TCM_NOALLOC_MAX_ATOMS and 0 <= lmax <= TCM_LMAX_MAX; larger
+ * requests return TCM_EINVAL with a message.
+ * Set-up: the first call on each GPU (with that GPU current) looks up the scratch
+ * address and copies the coefficient tables into it, synchronously; make that first
+ * call before any stream capture.
+ * Errors are reported as by the other calls (status code, tcm_last_error()). */
+int tcm_moments_noalloc(const tcm_system* s, const double* rot, int lmax, int precision, double* q_out,
+                        double* center_radius_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -415,6 +415,8 @@ int check_ctx(tcm_ctx* c) {
 
 }  // namespace
 
+int tcm::record_error(int code, const char* msg) { return set_err(code, "%s", msg); }
+
 extern "C" {
 
 const char* tcm_last_error(void) { return g_err; }

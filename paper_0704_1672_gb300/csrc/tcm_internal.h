@@ -159,4 +159,7 @@ int launch_direct(const void* a, long long na, int dta, const void* b, long long
                   double* part, int nblk, double* E, cudaStream_t s);
 int direct_blocks(long long na);
 
+// Sets the calling thread's tcm_last_error() message; returns code.
+int record_error(int code, const char* msg);
+
 }  // namespace tcm

@@ -1,0 +1,227 @@
+// tcm_moments_noalloc: the moment pass (Eq. (multipole)) without any device allocation.
+//
+// Some callers cannot allocate device memory: code that runs where cudaMalloc/cudaFree
+// would synchronise the device and break its latency budget, host applications whose
+// own allocator owns every byte of device memory, and plug-ins that are not allowed to
+// create allocations of their own.  tcm_moments needs a context, and a context
+// allocates (tables at creation, scratch on first use).  This entry point instead keeps
+// everything it needs -- the coefficient tables, the job and tile descriptors, the
+// centre/radius partials and the per-tile moment partials -- in one file-scope
+// __device__ array of fixed size, so a call allocates nothing.  The caller passes the
+// coordinates and the output buffer, as for tcm_moments.
+//
+// The array exists once per device (every GPU that loads the library holds it until the
+// process exits) and all calls on a device share it: two calls whose work overlaps on
+// the GPU race on it, so calls must be serialised (one stream, or events).  Each call
+// rewrites the descriptors and clears the work counters before its kernels run.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "tcm_internal.h"
+
+using namespace tcm;
+
+namespace {
+
+constexpr long long kNaMaxAtoms = TCM_NOALLOC_MAX_ATOMS;
+constexpr int kNaTileAtoms = 4096;                                   // atoms per tile, both precisions
+constexpr int kNaTilesPerChunk = (int)(kNaMaxAtoms / kNaTileAtoms);  // 64
+constexpr int kNaMaxChunks = 10;                                     // most chunks of any (precision, Lmax)
+constexpr int kNaPartialDoubles = kNaTilesPerChunk * 800;            // max over plans of chunks * kmax = 800
+constexpr int kNaMaxTiles = kNaTilesPerChunk * kNaMaxChunks;
+constexpr int kNaGeomTiles = (int)((kNaMaxAtoms + kGeomTileAtoms - 1) / kGeomTileAtoms);
+constexpr int kNaCompTotal = 5525;  // sum over L = 0..24 of (L+1)^2
+
+// Layout of the scratch array (byte offsets, 256-byte aligned sections).
+constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+constexpr size_t kOffPartials = 0;
+constexpr size_t kOffTiles = align256(kOffPartials + sizeof(double) * kNaPartialDoubles);
+constexpr size_t kOffJob = align256(kOffTiles + sizeof(MomTile) * kNaMaxTiles);
+constexpr size_t kOffGeom = align256(kOffJob + sizeof(MomJob));
+constexpr size_t kOffGJob = align256(kOffGeom + sizeof(SysGeom));
+constexpr size_t kOffGTiles = align256(kOffGJob + sizeof(GeomJob));
+constexpr size_t kOffGPart = align256(kOffGTiles + sizeof(GeomTile) * kNaGeomTiles);
+constexpr size_t kOffCounters = align256(kOffGPart + sizeof(double) * 4 * kNaGeomTiles);
+constexpr size_t kOffFtab = align256(kOffCounters + sizeof(int) * 64);
+constexpr size_t kOffCmapOff = align256(kOffFtab + sizeof(double) * (kLmaxMax + 1) * (kLmaxMax + 1));
+constexpr size_t kOffCmap = align256(kOffCmapOff + sizeof(int) * (kLmaxMax + 2));
+constexpr size_t kScratchBytes = align256(kOffCmap + sizeof(int2) * 2 * kNaCompTotal);
+
+// The scratch.  In host code this name is only a stand-in for the symbol; kernels get
+// the device address obtained with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_tcm_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+char* g_scratch_ptr[kMaxDevices] = {};  // device address of the scratch, per device
+
+int na_err(int code, const char* msg) { return record_error(code, msg); }
+
+// Host tables for the finalisation (F_lm and the component -> (chunk, slot) maps); the
+// same values a context uploads at creation.
+void host_tables(std::vector<double>& ftab, std::vector<int>& off, std::vector<int2>& cmap) {
+  const int N = kLmaxMax + 1;
+  std::vector<long double> fact(2 * N + 2);
+  fact[0] = 1.0L;
+  for (size_t k = 1; k < fact.size(); ++k) fact[k] = fact[k - 1] * (long double)k;
+  ftab.assign(N * N, 0.0);
+  for (int m = 0; m < N; ++m) {
+    long double s_prev = 0.0L, s = 1.0L;
+    for (int k = 1; k < 2 * m; k += 2) s *= (long double)k;
+    for (int l = m; l < N; ++l) {
+      if (l == m + 1) {
+        s_prev = s;
+        s = (long double)(2 * m + 1) * s;
+      } else if (l > m + 1) {
+        const long double sn = (long double)(l - 1 + m) * s_prev / (long double)(l - m);
+        s_prev = s;
+        s = sn;
+      }
+      ftab[l * N + m] = (double)(((m & 1) ? -1.0L : 1.0L) * std::sqrt(fact[l - m] / fact[l + m]) * s);
+    }
+  }
+  off.assign(N + 1, 0);
+  for (int L = 0; L < N; ++L) off[L + 1] = off[L] + (L + 1) * (L + 1);
+  cmap.assign(2 * off[N], make_int2(0, 0));
+  for (int pi = 0; pi < 2; ++pi) {
+    const int kmax = moments_kmax(pi == 0 ? TCM_FP64 : TCM_MIXED);
+    int2* cm = cmap.data() + pi * off[N];
+    for (int L = 0; L < N; ++L) {
+      const int nch = plan_nch(L, kmax);
+      for (int ch = 0; ch < nch; ++ch) {
+        const int m0 = plan_m0(L, kmax, nch, ch), m1 = plan_m0(L, kmax, nch, ch + 1);
+        for (int m = m0; m < m1; ++m)
+          for (int l = m; l <= L; ++l) {
+            const int slot = chunk_off(L, m0, m) + (m == 0 ? l : 2 * (l - m));
+            if (m == 0) {
+              cm[off[L] + l * l] = make_int2(ch, slot);
+            } else {
+              cm[off[L] + l * l + 2 * m - 1] = make_int2(ch, slot);
+              cm[off[L] + l * l + 2 * m] = make_int2(ch, slot + 1);
+            }
+          }
+      }
+    }
+  }
+}
+
+// Once per device, with that device current: the scratch address and the tables.
+int setup_device(int dev, char** out) {
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (g_scratch_ptr[dev]) {
+    *out = g_scratch_ptr[dev];
+    return TCM_OK;
+  }
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_tcm_noalloc_scratch);
+  if (e != cudaSuccess) return na_err(TCM_ECUDA, "tcm_moments_noalloc: cudaGetSymbolAddress of the scratch failed");
+  char* base = static_cast<char*>(ptr);
+  std::vector<double> ftab;
+  std::vector<int> off;
+  std::vector<int2> cmap;
+  host_tables(ftab, off, cmap);
+  if ((int)off.back() != kNaCompTotal) return na_err(TCM_ECUDA, "tcm_moments_noalloc: internal table size mismatch");
+  if (cudaMemcpy(base + kOffFtab, ftab.data(), ftab.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(base + kOffCmapOff, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(base + kOffCmap, cmap.data(), cmap.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+    return na_err(TCM_ECUDA, "tcm_moments_noalloc: copying the tables into the scratch failed");
+  g_scratch_ptr[dev] = base;
+  *out = base;
+  return TCM_OK;
+}
+
+// Writes one call's descriptors into the scratch and clears the work counters.  The
+// descriptors travel as kernel arguments, so no host staging buffer is involved.
+__global__ void k_noalloc_prepare(char* base, MomJob job, SysGeom geom, GeomJob gjob, int n_gtiles, int nch, int tpc) {
+  MomTile* tiles = reinterpret_cast<MomTile*>(base + kOffTiles);
+  GeomTile* gtiles = reinterpret_cast<GeomTile*>(base + kOffGTiles);
+  int* counters = reinterpret_cast<int*>(base + kOffCounters);
+  if (threadIdx.x == 0) {
+    *reinterpret_cast<MomJob*>(base + kOffJob) = job;
+    *reinterpret_cast<SysGeom*>(base + kOffGeom) = geom;
+    *reinterpret_cast<GeomJob*>(base + kOffGJob) = gjob;
+  }
+  for (int k = threadIdx.x; k < 64; k += blockDim.x) counters[k] = 0;
+  for (int k = threadIdx.x; k < n_gtiles; k += blockDim.x) gtiles[k] = GeomTile{0, k};
+  for (int k = threadIdx.x; k < nch * tpc; k += blockDim.x) tiles[k] = MomTile{0, k / tpc, k % tpc, k};
+}
+
+}  // namespace
+
+extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int lmax, int precision, double* q_out,
+                                   double* geom_out, void* cuda_stream) {
+  if (!s || !q_out) return na_err(TCM_EINVAL, "tcm_moments_noalloc: null argument");
+  if (lmax < 0 || lmax > TCM_LMAX_MAX) return na_err(TCM_EINVAL, "tcm_moments_noalloc: lmax outside [0, 24]");
+  if (precision != TCM_FP64 && precision != TCM_MIXED) return na_err(TCM_EINVAL, "tcm_moments_noalloc: bad precision");
+  if (s->n < 0 || s->n > kNaMaxAtoms)
+    return na_err(TCM_EINVAL, "tcm_moments_noalloc: atom count outside [0, TCM_NOALLOC_MAX_ATOMS = 262144]");
+  if (s->dtype != TCM_F32 && s->dtype != TCM_F64) return na_err(TCM_EINVAL, "tcm_moments_noalloc: bad dtype");
+  if (s->n > 0 && (!s->xyzq || (reinterpret_cast<uintptr_t>(s->xyzq) & 15u)))
+    return na_err(TCM_EINVAL, "tcm_moments_noalloc: coordinates null or not 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(q_out) & 15u) || (geom_out && (reinterpret_cast<uintptr_t>(geom_out) & 7u)))
+    return na_err(TCM_EINVAL, "tcm_moments_noalloc: misaligned output");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return na_err(TCM_ECUDA, "tcm_moments_noalloc: no usable CUDA device");
+  char* base = nullptr;
+  int rc = setup_device(dev, &base);
+  if (rc != TCM_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+  const int kmax = moments_kmax(precision);
+  const int nch = moments_nchunks(precision, lmax);
+  const int tpc = (int)std::max<long long>(1, (s->n + kNaTileAtoms - 1) / kNaTileAtoms);
+  if (nch > kNaMaxChunks || nch * kmax > 800 || tpc > kNaTilesPerChunk)
+    return na_err(TCM_EINVAL, "tcm_moments_noalloc: request exceeds the fixed scratch");
+  MomJob job{};
+  job.xyzq = s->xyzq;
+  job.n = s->n;
+  job.dtype = s->dtype;
+  job.L = lmax;
+  job.geom = 0;
+  job.tiles_per_chunk = tpc;
+  job.atoms_per_tile = (int)((s->n + tpc - 1) / tpc);
+  job.tile_base = 0;
+  for (int k = 0; k < 9; ++k) job.rot[k] = rot ? rot[k] : ((k % 4 == 0) ? 1.0 : 0.0);
+  job.out = q_out;
+  const bool known = s->has_center && s->radius >= 0.0;
+  SysGeom geom{};
+  for (int d = 0; d < 3; ++d) geom.c[d] = s->has_center ? s->center[d] : 0.0;
+  geom.a = s->radius >= 0.0 ? s->radius : 0.0;
+  GeomJob gj{};
+  gj.xyzq = s->xyzq;
+  gj.n = s->n;
+  gj.dtype = s->dtype;
+  gj.geom = 0;
+  gj.need_center = s->has_center ? 0 : 1;
+  gj.need_radius = 1;
+  gj.tile_base = 0;
+  gj.n_tiles = (int)std::max<long long>(1, (s->n + kGeomTileAtoms - 1) / kGeomTileAtoms);
+
+  MomJob* d_job = reinterpret_cast<MomJob*>(base + kOffJob);
+  SysGeom* d_geom = reinterpret_cast<SysGeom*>(base + kOffGeom);
+  k_noalloc_prepare<<<1, 256, 0, st>>>(base, job, geom, gj, known ? 0 : gj.n_tiles, nch, tpc);
+  if (cudaPeekAtLastError() != cudaSuccess) return na_err(TCM_ECUDA, "tcm_moments_noalloc: launch failed");
+  if (!known && launch_geom(reinterpret_cast<GeomJob*>(base + kOffGJob), 1, reinterpret_cast<GeomTile*>(base + kOffGTiles),
+                            gj.n_tiles, reinterpret_cast<double*>(base + kOffGPart), d_geom, st) != 0)
+    return na_err(TCM_ECUDA, "tcm_moments_noalloc: centre/radius launch failed");
+  int num_sms = 0;
+  if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return na_err(TCM_ECUDA, "tcm_moments_noalloc: cudaDeviceGetAttribute failed");
+  const int n_tiles = nch * tpc;
+  if (launch_moments(precision, lmax, d_job, reinterpret_cast<MomTile*>(base + kOffTiles), n_tiles,
+                     reinterpret_cast<int*>(base + kOffCounters), d_geom, reinterpret_cast<double*>(base + kOffPartials),
+                     std::min(n_tiles, 2 * num_sms), st) != 0)
+    return na_err(TCM_ECUDA, "tcm_moments_noalloc: moment launch failed");
+  if (launch_finalize(d_job, 1, reinterpret_cast<double*>(base + kOffPartials), d_geom,
+                      reinterpret_cast<int2*>(base + kOffCmap) + (precision == TCM_FP64 ? 0 : kNaCompTotal),
+                      reinterpret_cast<int*>(base + kOffCmapOff), reinterpret_cast<double*>(base + kOffFtab), kmax, st) != 0)
+    return na_err(TCM_ECUDA, "tcm_moments_noalloc: finalisation launch failed");
+  if (geom_out && cudaMemcpyAsync(geom_out, d_geom, sizeof(SysGeom), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return na_err(TCM_ECUDA, "tcm_moments_noalloc: copy of the centre and radius failed");
+  return TCM_OK;
+}

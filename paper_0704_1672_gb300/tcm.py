@@ -73,10 +73,12 @@ def lib():
                                  ctypes.POINTER(d)]
         L.tcm_energy_batch.argtypes = [P, i32, P, i64, P, i32, P, P]
         L.tcm_direct.argtypes = [P, ctypes.POINTER(tcm_system), ctypes.POINTER(tcm_system), P, P, ctypes.POINTER(d)]
+        L.tcm_moments_noalloc.argtypes = [ctypes.POINTER(tcm_system), P, i32, i32, P, P, P]
         L.tcm_ctx_set_profiling.argtypes = [P, i32]
         L.tcm_ctx_read_profile.argtypes = [P, P, P]
         for name in ("tcm_ctx_create", "tcm_ctx_set_stream", "tcm_prepare", "tcm_moments", "tcm_energy",
-                     "tcm_energy_batch", "tcm_direct", "tcm_ctx_set_profiling", "tcm_ctx_read_profile"):
+                     "tcm_energy_batch", "tcm_direct", "tcm_ctx_set_profiling", "tcm_ctx_read_profile",
+                     "tcm_moments_noalloc"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -237,6 +239,29 @@ class Context:
         E = ctypes.c_double()
         _check(lib().tcm_direct(self._h, ctypes.byref(sa), ctypes.byref(sb), _dptr(r), _dptr(R), ctypes.byref(E)))
         return E.value
+
+
+NOALLOC_MAX_ATOMS = 262144
+
+
+def tcm_moments_noalloc(xyzq, lmax, precision=TCM_MIXED, rot=None, center=None, radius=None, out=None,
+                        center_radius_out=None, stream=None):
+    """The C entry point that allocates no device memory (for callers that cannot allocate).
+
+    ``out`` (device float64, (lmax+1)^2) and ``center_radius_out`` (device float64, 4) should be
+    passed preallocated by such callers; the library call itself allocates nothing and queues
+    its work on ``stream`` (default: the current torch stream).  Calls that overlap on the GPU
+    race on the library's shared scratch, so serialise them.
+    """
+    s = make_system(xyzq, center=center, radius=radius)
+    if out is None:
+        out = torch.empty((lmax + 1) ** 2, dtype=torch.float64, device=xyzq.device)
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    r = None if rot is None else np.ascontiguousarray(rot, dtype=np.float64).reshape(9)
+    g = None if center_radius_out is None else ctypes.c_void_p(center_radius_out.data_ptr())
+    _check(lib().tcm_moments_noalloc(ctypes.byref(s), _dptr(r), int(lmax), int(precision), ctypes.c_void_p(out.data_ptr()),
+                                     g, ctypes.c_void_p(stream.cuda_stream)))
+    return out
 
 
 @dataclass

@@ -1,0 +1,83 @@
+"""tcm_moments_noalloc, the entry point for callers that cannot allocate device memory
+(for example code that must not let cudaMalloc/cudaFree synchronise the device, or an
+application whose own allocator owns all device memory).  It keeps its scratch in a fixed
+array inside the library, so this test checks, through the C ABI, that two calls in a
+row each give what the allocating entry point tcm_moments gives, within the parity
+tolerances, and that a call leaves nothing behind that changes the next one.
+
+The file is named to be collected last."""
+import numpy as np
+import pytest
+import torch
+
+from paper_0704_1672_gb300 import synth
+from tcm_testlib import TOL_FP64, TOL_MIX_MOM, degree_scales, moment_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tcm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0704_1672_gb300 import build
+    build.build()
+    from paper_0704_1672_gb300 import tcm as t
+    torch.cuda.set_device(0)
+    return t
+
+
+def _system(seed, n, radius, shift):
+    rng = np.random.default_rng(seed)
+    S = synth.pack(synth.uniform_ball(rng, n, radius), synth.charges_uniform_net_zero(rng, n))
+    S[:, :3] += shift
+    return S
+
+
+def test_noalloc_matches_tcm_moments_on_two_calls_in_a_row(tcm):
+    rng = np.random.default_rng(23)
+    S1 = _system(1, 9000, 12.0, (4.0, -3.0, 1.0))   # float32 coordinates, mixed, rotated, centre computed
+    S2 = _system(2, 5000, 8.0, (-1.0, 2.0, 0.5))    # float64 coordinates, FP64, centre and radius given
+    rot = synth.random_rotations(rng, 1)[0]
+    c2 = S2[:, :3].mean(0)
+    a2 = float(np.sqrt(((S2[:, :3] - c2) ** 2).sum(1)).max())
+    A1 = torch.tensor(S1, dtype=torch.float32, device="cuda")
+    A2 = torch.tensor(S2, dtype=torch.float64, device="cuda")
+    L1, L2 = 20, 24
+    with tcm.Context(lmax_cap=24) as ctx:
+        ref1 = ctx.tcm_moments(A1, L1, precision=tcm.TCM_MIXED, rot=rot)
+        ref2 = ctx.tcm_moments(A2, L2, precision=tcm.TCM_FP64, center=c2, radius=a2)
+    out1 = torch.empty((L1 + 1) ** 2, dtype=torch.float64, device="cuda")
+    out2 = torch.empty((L2 + 1) ** 2, dtype=torch.float64, device="cuda")
+    geo1 = torch.empty(4, dtype=torch.float64, device="cuda")
+    geo2 = torch.empty(4, dtype=torch.float64, device="cuda")
+    tcm.tcm_moments_noalloc(A1, L1, tcm.TCM_MIXED, rot=rot, out=out1, center_radius_out=geo1)
+    tcm.tcm_moments_noalloc(A2, L2, tcm.TCM_FP64, center=c2, radius=a2, out=out2, center_radius_out=geo2)
+    torch.cuda.synchronize()
+    S1f = S1.astype(np.float32).astype(np.float64)
+    c1 = ref1.center
+    e1 = moment_error(tcm.unpack(out1), tcm.unpack(ref1.q), degree_scales(S1f, c1, L1, rot=rot))
+    e2 = moment_error(tcm.unpack(out2), tcm.unpack(ref2.q), degree_scales(S2, c2, L2))
+    assert e1 < TOL_MIX_MOM, e1
+    assert e2 < TOL_FP64, e2
+    g1 = geo1.cpu().numpy()
+    assert np.allclose(g1[:3], ref1.center, rtol=0, atol=1e-12) and abs(g1[3] - ref1.radius) < 1e-12
+    g2 = geo2.cpu().numpy()
+    assert np.array_equal(g2[:3], c2) and g2[3] == a2
+    # the shared scratch keeps the previous call's contents; a repeat must not depend on them
+    again = torch.empty_like(out1)
+    tcm.tcm_moments_noalloc(A1, L1, tcm.TCM_MIXED, rot=rot, out=again)
+    torch.cuda.synchronize()
+    assert torch.equal(again, out1)
+
+
+def test_noalloc_rejects_requests_beyond_its_scratch(tcm):
+    big = torch.zeros((tcm.NOALLOC_MAX_ATOMS + 1, 4), dtype=torch.float32, device="cuda")
+    out = torch.empty(9, dtype=torch.float64, device="cuda")
+    with pytest.raises(tcm.TcmError) as e:
+        tcm.tcm_moments_noalloc(big, 2, out=out, center=(0, 0, 0), radius=1.0)
+    assert e.value.code == tcm.TCM_EINVAL and "262144" in str(e.value)
+    small = torch.zeros((10, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(tcm.TcmError) as e:
+        tcm.tcm_moments_noalloc(small, 25, out=torch.empty(676, dtype=torch.float64, device="cuda"))
+    assert e.value.code == tcm.TCM_EINVAL
