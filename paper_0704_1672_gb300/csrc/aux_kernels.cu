@@ -184,32 +184,93 @@ __global__ void __launch_bounds__(256) k_finalize(const MomJob* __restrict__ job
   }
 }
 
-// a4 + a5: one CTA per energy.
-//   Qhat_lm = Q_lm / sqrt((l+m)! (l-m)!)                    (m >= 0, complex)
-//   J_LM    = (-1)^M (L-M)! P_L^M(cos t) e^{-i M p} / R^{L+1}  (L <= 2 Lmax, M >= 0)
-//           = sqrt((L+M)!(L-M)!) sqrt(4pi/(2L+1)) Y*_LM(R0hat) / R^{L+1}
-// With the stretched 3j symbol (L = l1 + l2) Eq. (Formula) becomes
+// a4 + a5: one CTA per energy, in the frame where R0hat is the z axis.
+//
+// With the stretched 3j symbol (L = l1 + l2) Eq. (Formula) reads
 //   U = sum (-1)^l2 Qhat^A_l1m1 Qhat^B_l2m2 J_{l1+l2, m1+m2},
-// and for real charges Qhat_l,-m = (-1)^m conj(Qhat_lm), J_L,-M = (-1)^M conj(J_LM),
-// so U = sum_{l1, m1>=0} w_m1 Re(Qhat^A_l1m1 V_l1m1) with w = 1 (m1 = 0) or 2.
-// J is built by the recurrences
-//   J_00 = 1/R,  J_k+1,k+1 = -(2k+1) (x - iy)/R^2 J_kk,
-//   J_M+1,M = (2M+1) z J_MM / R^2,
-//   J_L+1,M = ((2L+1) z J_LM - (L^2 - M^2) J_L-1,M) / R^2.
+//   Qhat_lm = Q_lm / sqrt((l+m)!(l-m)!),  J_LM = sqrt((L+M)!(L-M)!) sqrt(4pi/(2L+1)) Y*_LM(R0hat) / R^{L+1}.
+// U does not change when A, B and R0 rotate together.  In the frame W = R_y(-beta) R_z(-alpha)
+// that takes R0hat = (sin b cos a, sin b sin a, cos b) to z, J_LM = delta_M0 L! / R^{L+1}, so
+//   U = sum_{l1,l2} (-1)^l2 (l1+l2)! / R^{l1+l2+1}
+//         [Qhat'^A_l1,0 Qhat'^B_l2,0 + 2 sum_{m>=1} (-1)^m Re(Qhat'^A_l1m conj(Qhat'^B_l2m))]
+// (real charges: Q_l,-m = (-1)^m conj(Q_lm)).  Moments enter in the rotated frame: those of B
+// either come from the moment kernels with W folded into the atom transform (item flag
+// b_in_frame) or, like those of A, are rotated here:
+//   Q'_lm = sum_m' e^{-i m' alpha} d^l_{m'm}(beta) Q_lm'
+// with the Wigner d^l_{ab}, a >= |b|, from the three-term recursion in l started at
+//   d^a_{ab} = (-1)^{a-b} sqrt(C(2a, a+b)) cos^{a+b}(beta/2) sin^{a-b}(beta/2),
+// the other entries by d_{m'm} = (-1)^{m-m'} d_{mm'} = d_{-m,-m'}.  O(L^3) work per energy.
 constexpr int kContractThreads = 256;
+
+// Offsets of the per-(l, a) tables in ztab (doubles), each [kLmaxMax+1][kLmaxMax+1].
+constexpr int kZN = kLmaxMax + 1;
+constexpr int kZ_K1 = 0;                 // l(2l-1) / sqrt(l^2 - a^2)        (a < l)
+constexpr int kZ_IRS = kZ_K1 + kZN * kZN;  // 1 / sqrt(l^2 - b^2)              (b < l)
+constexpr int kZ_K2 = kZ_IRS + kZN * kZN;  // sqrt((l-1)^2 - a^2) / ((l-1)(2l-1)) (l >= 2)
+constexpr int kZ_RS1 = kZ_K2 + kZN * kZN;  // sqrt((l-1)^2 - b^2)              (l >= 1)
+constexpr int kZ_ILL = kZ_RS1 + kZN * kZN; // 1 / (l (l-1))                    (l >= 2)
+constexpr int kZ_SQC = kZ_ILL + kZN;       // sqrt(C(2a, a+b)), [kZN][2 kZN]
+constexpr int kZ_FACT = kZ_SQC + kZN * 2 * kZN;  // k!, k <= 2 kLmaxMax
+constexpr int kZ_ISF = kZ_FACT + 2 * kZN;  // 1 / sqrt((l+m)! (l-m)!)
+constexpr int kZ_TOTAL = kZ_ISF + kZN * kZN;
+
+__device__ __forceinline__ double flip(double x, int odd) {  // (-1)^odd x without an FP64 op
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)(odd & 1) << 63));
+}
+
+__device__ __forceinline__ int tri_l(int k) {  // l with l(l+1)/2 <= k < (l+1)(l+2)/2
+  int l = (int)((sqrtf(8.0f * k + 1.0f) - 1.0f) * 0.5f);
+  while (l * (l + 1) / 2 > k) --l;
+  while ((l + 1) * (l + 2) / 2 <= k) ++l;
+  return l;
+}
+
+// d^l_{m'm} for m >= 0 from the half table D (entries a >= |b|, D[off(l) + a*a + a + b]).
+__device__ __forceinline__ double dget(const double* D, int offl, int mp, int m) {
+  if (mp <= m && -mp <= m) return flip(D[offl + m * m + m + mp], m - mp);
+  if (mp > m) return D[offl + mp * mp + mp + m];
+  return flip(D[offl + mp * mp - mp - m], m - mp);  // a = -mp, b = -m
+}
+
+// Rotate the packed moments p (m >= 0, complex in qin) into the frame: writes qout, normalised
+// to Qhat.  Threads stride over (l, m).
+__device__ void rotate_into_frame(const double2* qin, double2* qout, const double* D, const double2* ph, int L,
+                                  const double* ztab) {
+  const int nq = (L + 1) * (L + 2) / 2;
+  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+    const int l = tri_l(k);
+    const int m = k - l * (l + 1) / 2;
+    const int offl = l * (l + 1) * (2 * l + 1) / 6;
+    const double2* q = qin + l * (l + 1) / 2;
+    double re = dget(D, offl, 0, m) * q[0].x;
+    double im = 0.0;
+    for (int mp = 1; mp <= l; ++mp) {
+      // P = e^{-i mp alpha} Q_l,mp
+      const double2 e = ph[mp];
+      const double px = e.x * q[mp].x - e.y * q[mp].y;
+      const double py = e.x * q[mp].y + e.y * q[mp].x;
+      const double d1 = dget(D, offl, mp, m);
+      const double d2 = flip(dget(D, offl, -mp, m), mp);
+      re = fma(d1 + d2, px, re);
+      im = fma(d1 - d2, py, im);
+    }
+    const double f = ztab[kZ_ISF + l * kZN + m];
+    qout[k] = make_double2(re * f, im * f);
+  }
+}
 
 __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* __restrict__ items,
                                                                const MomJob* __restrict__ jobs,
                                                                const SysGeom* __restrict__ geoms,
-                                                               const double* __restrict__ isf,
+                                                               const double* __restrict__ ztab,
                                                                double* __restrict__ E, int32_t* __restrict__ status) {
   extern __shared__ double2 sm2[];
   __shared__ double sh[32];
+  __shared__ double g_cb, g_ch, g_sh, g_iR;
   const PairDesc d = items[blockIdx.x];
   const int L = d.L;
   const double x = d.R0[0], y = d.R0[1], z = d.R0[2];
-  const double R2 = x * x + y * y + z * z;
-  const double R = sqrt(R2);
+  const double R = sqrt(x * x + y * y + z * z);
   const double aA = geoms[d.geomA].a, aB = geoms[d.geomB].a;
   if (!(R > aA + aB)) {  // Eq. (mainCond) violated: the expansion does not converge
     if (threadIdx.x == 0) {
@@ -219,96 +280,116 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     return;
   }
   const int nq = (L + 1) * (L + 2) / 2;
-  const int LL = 2 * L;
-  double2* qa = sm2;
-  double2* qb = sm2 + nq;
-  double2* J = sm2 + 2 * nq;
+  const int nd = (L + 1) * (L + 2) * (2 * L + 3) / 6;  // sum of (l+1)^2
+  double2* qa = sm2;           // lab frame, then reused
+  double2* qb = qa + nq;
+  double2* ra = qb + nq;       // Qhat' of A
+  double2* rb = ra + nq;       // Qhat' of B
+  double2* ph = rb + nq;       // e^{-i m alpha}, m <= L
+  double* cp = reinterpret_cast<double*>(ph + (L + 1));  // cos^k(beta/2), k <= 2L
+  double* sp = cp + 2 * L + 1;                             // sin^k(beta/2)
+  double* rp = sp + 2 * L + 1;                             // R^-(k+1), k <= 2L
+  double* D = rp + 2 * L + 1;                              // half Wigner table, nd entries
   const double* pa = jobs[d.jobA].out;
   const double* pb = jobs[d.jobB].out;
-  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
-    int l = (int)((sqrt(8.0 * k + 1.0) - 1.0) * 0.5);
-    while (l * (l + 1) / 2 > k) --l;
-    while ((l + 1) * (l + 2) / 2 <= k) ++l;
-    const int m = k - l * (l + 1) / 2;
-    const double f = isf[l * (kLmaxMax + 1) + m];
-    if (m == 0) {
-      qa[k] = make_double2(pa[l * l] * f, 0.0);
-      qb[k] = make_double2(pb[l * l] * f, 0.0);
+  const bool b_in_frame = d.b_in_frame != 0;
+  // geometry of the frame; half angles without cancellation
+  if (threadIdx.x == 0) {
+    const double rho2 = x * x + y * y;
+    double opc, omc;  // 1 + cos b, 1 - cos b
+    if (z >= 0.0) {
+      opc = (R + z) / R;
+      omc = rho2 / (R * (R + z));
     } else {
-      qa[k] = make_double2(pa[l * l + 2 * m - 1] * f, pa[l * l + 2 * m] * f);
-      qb[k] = make_double2(pb[l * l + 2 * m - 1] * f, pb[l * l + 2 * m] * f);
+      omc = (R - z) / R;
+      opc = rho2 / (R * (R - z));
     }
+    g_cb = z / R;
+    g_ch = sqrt(0.5 * opc);
+    g_sh = sqrt(0.5 * omc);
+    g_iR = 1.0 / R;
   }
-  const double iR2 = 1.0 / R2;
-  for (int M = threadIdx.x; M <= LL; M += blockDim.x) {
-    double jr = 1.0 / R, ji = 0.0;
-    const double wr = x * iR2, wi = -y * iR2;  // (x - iy) / R^2
-    for (int k = 0; k < M; ++k) {
-      const double f = -(2.0 * k + 1.0);
-      const double nr = f * (jr * wr - ji * wi);
-      const double ni = f * (jr * wi + ji * wr);
-      jr = nr;
-      ji = ni;
+  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+    const int l = tri_l(k);
+    const int m = k - l * (l + 1) / 2;
+    qa[k] = m == 0 ? make_double2(pa[l * l], 0.0) : make_double2(pa[l * l + 2 * m - 1], pa[l * l + 2 * m]);
+    qb[k] = m == 0 ? make_double2(pb[l * l], 0.0) : make_double2(pb[l * l + 2 * m - 1], pb[l * l + 2 * m]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 32) {  // e^{-i m alpha}
+    const double rho = sqrt(x * x + y * y);
+    const double ca = rho > 0.0 ? x / rho : 1.0, sa = rho > 0.0 ? y / rho : 0.0;
+    double er = 1.0, ei = 0.0;
+    for (int m = 0; m <= L; ++m) {
+      ph[m] = make_double2(er, ei);
+      const double nr = er * ca + ei * sa;
+      ei = ei * ca - er * sa;
+      er = nr;
     }
-    J[M * (M + 1) / 2 + M] = make_double2(jr, ji);
-    if (M + 1 <= LL) {
-      double pr = jr, pi = ji;
-      const double f = (2.0 * M + 1.0) * z * iR2;
-      double cr = f * jr, ci = f * ji;
-      J[(M + 1) * (M + 2) / 2 + M] = make_double2(cr, ci);
-      for (int Lp = M + 1; Lp < LL; ++Lp) {
-        const double a1 = (2.0 * Lp + 1.0) * z * iR2;
-        const double a2 = (double)(Lp * Lp - M * M) * iR2;
-        const double nr = a1 * cr - a2 * pr;
-        const double ni = a1 * ci - a2 * pi;
-        pr = cr;
-        pi = ci;
-        cr = nr;
-        ci = ni;
-        J[(Lp + 1) * (Lp + 2) / 2 + M] = make_double2(cr, ci);
-      }
+  } else if (threadIdx.x == 64) {
+    double c = 1.0, s = 1.0;
+    for (int k = 0; k <= 2 * L; ++k) {
+      cp[k] = c;
+      sp[k] = s;
+      c *= g_ch;
+      s *= g_sh;
+    }
+  } else if (threadIdx.x == 96) {
+    double r = g_iR;
+    for (int k = 0; k <= 2 * L; ++k) {
+      rp[k] = r;
+      r *= g_iR;
     }
   }
   __syncthreads();
-  // Work items (l1, m1 >= 0, l2): T = sum_m2 Qhat^B_l2m2 J_{l1+l2, m1+m2}.
-  const int nwork = nq * (L + 1);
-  double acc = 0.0;
-  for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
-    const int k1 = w / (L + 1);
-    const int l2 = w - k1 * (L + 1);
-    int l1 = (int)((sqrt(8.0 * k1 + 1.0) - 1.0) * 0.5);
-    while (l1 * (l1 + 1) / 2 > k1) --l1;
-    while ((l1 + 1) * (l1 + 2) / 2 <= k1) ++l1;
-    const int m1 = k1 - l1 * (l1 + 1) / 2;
-    const int Lp = l1 + l2;
-    const double2* Jr = J + Lp * (Lp + 1) / 2;
-    const double2* qr = qb + l2 * (l2 + 1) / 2;
-    double2 b = qr[0];
-    double2 j = Jr[m1];
-    double tr = b.x * j.x - b.y * j.y;
-    double ti = b.x * j.y + b.y * j.x;
-    for (int m2 = 1; m2 <= l2; ++m2) {
-      b = qr[m2];
-      j = Jr[m1 + m2];  // + m2
-      tr += b.x * j.x - b.y * j.y;
-      ti += b.x * j.y + b.y * j.x;
-      // - m2: Qhat^B_l2,-m2 = (-1)^m2 conj(b)
-      if (m2 <= m1) {  // J_{L, m1-m2}, non-negative order
-        j = Jr[m1 - m2];
-        const double s = (m2 & 1) ? -1.0 : 1.0;
-        tr += s * (b.x * j.x + b.y * j.y);
-        ti += s * (b.x * j.y - b.y * j.x);
-      } else {  // J_{L, m1-m2} = (-1)^(m2-m1) conj(J_{L, m2-m1}); total sign (-1)^m1 conj(b j)
-        j = Jr[m2 - m1];
-        const double s = (m1 & 1) ? -1.0 : 1.0;
-        tr += s * (b.x * j.x - b.y * j.y);
-        ti -= s * (b.x * j.y + b.y * j.x);
-      }
+  // Wigner d^l_{ab}, a >= |b|: one thread per (a, b) walks l upward.
+  const double cb = g_cb;
+  for (int p = threadIdx.x; p < (L + 1) * (L + 1); p += blockDim.x) {
+    int a = (int)sqrtf((float)p);
+    while (a * a > p) --a;
+    while ((a + 1) * (a + 1) <= p) ++a;
+    const int b = p - a * a - a;
+    const int ab = b < 0 ? -b : b;
+    double d1 = flip(ztab[kZ_SQC + a * 2 * kZN + a + b] * cp[a + b] * sp[a - b], a - b);
+    double d2 = 0.0;
+    D[a * (a + 1) * (2 * a + 1) / 6 + a * a + a + b] = d1;
+    const double abd = (double)(a * b);
+    for (int l = a + 1; l <= L; ++l) {
+      const double A = ztab[kZ_K1 + l * kZN + a] * ztab[kZ_IRS + l * kZN + ab];
+      const double t = fma(-abd, ztab[kZ_ILL + l], cb);
+      double v = t * d1;
+      if (l - 2 >= a) v = fma(-ztab[kZ_K2 + l * kZN + a] * ztab[kZ_RS1 + l * kZN + ab], d2, v);
+      v *= A;
+      D[l * (l + 1) * (2 * l + 1) / 6 + a * a + a + b] = v;
+      d2 = d1;
+      d1 = v;
     }
-    const double2 a = qa[k1];
-    const double re = a.x * tr - a.y * ti;
-    const double wgt = (m1 > 0 ? 2.0 : 1.0) * ((l2 & 1) ? -1.0 : 1.0);
-    acc += wgt * re;
+  }
+  __syncthreads();
+  rotate_into_frame(qa, ra, D, ph, L, ztab);
+  if (!b_in_frame) {
+    rotate_into_frame(qb, rb, D, ph, L, ztab);
+  } else {
+    for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+      const int l = tri_l(k);
+      const int m = k - l * (l + 1) / 2;
+      const double f = ztab[kZ_ISF + l * kZN + m];
+      rb[k] = make_double2(qb[k].x * f, qb[k].y * f);
+    }
+  }
+  __syncthreads();
+  // z-axis contraction: one thread per (l1, l2)
+  double acc = 0.0;
+  for (int p = threadIdx.x; p < (L + 1) * (L + 1); p += blockDim.x) {
+    const int l1 = p / (L + 1);
+    const int l2 = p - l1 * (L + 1);
+    const double2* a = ra + l1 * (l1 + 1) / 2;
+    const double2* b = rb + l2 * (l2 + 1) / 2;
+    const int mm = l1 < l2 ? l1 : l2;
+    double s = 0.0;
+    for (int m = 1; m <= mm; ++m) s += flip(fma(a[m].x, b[m].x, a[m].y * b[m].y), m);
+    s = fma(2.0, s, a[0].x * b[0].x);
+    acc = fma(flip(ztab[kZ_FACT + l1 + l2] * rp[l1 + l2], l2), s, acc);
   }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) {
@@ -383,6 +464,12 @@ __global__ void k_direct_final(const double* __restrict__ part, int nblk, double
 
 }  // namespace
 
+int contract_smem_bytes(int L) {
+  const int nq = (L + 1) * (L + 2) / 2;
+  const int nd = (L + 1) * (L + 2) * (2 * L + 3) / 6;
+  return (4 * nq + (L + 1)) * (int)sizeof(double2) + (3 * (2 * L + 1) + nd) * (int)sizeof(double);
+}
+
 int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n_gtiles, double* gpart,
                 SysGeom* geoms, cudaStream_t s) {
   if (n_gjobs <= 0) return 0;
@@ -402,16 +489,41 @@ int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, cons
 }
 
 int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const MomJob* jobs, const SysGeom* geoms,
-                    const double* isf, double* E, int32_t* status, cudaStream_t s) {
+                    const double* ztab, double* E, int32_t* status, cudaStream_t s) {
   if (n_items <= 0) return 0;
-  const int nq = (Lmax_items + 1) * (Lmax_items + 2) / 2;
-  const int nj = (2 * Lmax_items + 1) * (2 * Lmax_items + 2) / 2;
-  const int smem = (2 * nq + nj) * (int)sizeof(double2);
+  const int smem = contract_smem_bytes(Lmax_items);
   if (smem > 48 * 1024) {
     if (cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return -1;
   }
-  k_contract<<<n_items, kContractThreads, smem, s>>>(items, jobs, geoms, isf, E, status);
+  k_contract<<<n_items, kContractThreads, smem, s>>>(items, jobs, geoms, ztab, E, status);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+int contract_table_size() { return kZ_TOTAL; }
+
+void contract_tables(double* t) {
+  for (int k = 0; k < kZ_TOTAL; ++k) t[k] = 0.0;
+  long double fact[2 * kZN + 2];
+  fact[0] = 1.0L;
+  for (int k = 1; k < 2 * kZN + 2; ++k) fact[k] = fact[k - 1] * (long double)k;
+  for (int l = 0; l < kZN; ++l) {
+    for (int a = 0; a <= l; ++a) {
+      if (a < l) {
+        const long double r = sqrtl((long double)(l * l - a * a));
+        t[kZ_K1 + l * kZN + a] = (double)((long double)(l * (2 * l - 1)) / r);
+        t[kZ_IRS + l * kZN + a] = (double)(1.0L / r);
+      }
+      if (l >= 1 && a <= l - 1) t[kZ_RS1 + l * kZN + a] = (double)sqrtl((long double)((l - 1) * (l - 1) - a * a));
+      if (l >= 2 && a <= l - 1)
+        t[kZ_K2 + l * kZN + a] = (double)(sqrtl((long double)((l - 1) * (l - 1) - a * a)) /
+                                          (long double)((l - 1) * (2 * l - 1)));
+      t[kZ_ISF + l * kZN + a] = (double)(1.0L / sqrtl(fact[l + a] * fact[l - a]));
+    }
+    if (l >= 2) t[kZ_ILL + l] = (double)(1.0L / (long double)(l * (l - 1)));
+    for (int b = -l; b <= l; ++b)
+      t[kZ_SQC + l * 2 * kZN + l + b] = (double)sqrtl(fact[2 * l] / (fact[l + b] * fact[l - b]));
+  }
+  for (int k = 0; k < 2 * kZN; ++k) t[kZ_FACT + k] = (double)fact[k];
 }
 
 int direct_blocks(long long na) { return (int)((na + kDirectThreads - 1) / kDirectThreads); }

@@ -86,7 +86,7 @@ struct tcm_ctx {
   cudaStream_t stream = nullptr;
   // tables
   double* d_ftab = nullptr;  // F_lm, [kLmaxMax+1][kLmaxMax+1]
-  double* d_isf = nullptr;   // 1/sqrt((l+m)!(l-m)!)
+  double* d_ztab = nullptr;  // contraction tables (Wigner-d recursion, factorials, 1/sqrt((l+m)!(l-m)!))
   int2* d_cmap[2] = {nullptr, nullptr};
   int* d_cmap_off = nullptr;
   // scratch
@@ -327,7 +327,7 @@ int build_tables(tcm_ctx* c) {
   std::vector<long double> fact(2 * N + 2);
   fact[0] = 1.0L;
   for (size_t k = 1; k < fact.size(); ++k) fact[k] = fact[k - 1] * (long double)k;
-  std::vector<double> ftab(N * N, 0.0), isf(N * N, 0.0);
+  std::vector<double> ftab(N * N, 0.0);
   for (int m = 0; m < N; ++m) {
     // s_lm: normalisation of the kernel's G_lm (see tcm_internal.h)
     long double s_prev = 0.0L, s = 1.0L;
@@ -343,7 +343,6 @@ int build_tables(tcm_ctx* c) {
       }
       const long double sgn = (m & 1) ? -1.0L : 1.0L;
       ftab[l * N + m] = (double)(sgn * std::sqrt(fact[l - m] / fact[l + m]) * s);
-      isf[l * N + m] = (double)(1.0L / std::sqrt(fact[l + m] * fact[l - m]));
     }
   }
   std::vector<int> off(N + 1, 0);
@@ -375,11 +374,13 @@ int build_tables(tcm_ctx* c) {
       if (e.x < 0 || e.y < 0 || e.y >= moments_kmax(pi == 0 ? TCM_FP64 : TCM_MIXED))
         return set_err(TCM_ECUDA, "internal error: incomplete moment component map");
   TRY_CUDA(cudaMalloc(&c->d_ftab, ftab.size() * sizeof(double)));
-  TRY_CUDA(cudaMalloc(&c->d_isf, isf.size() * sizeof(double)));
+  std::vector<double> zt(contract_table_size());
+  contract_tables(zt.data());
+  TRY_CUDA(cudaMalloc(&c->d_ztab, zt.size() * sizeof(double)));
   TRY_CUDA(cudaMalloc(&c->d_cmap_off, off.size() * sizeof(int)));
   for (int pi = 0; pi < 2; ++pi) TRY_CUDA(cudaMalloc(&c->d_cmap[pi], cmap[pi].size() * sizeof(int2)));
   TRY_CUDA(cudaMemcpy(c->d_ftab, ftab.data(), ftab.size() * sizeof(double), cudaMemcpyHostToDevice));
-  TRY_CUDA(cudaMemcpy(c->d_isf, isf.data(), isf.size() * sizeof(double), cudaMemcpyHostToDevice));
+  TRY_CUDA(cudaMemcpy(c->d_ztab, zt.data(), zt.size() * sizeof(double), cudaMemcpyHostToDevice));
   TRY_CUDA(cudaMemcpy(c->d_cmap_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
   for (int pi = 0; pi < 2; ++pi)
     TRY_CUDA(cudaMemcpy(c->d_cmap[pi], cmap[pi].data(), cmap[pi].size() * sizeof(int2), cudaMemcpyHostToDevice));
@@ -390,7 +391,7 @@ void free_ctx(tcm_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   cudaFree(c->d_ftab);
-  cudaFree(c->d_isf);
+  cudaFree(c->d_ztab);
   cudaFree(c->d_cmap_off);
   for (auto* p : c->d_cmap) cudaFree(p);
   for (DevBuf* b : {&c->desc, &c->partials, &c->gpart, &c->counters, &c->moms, &c->escr, &c->dpart}) cudaFree(b->p);
@@ -611,7 +612,7 @@ int tcm_energy(tcm_ctx_t c, const tcm_moments_t* A, const tcm_moments_t* B, cons
     PhaseScope ps(c, TCM_PHASE_CONTRACT, 1);
     TRY_LAUNCH(launch_contract(reinterpret_cast<PairDesc*>(base + o_it), 1, lmax,
                                reinterpret_cast<MomJob*>(base + o_job), reinterpret_cast<SysGeom*>(base + o_geo),
-                               c->d_isf, dE, nullptr, c->stream));
+                               c->d_ztab, dE, nullptr, c->stream));
   }
   TRY_CUDA(cudaMemcpyAsync(c->pinned_small, dE, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   TRY_CUDA(cudaStreamSynchronize(c->stream));
@@ -681,8 +682,20 @@ int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int6
   for (int64_t k = 0; k < n_items; ++k) {
     const tcm_pair_item& it = items[k];
     const int ja = get_job(it.a, it.lmax, -1, nullptr);
-    const int jb = it.has_rot ? get_job(it.b, it.lmax, (int)k, it.rotB) : get_job(it.b, it.lmax, -1, nullptr);
-    pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, 0, {it.R0[0], it.R0[1], it.R0[2]}};
+    int jb;
+    if (it.has_rot) {
+      // B is moved per item anyway: fold the rotation W that takes R0hat to z into its
+      // atom transform, so the contraction receives B's moments already in that frame.
+      double W[9], M[9];
+      frame_rotation(it.R0, W);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          M[3 * i + j] = W[3 * i + 0] * it.rotB[0 + j] + W[3 * i + 1] * it.rotB[3 + j] + W[3 * i + 2] * it.rotB[6 + j];
+      jb = get_job(it.b, it.lmax, (int)k, M);
+    } else {
+      jb = get_job(it.b, it.lmax, -1, nullptr);
+    }
+    pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, it.has_rot ? 1 : 0, {it.R0[0], it.R0[1], it.R0[2]}};
   }
   P.n_tile_ids = next_id;
   TRY(dev_ensure(c, c->moms, std::max<size_t>(moff, 1) * sizeof(double)));
@@ -713,7 +726,7 @@ int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int6
   {
     PhaseScope ps(c, TCM_PHASE_CONTRACT, 1);
     TRY_LAUNCH(launch_contract(reinterpret_cast<PairDesc*>(base + o_it), (int)n_items, Lmax_items, d_jobs, d_geo,
-                               c->d_isf, E, status, c->stream));
+                               c->d_ztab, E, status, c->stream));
   }
   return TCM_OK;
 }

@@ -131,7 +131,7 @@ struct PairDesc {  // one energy: moments of jobA and jobB at lmax L, separation
   int jobA, jobB;
   int geomA, geomB;
   int L;
-  int pad;
+  int b_in_frame;  // nonzero: jobB's moments are already in the frame where R0hat = z
   double R0[3];
 };
 
@@ -153,7 +153,22 @@ int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms,
                     const int2* cmap, const int* cmap_off, const double* ftab, int kmax, cudaStream_t s);
 int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const MomJob* jobs,
-                    const SysGeom* geoms, const double* isf, double* E, int32_t* status, cudaStream_t s);
+                    const SysGeom* geoms, const double* ztab, double* E, int32_t* status, cudaStream_t s);
+int contract_smem_bytes(int L);
+int contract_table_size();
+void contract_tables(double* t);  // host: fills contract_table_size() doubles
+
+// Rotation W = R_y(-beta) R_z(-alpha) taking R0hat to the z axis (row-major).
+__host__ __device__ inline void frame_rotation(const double* R0, double* W) {
+  const double x = R0[0], y = R0[1], z = R0[2];
+  const double R = sqrt(x * x + y * y + z * z);
+  const double rho = sqrt(x * x + y * y);
+  const double cb = z / R, sb = rho / R;
+  const double ca = rho > 0.0 ? x / rho : 1.0, sa = rho > 0.0 ? y / rho : 0.0;
+  W[0] = cb * ca; W[1] = cb * sa; W[2] = -sb;
+  W[3] = -sa;     W[4] = ca;      W[5] = 0.0;
+  W[6] = sb * ca; W[7] = sb * sa; W[8] = cb;
+}
 int launch_direct(const void* a, long long na, int dta, const void* b, long long nb, int dtb,
                   const SysGeom* geo /* device: [A, B] centres */, const double* xf /* device: rot[9], R0[3] */,
                   double* part, int nblk, double* E, cudaStream_t s);
