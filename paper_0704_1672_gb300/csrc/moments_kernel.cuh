@@ -139,25 +139,35 @@ __device__ __forceinline__ Xform<T> make_xform(const MomJob& job, const SysGeom&
   return x;
 }
 
-// Load atom i and produce (u_x, u_y, c, rho, q) in the scaled, rotated frame.
+// Centred coordinates of one atom record.  The input type is a template parameter so that
+// the atom loop never carries the other type's instructions (a runtime test inside the
+// loop is if-converted, and the idle double path still occupies the FP64 pipe).
 template <typename T>
-__device__ __forceinline__ void load_setup(const void* xyzq, int dtype, long long i, const Xform<T>& xf,
-                                           const double* cd, T& ux, T& uy, T& cz, T& rho, T& q) {
-  T d0, d1, d2;
-  if (dtype == TCM_F32) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(xyzq) + i);
-    d0 = ((T)v.x - xf.chi[0]) - xf.clo[0];
-    d1 = ((T)v.y - xf.chi[1]) - xf.clo[1];
-    d2 = ((T)v.z - xf.chi[2]) - xf.clo[2];
-    q = (T)v.w;
-  } else {
-    const double2 v0 = __ldg(reinterpret_cast<const double2*>(xyzq) + 2 * i);
-    const double2 v1 = __ldg(reinterpret_cast<const double2*>(xyzq) + 2 * i + 1);
-    d0 = (T)(v0.x - cd[0]);
-    d1 = (T)(v0.y - cd[1]);
-    d2 = (T)(v1.x - cd[2]);
-    q = (T)v1.y;
-  }
+__device__ __forceinline__ void centre(const float4& v, const Xform<T>& xf, const double*, T& d0, T& d1, T& d2, T& q) {
+  d0 = ((T)v.x - xf.chi[0]) - xf.clo[0];
+  d1 = ((T)v.y - xf.chi[1]) - xf.clo[1];
+  d2 = ((T)v.z - xf.chi[2]) - xf.clo[2];
+  q = (T)v.w;
+}
+struct Rec64 {
+  double2 a, b;
+};
+template <typename T>
+__device__ __forceinline__ void centre(const Rec64& v, const Xform<T>&, const double* cd, T& d0, T& d1, T& d2, T& q) {
+  d0 = (T)(v.a.x - cd[0]);
+  d1 = (T)(v.a.y - cd[1]);
+  d2 = (T)(v.b.x - cd[2]);
+  q = (T)v.b.y;
+}
+__device__ __forceinline__ float4 load_rec(const float4* p, long long i) { return __ldg(p + i); }
+__device__ __forceinline__ Rec64 load_rec(const Rec64* p, long long i) {
+  const double2* q = reinterpret_cast<const double2*>(p + i);
+  return Rec64{__ldg(q), __ldg(q + 1)};
+}
+
+// (u_x, u_y, c, rho) of the centred atom in the scaled, rotated frame.
+template <typename T>
+__device__ __forceinline__ void setup(T d0, T d1, T d2, const Xform<T>& xf, T& ux, T& uy, T& cz, T& rho) {
   const T px = fmaT(xf.M[0], d0, fmaT(xf.M[1], d1, xf.M[2] * d2));
   const T py = fmaT(xf.M[3], d0, fmaT(xf.M[4], d1, xf.M[5] * d2));
   const T pz = fmaT(xf.M[6], d0, fmaT(xf.M[7], d1, xf.M[8] * d2));
@@ -232,25 +242,20 @@ __device__ __forceinline__ void cta_reduce_store(const T (&acc)[NACC], unsigned 
   __syncthreads();
 }
 
-template <typename T, int L, int M0, int M1>
-__device__ __forceinline__ void run_chunk(const MomTile& tile, const MomJob* __restrict__ jobs,
-                                          const SysGeom* __restrict__ geoms, double* __restrict__ partials,
-                                          unsigned char* smem) {
-  using R = Regs<T, L, M0, M1>;
-  const MomJob& job = jobs[tile.job];
-  const SysGeom g = geoms[job.geom];
-  const Xform<T> xf = make_xform<T>(job, g);
-  const long long n = job.n;
-  const long long i0 = (long long)tile.t * job.atoms_per_tile;
-  const long long i1 = min(n, i0 + (long long)job.atoms_per_tile);
-  const void* xyzq = job.xyzq;
-  const int dtype = job.dtype;
-  R s;
-#pragma unroll
-  for (int k = 0; k < R::NACC; ++k) s.acc[k] = (T)0;
-  for (long long i = i0 + threadIdx.x; i < i1; i += kThreads) {
-    T ux, uy, cz, rho, q;
-    load_setup<T>(xyzq, dtype, i, xf, g.c, ux, uy, cz, rho, q);
+// Walks this thread's atoms of [i0, i1), the next record prefetched while the current
+// one is processed.
+template <typename T, int L, int M0, int M1, typename Rec>
+__device__ __forceinline__ void atom_loop(Regs<T, L, M0, M1>& s, const Rec* __restrict__ xyzq, long long i0,
+                                          long long i1, const Xform<T>& xf, const double* cd) {
+  long long i = i0 + threadIdx.x;
+  if (i >= i1) return;
+  Rec nxt = load_rec(xyzq, i);
+  for (; i < i1; i += kThreads) {
+    const Rec cur = nxt;
+    if (i + kThreads < i1) nxt = load_rec(xyzq, i + kThreads);
+    T d0, d1, d2, q, ux, uy, cz, rho;
+    centre<T>(cur, xf, cd, d0, d1, d2, q);
+    setup<T>(d0, d1, d2, xf, ux, uy, cz, rho);
     if constexpr (M0 == 0) {
       s.dr = (T)1;
       s.di = (T)0;
@@ -267,28 +272,53 @@ __device__ __forceinline__ void run_chunk(const MomTile& tile, const MomJob* __r
     }
     levels<T, L, M0, M1, 0>(s, ux, uy, cz, rho, q);
   }
+}
+
+template <typename T, int L, int M0, int M1>
+__device__ __forceinline__ void run_chunk(const MomTile& tile, const MomJob* __restrict__ jobs,
+                                          const SysGeom* __restrict__ geoms, double* __restrict__ partials,
+                                          unsigned char* smem, Xform<T>* xf_sh) {
+  using R = Regs<T, L, M0, M1>;
+  const MomJob& job = jobs[tile.job];
+  const SysGeom g = geoms[job.geom];
+  if (threadIdx.x == 0) *xf_sh = make_xform<T>(job, g);  // double math once per tile, not per thread
+  __syncthreads();
+  const Xform<T> xf = *xf_sh;
+  const long long n = job.n;
+  const long long i0 = (long long)tile.t * job.atoms_per_tile;
+  const long long i1 = min(n, i0 + (long long)job.atoms_per_tile);
+  const void* xyzq = job.xyzq;
+  const int dtype = job.dtype;
+  R s;
+#pragma unroll
+  for (int k = 0; k < R::NACC; ++k) s.acc[k] = (T)0;
+  if (dtype == TCM_F32)
+    atom_loop<T, L, M0, M1>(s, reinterpret_cast<const float4*>(xyzq), i0, i1, xf, g.c);
+  else
+    atom_loop<T, L, M0, M1>(s, reinterpret_cast<const Rec64*>(xyzq), i0, i1, xf, g.c);
   cta_reduce_store<T, R::NACC>(s.acc, smem, partials + (long long)tile.id * Plan<T, L>::kmax);
 }
 
 template <typename T, int L, int C>
 __device__ __forceinline__ void run_tile(const MomTile& tile, const MomJob* __restrict__ jobs,
                                          const SysGeom* __restrict__ geoms, double* __restrict__ partials,
-                                         unsigned char* smem) {
+                                         unsigned char* smem, Xform<T>* xf_sh) {
   using P = Plan<T, L>;
   if constexpr (C < P::nch) {
     if (tile.chunk == C)
-      run_chunk<T, L, P::m0(C), P::m0(C + 1)>(tile, jobs, geoms, partials, smem);
+      run_chunk<T, L, P::m0(C), P::m0(C + 1)>(tile, jobs, geoms, partials, smem, xf_sh);
     else
-      run_tile<T, L, C + 1>(tile, jobs, geoms, partials, smem);
+      run_tile<T, L, C + 1>(tile, jobs, geoms, partials, smem, xf_sh);
   }
 }
 
 template <typename T, int L>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, TCM_MOMENT_CTAS_PER_SM)
     k_moments(const MomJob* __restrict__ jobs, const MomTile* __restrict__ tiles, int n_tiles,
               int* __restrict__ counter, const SysGeom* __restrict__ geoms, double* __restrict__ partials) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_next;
+  __shared__ Xform<T> s_xf;
   for (;;) {
     if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
     __syncthreads();
@@ -296,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     if (ti >= n_tiles) return;
     const MomTile tile = tiles[ti];
-    run_tile<T, L, 0>(tile, jobs, geoms, partials, smem);
+    run_tile<T, L, 0>(tile, jobs, geoms, partials, smem, &s_xf);
   }
 }
 

@@ -29,27 +29,42 @@ namespace tcm {
 constexpr int kLmaxMax = TCM_LMAX_MAX;
 constexpr int kThreads = 128;  // threads per moment CTA (4 warps)
 
-// Accumulator budget per thread for the float and double moment kernels.
-constexpr int kKmaxF32 = 160;
-constexpr int kKmaxF64 = 80;
+// Accumulator budget per thread for the float and double moment kernels, and the CTAs
+// per SM the moment kernels are compiled for (register limit 65536 / (128 x CTAs)).
+#ifndef TCM_KMAX_F32
+#define TCM_KMAX_F32 160
+#endif
+#ifndef TCM_KMAX_F64
+#define TCM_KMAX_F64 80
+#endif
+#ifndef TCM_MOMENT_CTAS_PER_SM
+#define TCM_MOMENT_CTAS_PER_SM 2
+#endif
+constexpr int kKmaxF32 = TCM_KMAX_F32;
+constexpr int kKmaxF64 = TCM_KMAX_F64;
 
 // ---------------------------------------------------------------------------------
 // Column-chunk plan (host and device, compile time).
 __host__ __device__ constexpr int col_acc(int L, int m) { return m == 0 ? (L + 1) : 2 * (L - m + 1); }
 
-// First column of chunk c when the columns 0..L are split greedily into nch chunks
-// of at most kmax accumulators, each filled up to the balanced target.
+// First column of chunk c when the columns 0..L are split greedily into nch chunks of at
+// most kmax accumulators: a chunk closes once it reaches the balanced target, provided
+// the remaining columns still fit into the remaining chunks.
 __host__ __device__ constexpr int plan_m0(int L, int kmax, int nch, int c) {
   int total = (L + 1) * (L + 1);
   int target = (total + nch - 1) / nch;
   int m = 0;
+  int placed = 0;
   for (int cc = 0; cc < nch; ++cc) {
     if (cc == c) return m;
     int acc = 0;
-    while (m <= L && acc + col_acc(L, m) <= kmax && (acc < target || acc == 0)) {
+    while (m <= L && acc + col_acc(L, m) <= kmax) {
+      const int rest = total - placed - acc;
+      if (acc >= target && rest <= kmax * (nch - cc - 1)) break;
       acc += col_acc(L, m);
       ++m;
     }
+    placed += acc;
   }
   return m;
 }
