@@ -54,68 +54,111 @@ struct Plan {
   }
 };
 
-// Register state of one column chunk [M0, M1).
+// Pairs: float2 in the float kernels, where the (Re, Im) halves of a complex step go
+// through one packed f32x2 instruction; double2 with scalar arithmetic in the double ones.
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+template <typename T>
+using P2 = typename Pair<T>::type;
+
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+  return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+}
+template <typename T>
+__device__ __forceinline__ P2<T> pair(T a, T b) {
+  P2<T> r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+
+// Register state of one column chunk [M0, M1).  The kernels carry H_j = sigma_j G_{m+j}
+// (sigma = +, +, -, -, +, +, ... along each column), for which the recurrence reads
+//   H_{j+1} = (-1)^j k_{m+j,m} c H_j + H_{j-1}
+// without a subtraction, so a complex step is one packed multiply (t, t) = (k', k') (c, c),
+// one packed FMA for the recurrence and one packed FMA for the accumulation.  The sign
+// sigma_{l-m} is part of the finalisation factor.
 template <typename T, int L, int M0, int M1>
 struct Regs {
   static constexpr int NC = M1 - M0;
   static constexpr int NACC = chunk_off(L, M0, M1);
-  T acc[NACC];
-  T gr[NC], gi[NC];  // G_l,m   (real, imaginary)
-  T pr[NC], pi[NC];  // G_l-1,m
-  T dr, di;          // running diagonal power u^m
+  static constexpr int N0 = M0 == 0 ? L + 1 : 0;  // real accumulators of column 0
+  static constexpr int NP = (NACC - N0) / 2;      // complex accumulators
+  T acc0[N0 > 0 ? N0 : 1];
+  P2<T> accp[NP > 0 ? NP : 1];
+  T g0, p0;             // column 0: H_j, H_j-1
+  P2<T> g[NC], p[NC];   // columns m >= 1
+  T dr, di;             // running diagonal power u^m
 };
 
-// Column m at degree l: advance its recurrence to G_lm and accumulate qr * G_lm.
+// Column m at degree l: advance its recurrence and accumulate qr * H.
 template <typename T, int L, int M0, int M1, int l, int m>
-__device__ __forceinline__ void col_step(Regs<T, L, M0, M1>& s, T ux, T uy, T c, T qr) {
+__device__ __forceinline__ void col_step(Regs<T, L, M0, M1>& s, T ux, T uy, P2<T> cc, P2<T> qq) {
   if constexpr (m <= l) {
     constexpr int j = m - M0;
-    if constexpr (l == m) {
-      if constexpr (m > M0) {
-        const T nr = s.dr * ux - s.di * uy;
-        const T ni = s.dr * uy + s.di * ux;
-        s.dr = nr;
-        s.di = ni;
+    constexpr int jj = l - m;  // index along the column
+    if constexpr (m == 0) {
+      if constexpr (jj == 0) {
+        s.g0 = (T)1;
+      } else if constexpr (jj == 1) {
+        s.p0 = s.g0;
+        s.g0 = cc.x;
+      } else {
+        constexpr T k = (T)(((jj - 1) & 1) ? -kcoef(l - 1, 0) : kcoef(l - 1, 0));
+        const T t = k * cc.x;
+        const T n = fmaT(t, s.g0, s.p0);
+        s.p0 = s.g0;
+        s.g0 = n;
       }
-      s.gr[j] = s.dr;
-      s.gi[j] = s.di;
-    } else if constexpr (l == m + 1) {
-      s.pr[j] = s.gr[j];
-      s.gr[j] = c * s.pr[j];
-      if constexpr (m > 0) {
-        s.pi[j] = s.gi[j];
-        s.gi[j] = c * s.pi[j];
-      }
+      s.acc0[l] = fmaT(qq.x, s.g0, s.acc0[l]);
     } else {
-      constexpr T k = (T)kcoef(l - 1, m);
-      const T t = k * c;
-      const T nr = fmaT(t, s.gr[j], -s.pr[j]);
-      s.pr[j] = s.gr[j];
-      s.gr[j] = nr;
-      if constexpr (m > 0) {
-        const T ni = fmaT(t, s.gi[j], -s.pi[j]);
-        s.pi[j] = s.gi[j];
-        s.gi[j] = ni;
+      if constexpr (jj == 0) {
+        if constexpr (m > M0) {
+          const T nr = s.dr * ux - s.di * uy;
+          const T ni = s.dr * uy + s.di * ux;
+          s.dr = nr;
+          s.di = ni;
+        }
+        s.g[j] = pair<T>(s.dr, s.di);
+      } else if constexpr (jj == 1) {
+        s.p[j] = s.g[j];
+        s.g[j] = mul2(cc, s.g[j]);
+      } else {
+        constexpr T k = (T)(((jj - 1) & 1) ? -kcoef(l - 1, m) : kcoef(l - 1, m));
+        const P2<T> tt = mul2(cc, pair<T>(k, k));
+        const P2<T> n = fma2(tt, s.g[j], s.p[j]);
+        s.p[j] = s.g[j];
+        s.g[j] = n;
       }
+      constexpr int a = (chunk_off(L, M0, m) - Regs<T, L, M0, M1>::N0) / 2 + jj;
+      s.accp[a] = fma2(qq, s.g[j], s.accp[a]);
     }
-    constexpr int a = chunk_off(L, M0, m) + (m == 0 ? l : 2 * (l - m));
-    s.acc[a] = fmaT(qr, s.gr[j], s.acc[a]);
-    if constexpr (m > 0) s.acc[a + 1] = fmaT(qr, s.gi[j], s.acc[a + 1]);
   }
 }
 
 template <typename T, int L, int M0, int M1, int l, int m>
-__device__ __forceinline__ void level_cols(Regs<T, L, M0, M1>& s, T ux, T uy, T c, T qr) {
+__device__ __forceinline__ void level_cols(Regs<T, L, M0, M1>& s, T ux, T uy, P2<T> cc, P2<T> qq) {
   if constexpr (m < M1) {
-    col_step<T, L, M0, M1, l, m>(s, ux, uy, c, qr);
-    level_cols<T, L, M0, M1, l, m + 1>(s, ux, uy, c, qr);
+    col_step<T, L, M0, M1, l, m>(s, ux, uy, cc, qq);
+    level_cols<T, L, M0, M1, l, m + 1>(s, ux, uy, cc, qq);
   }
 }
 
 template <typename T, int L, int M0, int M1, int l>
-__device__ __forceinline__ void levels(Regs<T, L, M0, M1>& s, T ux, T uy, T c, T rho, T qr) {
-  level_cols<T, L, M0, M1, l, M0>(s, ux, uy, c, qr);
-  if constexpr (l < L) levels<T, L, M0, M1, l + 1>(s, ux, uy, c, rho, qr * rho);
+__device__ __forceinline__ void levels(Regs<T, L, M0, M1>& s, T ux, T uy, P2<T> cc, P2<T> rr, P2<T> qq) {
+  level_cols<T, L, M0, M1, l, M0>(s, ux, uy, cc, qq);
+  if constexpr (l < L) levels<T, L, M0, M1, l + 1>(s, ux, uy, cc, rr, mul2(qq, rr));
 }
 
 // Per-tile transform of the coordinates: centring and rot / a.
@@ -205,11 +248,14 @@ __device__ __forceinline__ double row_sum32(const double* p) {
   return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
 
-// CTA reduction of the per-thread accumulators into one double row `out[0..NACC)`.
-// Each warp transposes its 32 x NACC block through shared memory and every lane
-// tree-sums whole rows (fixed order); the four warp sums are then added in double.
-template <typename T, int NACC>
-__device__ __forceinline__ void cta_reduce_store(const T (&acc)[NACC], unsigned char* smem_raw, double* out) {
+// CTA reduction of the per-thread accumulators into one double row `out[0..NACC)` (the
+// column-0 reals first, then the complex pairs, in slot order).  Each warp transposes its
+// 32 x NACC block through shared memory and every lane tree-sums whole rows (fixed order);
+// the four warp sums are then added in double.
+template <typename T, int L, int M0, int M1>
+__device__ __forceinline__ void cta_reduce_store(const Regs<T, L, M0, M1>& s, unsigned char* smem_raw, double* out) {
+  using R = Regs<T, L, M0, M1>;
+  constexpr int NACC = R::NACC;
   constexpr int S = MomTraits<T>::stride;
   constexpr int NW = kThreads / 32;
   constexpr int NR = (NACC + 31) / 32;
@@ -217,7 +263,12 @@ __device__ __forceinline__ void cta_reduce_store(const T (&acc)[NACC], unsigned 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* wb = buf + warp * (NACC * S);
 #pragma unroll
-  for (int k = 0; k < NACC; ++k) wb[k * S + lane] = acc[k];
+  for (int k = 0; k < R::N0; ++k) wb[k * S + lane] = s.acc0[k];
+#pragma unroll
+  for (int k = 0; k < R::NP; ++k) {
+    wb[(R::N0 + 2 * k) * S + lane] = s.accp[k].x;
+    wb[(R::N0 + 2 * k + 1) * S + lane] = s.accp[k].y;
+  }
   __syncwarp();
   T rs[NR];
 #pragma unroll
@@ -234,10 +285,10 @@ __device__ __forceinline__ void cta_reduce_store(const T (&acc)[NACC], unsigned 
   }
   __syncthreads();
   for (int k = threadIdx.x; k < NACC; k += kThreads) {
-    double s = 0.0;
+    double a = 0.0;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) s += (double)ws[w * NACC + k];
-    out[k] = s;
+    for (int w = 0; w < NW; ++w) a += (double)ws[w * NACC + k];
+    out[k] = a;
   }
   __syncthreads();
 }
@@ -256,6 +307,7 @@ __device__ __forceinline__ void atom_loop(Regs<T, L, M0, M1>& s, const Rec* __re
     T d0, d1, d2, q, ux, uy, cz, rho;
     centre<T>(cur, xf, cd, d0, d1, d2, q);
     setup<T>(d0, d1, d2, xf, ux, uy, cz, rho);
+    const P2<T> cc = pair<T>(cz, cz), rr = pair<T>(rho, rho), qq = pair<T>(q, q);
     if constexpr (M0 == 0) {
       s.dr = (T)1;
       s.di = (T)0;
@@ -270,7 +322,7 @@ __device__ __forceinline__ void atom_loop(Regs<T, L, M0, M1>& s, const Rec* __re
         s.di = ni;
       }
     }
-    levels<T, L, M0, M1, 0>(s, ux, uy, cz, rho, q);
+    levels<T, L, M0, M1, 0>(s, ux, uy, cc, rr, qq);
   }
 }
 
@@ -291,12 +343,14 @@ __device__ __forceinline__ void run_chunk(const MomTile& tile, const MomJob* __r
   const int dtype = job.dtype;
   R s;
 #pragma unroll
-  for (int k = 0; k < R::NACC; ++k) s.acc[k] = (T)0;
+  for (int k = 0; k < R::N0; ++k) s.acc0[k] = (T)0;
+#pragma unroll
+  for (int k = 0; k < R::NP; ++k) s.accp[k] = pair<T>((T)0, (T)0);
   if (dtype == TCM_F32)
     atom_loop<T, L, M0, M1>(s, reinterpret_cast<const float4*>(xyzq), i0, i1, xf, g.c);
   else
     atom_loop<T, L, M0, M1>(s, reinterpret_cast<const Rec64*>(xyzq), i0, i1, xf, g.c);
-  cta_reduce_store<T, R::NACC>(s.acc, smem, partials + (long long)tile.id * Plan<T, L>::kmax);
+  cta_reduce_store<T, L, M0, M1>(s, smem, partials + (long long)tile.id * Plan<T, L>::kmax);
 }
 
 template <typename T, int L, int C>

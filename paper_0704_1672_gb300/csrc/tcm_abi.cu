@@ -341,7 +341,8 @@ int build_tables(tcm_ctx* c) {
         s_prev = s;
         s = sn;
       }
-      const long double sgn = (m & 1) ? -1.0L : 1.0L;
+      // (-1)^m of the Condon-Shortley phase times sigma_{l-m} of the kernels' H variables
+      const long double sgn = ((m & 1) ? -1.0L : 1.0L) * (((l - m) & 2) ? -1.0L : 1.0L);
       ftab[l * N + m] = (double)(sgn * std::sqrt(fact[l - m] / fact[l + m]) * s);
     }
   }

@@ -8,9 +8,8 @@
 //     G_m+1,m  = c G_mm
 //     G_l+1,m  = k_lm c G_lm - G_l-1,m           (l >= m+1)
 // whose normalisation is chosen so that the G_l-1 coefficient is exactly one, and
-// accumulate q (r/a)^l G_lm.  The deferred factor F_lm a^l (F_lm below) turns the
-// sums into Q_lm.  Per real component this is one FMUL shared by Re/Im, one FFMA
-// for the recurrence and one FFMA for the accumulation.
+// accumulate q (r/a)^l G_lm (in the sign-alternated form H of moments_kernel.cuh).
+// The deferred factor F_lm a^l (times the sign of H) turns the sums into Q_lm.
 //
 // Accumulators live in registers, so the (Lmax+1)^2 components are split into
 // column chunks [m0, m1) of at most kmax accumulators; a chunk is a separate tile

@@ -81,7 +81,8 @@ void host_tables(std::vector<double>& ftab, std::vector<int>& off, std::vector<i
         s_prev = s;
         s = sn;
       }
-      ftab[l * N + m] = (double)(((m & 1) ? -1.0L : 1.0L) * std::sqrt(fact[l - m] / fact[l + m]) * s);
+      const long double sgn = ((m & 1) ? -1.0L : 1.0L) * (((l - m) & 2) ? -1.0L : 1.0L);
+      ftab[l * N + m] = (double)(sgn * std::sqrt(fact[l - m] / fact[l + m]) * s);
     }
   }
   off.assign(N + 1, 0);
