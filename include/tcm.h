@@ -130,6 +130,12 @@ typedef enum {
   TCM_NPHASES = 5
 } tcm_phase;
 
+/* Tiling of the moment pass for one precision: each warp of the moment kernels takes
+ * tiles of 32 x atoms_per_lane atoms (1..4096; defaults 64 for TCM_MIXED, 32 for
+ * TCM_FP64).  A system's tiles, and so the rounding of its moments, depend only on its
+ * atom count, its Lmax and this setting.  Used by the autotuner. */
+int tcm_ctx_set_tiling(tcm_ctx_t ctx, int precision, int atoms_per_lane);
+
 /* Enable (1) or disable (0) phase timing: the context then records a CUDA event pair on
  * its stream around every phase it queues.  Off by default. */
 int tcm_ctx_set_profiling(tcm_ctx_t ctx, int enable);

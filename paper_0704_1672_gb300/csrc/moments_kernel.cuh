@@ -1,7 +1,6 @@
-// Moment kernels, Eq. (multipole): persistent CTAs pull tiles (job, column chunk,
-// atom range); every thread keeps the chunk's accumulators in registers while it
-// walks its atoms, then the CTA reduces them into one double-precision partial row
-// per tile.  Included by the per-Lmax translation units, which instantiate
+// Moment kernels, Eq. (multipole): persistent warps pull warp tiles (job, column chunk,
+// atom range); every lane keeps the chunk's accumulators in registers while it walks
+// its atoms, then the warp reduces them into one double-precision partial row per tile.  Included by the per-Lmax translation units, which instantiate
 // launch_moments_t<T, L> explicitly.
 //
 // Per atom (after the per-tile transform M = rot / a', a' = scale_radius(a) a power of
@@ -248,20 +247,16 @@ __device__ __forceinline__ double row_sum32(const double* p) {
   return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
 
-// CTA reduction of the per-thread accumulators into one double row `out[0..NACC)` (the
-// column-0 reals first, then the complex pairs, in slot order).  Each warp transposes its
-// 32 x NACC block through shared memory and every lane tree-sums whole rows (fixed order);
-// the four warp sums are then added in double.
+// Warp reduction of the per-lane accumulators into one double row `out[0..NACC)` (the
+// column-0 reals first, then the complex pairs, in slot order).  The warp transposes its
+// 32 x NACC block through its own shared-memory region and every lane tree-sums whole rows
+// (fixed order), converts them to double and stores them.  No CTA barrier is involved.
 template <typename T, int L, int M0, int M1>
-__device__ __forceinline__ void cta_reduce_store(const Regs<T, L, M0, M1>& s, unsigned char* smem_raw, double* out) {
+__device__ __forceinline__ void warp_reduce_store(const Regs<T, L, M0, M1>& s, T* wb, double* out) {
   using R = Regs<T, L, M0, M1>;
   constexpr int NACC = R::NACC;
   constexpr int S = MomTraits<T>::stride;
-  constexpr int NW = kThreads / 32;
-  constexpr int NR = (NACC + 31) / 32;
-  T* buf = reinterpret_cast<T*>(smem_raw);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* wb = buf + warp * (NACC * S);
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < R::N0; ++k) wb[k * S + lane] = s.acc0[k];
 #pragma unroll
@@ -270,40 +265,25 @@ __device__ __forceinline__ void cta_reduce_store(const Regs<T, L, M0, M1>& s, un
     wb[(R::N0 + 2 * k + 1) * S + lane] = s.accp[k].y;
   }
   __syncwarp();
-  T rs[NR];
 #pragma unroll
-  for (int rr = 0; rr < NR; ++rr) {
+  for (int rr = 0; rr < (NACC + 31) / 32; ++rr) {
     const int r = lane + 32 * rr;
-    rs[rr] = (r < NACC) ? row_sum32(wb + r * S) : (T)0;
+    if (r < NACC) out[r] = (double)row_sum32(wb + r * S);
   }
-  __syncthreads();
-  T* ws = buf;  // [NW][NACC], reuses the transpose buffer
-#pragma unroll
-  for (int rr = 0; rr < NR; ++rr) {
-    const int r = lane + 32 * rr;
-    if (r < NACC) ws[warp * NACC + r] = rs[rr];
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < NACC; k += kThreads) {
-    double a = 0.0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) a += (double)ws[w * NACC + k];
-    out[k] = a;
-  }
-  __syncthreads();
+  __syncwarp();
 }
 
-// Walks this thread's atoms of [i0, i1), the next record prefetched while the current
-// one is processed.
+// Walks this lane's atoms of the warp tile [i0, i1), the next record prefetched while the
+// current one is processed.
 template <typename T, int L, int M0, int M1, typename Rec>
 __device__ __forceinline__ void atom_loop(Regs<T, L, M0, M1>& s, const Rec* __restrict__ xyzq, long long i0,
                                           long long i1, const Xform<T>& xf, const double* cd) {
-  long long i = i0 + threadIdx.x;
+  long long i = i0 + (threadIdx.x & 31);
   if (i >= i1) return;
   Rec nxt = load_rec(xyzq, i);
-  for (; i < i1; i += kThreads) {
+  for (; i < i1; i += 32) {
     const Rec cur = nxt;
-    if (i + kThreads < i1) nxt = load_rec(xyzq, i + kThreads);
+    if (i + 32 < i1) nxt = load_rec(xyzq, i + 32);
     T d0, d1, d2, q, ux, uy, cz, rho;
     centre<T>(cur, xf, cd, d0, d1, d2, q);
     setup<T>(d0, d1, d2, xf, ux, uy, cz, rho);
@@ -328,14 +308,14 @@ __device__ __forceinline__ void atom_loop(Regs<T, L, M0, M1>& s, const Rec* __re
 
 template <typename T, int L, int M0, int M1>
 __device__ __forceinline__ void run_chunk(const MomTile& tile, const MomJob* __restrict__ jobs,
-                                          const SysGeom* __restrict__ geoms, double* __restrict__ partials,
-                                          unsigned char* smem, Xform<T>* xf_sh) {
+                                          const SysGeom* __restrict__ geoms, double* __restrict__ partials, T* wb,
+                                          Xform<T>* xf_w) {
   using R = Regs<T, L, M0, M1>;
   const MomJob& job = jobs[tile.job];
   const SysGeom g = geoms[job.geom];
-  if (threadIdx.x == 0) *xf_sh = make_xform<T>(job, g);  // double math once per tile, not per thread
-  __syncthreads();
-  const Xform<T> xf = *xf_sh;
+  if ((threadIdx.x & 31) == 0) *xf_w = make_xform<T>(job, g);  // double math once per tile
+  __syncwarp();
+  const Xform<T> xf = *xf_w;
   const long long n = job.n;
   const long long i0 = (long long)tile.t * job.atoms_per_tile;
   const long long i1 = min(n, i0 + (long long)job.atoms_per_tile);
@@ -350,37 +330,39 @@ __device__ __forceinline__ void run_chunk(const MomTile& tile, const MomJob* __r
     atom_loop<T, L, M0, M1>(s, reinterpret_cast<const float4*>(xyzq), i0, i1, xf, g.c);
   else
     atom_loop<T, L, M0, M1>(s, reinterpret_cast<const Rec64*>(xyzq), i0, i1, xf, g.c);
-  cta_reduce_store<T, L, M0, M1>(s, smem, partials + (long long)tile.id * Plan<T, L>::kmax);
+  warp_reduce_store<T, L, M0, M1>(s, wb, partials + (long long)tile.id * Plan<T, L>::kmax);
 }
 
 template <typename T, int L, int C>
 __device__ __forceinline__ void run_tile(const MomTile& tile, const MomJob* __restrict__ jobs,
-                                         const SysGeom* __restrict__ geoms, double* __restrict__ partials,
-                                         unsigned char* smem, Xform<T>* xf_sh) {
+                                         const SysGeom* __restrict__ geoms, double* __restrict__ partials, T* wb,
+                                         Xform<T>* xf_w) {
   using P = Plan<T, L>;
   if constexpr (C < P::nch) {
     if (tile.chunk == C)
-      run_chunk<T, L, P::m0(C), P::m0(C + 1)>(tile, jobs, geoms, partials, smem, xf_sh);
+      run_chunk<T, L, P::m0(C), P::m0(C + 1)>(tile, jobs, geoms, partials, wb, xf_w);
     else
-      run_tile<T, L, C + 1>(tile, jobs, geoms, partials, smem, xf_sh);
+      run_tile<T, L, C + 1>(tile, jobs, geoms, partials, wb, xf_w);
   }
 }
 
+// Persistent kernel: every warp pulls warp tiles from the shared counter until none are
+// left, so warps never wait for each other.
 template <typename T, int L>
 __global__ void __launch_bounds__(kThreads, TCM_MOMENT_CTAS_PER_SM)
     k_moments(const MomJob* __restrict__ jobs, const MomTile* __restrict__ tiles, int n_tiles,
               int* __restrict__ counter, const SysGeom* __restrict__ geoms, double* __restrict__ partials) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_next;
-  __shared__ Xform<T> s_xf;
+  __shared__ Xform<T> s_xf[kThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* wb = reinterpret_cast<T*>(smem) + warp * (Plan<T, L>::max_nacc() * MomTraits<T>::stride);
   for (;;) {
-    if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
-    __syncthreads();
-    const int ti = s_next;
-    __syncthreads();
+    int ti = 0;
+    if (lane == 0) ti = atomicAdd(counter, 1);
+    ti = __shfl_sync(0xffffffffu, ti, 0);
     if (ti >= n_tiles) return;
     const MomTile tile = tiles[ti];
-    run_tile<T, L, 0>(tile, jobs, geoms, partials, smem, &s_xf);
+    run_tile<T, L, 0>(tile, jobs, geoms, partials, wb, &s_xf[warp]);
   }
 }
 

@@ -94,7 +94,7 @@ struct tcm_ctx {
   Stage stage[kStages];
   int stage_next = 0;
   void* pinned_small = nullptr;  // 256 B for small device->host reads
-  int atoms_per_thread[2] = {16, 32};  // [TCM_FP64, TCM_MIXED]
+  int atoms_per_thread[2] = {32, 64};  // atoms per lane of a warp tile, [TCM_FP64, TCM_MIXED]
   // phase profiling
   bool prof = false;
   struct Mark {
@@ -218,7 +218,7 @@ struct Plan {
 
 void plan_job(tcm_ctx* c, int precision, MomJob& j, int& next_id) {
   const int nch = moments_nchunks(precision, j.L);
-  const long long per_tile = (long long)kThreads * c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1];
+  const long long per_tile = 32LL * c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1];  // one warp
   long long tpc = (j.n + per_tile - 1) / per_tile;
   if (tpc < 1) tpc = 1;
   j.tiles_per_chunk = (int)tpc;
@@ -275,7 +275,7 @@ int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, 
     for (int L = 0; L <= kLmaxMax; ++L) {
       const int b = P.tile_begin[L], e = P.tile_begin[L + 1];
       if (e == b) continue;
-      const int grid = std::min(e - b, 2 * c->num_sms);
+      const int grid = std::min((e - b + kThreads / 32 - 1) / (kThreads / 32), 2 * c->num_sms);  // warp tiles
       TRY_LAUNCH(launch_moments(precision, L, d_jobs, d_tiles + b, e - b, counters + L, d_geoms, parts, grid, c->stream));
     }
   }
@@ -465,6 +465,15 @@ int tcm_ctx_set_stream(tcm_ctx_t c, void* cuda_stream) {
   TRY(check_ctx(c));
   TRY_CUDA(cudaStreamSynchronize(c->stream));
   c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return TCM_OK;
+}
+
+int tcm_ctx_set_tiling(tcm_ctx_t c, int precision, int atoms_per_lane) {
+  TRY(check_ctx(c));
+  if (precision != TCM_FP64 && precision != TCM_MIXED) return set_err(TCM_EINVAL, "tcm_ctx_set_tiling: bad precision");
+  if (atoms_per_lane < 1 || atoms_per_lane > 4096)
+    return set_err(TCM_EINVAL, "tcm_ctx_set_tiling: atoms_per_lane outside [1, 4096]");
+  c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1] = atoms_per_lane;
   return TCM_OK;
 }
 

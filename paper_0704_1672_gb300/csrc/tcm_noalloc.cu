@@ -216,7 +216,7 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   const int n_tiles = nch * tpc;
   if (launch_moments(precision, lmax, d_job, reinterpret_cast<MomTile*>(base + kOffTiles), n_tiles,
                      reinterpret_cast<int*>(base + kOffCounters), d_geom, reinterpret_cast<double*>(base + kOffPartials),
-                     std::min(n_tiles, 2 * num_sms), st) != 0)
+                     std::min((n_tiles + kThreads / 32 - 1) / (kThreads / 32), 2 * num_sms), st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: moment launch failed");
   if (launch_finalize(d_job, 1, reinterpret_cast<double*>(base + kOffPartials), d_geom,
                       reinterpret_cast<int2*>(base + kOffCmap) + (precision == TCM_FP64 ? 0 : kNaCompTotal),
