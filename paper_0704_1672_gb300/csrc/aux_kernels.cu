@@ -72,13 +72,16 @@ __device__ __forceinline__ void load_xyz(const void* p, int dtype, long long i, 
   }
 }
 
-constexpr int kGeomThreads = 256;
+constexpr int kGeomThreads = 128;
 
-// a1, pass 1: per-tile sums of the coordinates (double).
-__global__ void __launch_bounds__(kGeomThreads) k_geom_sum(const GeomJob* __restrict__ gj,
-                                                           const GeomTile* __restrict__ gt,
-                                                           double* __restrict__ gpart) {
+// a1, pass 1: per-tile sums of the coordinates (double); the last CTA of a system to
+// finish (ticket) adds the tile sums in tile order and writes the centroid.
+__global__ void __launch_bounds__(kGeomThreads) k_geom_centroid(const GeomJob* __restrict__ gj,
+                                                                const GeomTile* __restrict__ gt,
+                                                                double* __restrict__ gpart, int* __restrict__ tickets,
+                                                                SysGeom* __restrict__ geoms) {
   __shared__ double sh[32];
+  __shared__ int s_last;
   const GeomTile tile = gt[blockIdx.x];
   const GeomJob j = gj[tile.gjob];
   const long long i0 = (long long)tile.t * kGeomTileAtoms;
@@ -99,29 +102,32 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom_sum(const GeomJob* __rest
     o[0] = sx;
     o[1] = sy;
     o[2] = sz;
+    __threadfence();
+    s_last = atomicAdd(&tickets[tile.gjob], 1) == j.n_tiles - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    tickets[tile.gjob] = 0;
+    if (j.need_center) {
+      double s[3] = {0.0, 0.0, 0.0};
+      const volatile double* p = gpart + 4LL * j.tile_base;
+      for (int t = 0; t < j.n_tiles; ++t)
+        for (int d = 0; d < 3; ++d) s[d] += p[4 * t + d];
+      const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
+      for (int d = 0; d < 3; ++d) geoms[j.geom].c[d] = s[d] * inv;
+    }
   }
 }
 
-// a1, pass 2: centroid from the tile sums (fixed order), one thread per system.
-__global__ void k_geom_center(const GeomJob* __restrict__ gj, int n, const double* __restrict__ gpart,
-                              SysGeom* __restrict__ geoms) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const GeomJob j = gj[k];
-  if (!j.need_center) return;
-  double s[3] = {0.0, 0.0, 0.0};
-  for (int t = 0; t < j.n_tiles; ++t)
-    for (int d = 0; d < 3; ++d) s[d] += gpart[4LL * (j.tile_base + t) + d];
-  const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
-  for (int d = 0; d < 3; ++d) geoms[j.geom].c[d] = s[d] * inv;
-}
-
-// a1, pass 3: per-tile max of |x - c|^2.
-__global__ void __launch_bounds__(kGeomThreads) k_geom_rmax(const GeomJob* __restrict__ gj,
-                                                            const GeomTile* __restrict__ gt,
-                                                            const SysGeom* __restrict__ geoms,
-                                                            double* __restrict__ gpart) {
+// a1, pass 2: per-tile max of |x - c|^2; the last CTA of a system writes the radius.
+__global__ void __launch_bounds__(kGeomThreads) k_geom_radius(const GeomJob* __restrict__ gj,
+                                                              const GeomTile* __restrict__ gt,
+                                                              double* __restrict__ gpart, int* __restrict__ tickets,
+                                                              SysGeom* __restrict__ geoms) {
   __shared__ double sh[32];
+  __shared__ int s_last;
   const GeomTile tile = gt[blockIdx.x];
   const GeomJob j = gj[tile.gjob];
   const double cx = geoms[j.geom].c[0], cy = geoms[j.geom].c[1], cz = geoms[j.geom].c[2];
@@ -135,19 +141,23 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom_rmax(const GeomJob* __res
     mx = fmax(mx, dx * dx + dy * dy + dz * dz);
   }
   mx = block_max(mx, sh);
-  if (threadIdx.x == 0) gpart[4LL * (j.tile_base + tile.t) + 3] = mx;
-}
-
-// a1, pass 4: radius.
-__global__ void k_geom_radius(const GeomJob* __restrict__ gj, int n, const double* __restrict__ gpart,
-                              SysGeom* __restrict__ geoms) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const GeomJob j = gj[k];
-  if (!j.need_radius) return;
-  double mx = 0.0;
-  for (int t = 0; t < j.n_tiles; ++t) mx = fmax(mx, gpart[4LL * (j.tile_base + t) + 3]);
-  geoms[j.geom].a = sqrt(mx);
+  if (threadIdx.x == 0) {
+    gpart[4LL * (j.tile_base + tile.t) + 3] = mx;
+    __threadfence();
+    s_last = atomicAdd(&tickets[tile.gjob], 1) == j.n_tiles - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    tickets[tile.gjob] = 0;
+    if (j.need_radius) {
+      const volatile double* p = gpart + 4LL * j.tile_base;
+      double m = 0.0;
+      for (int t = 0; t < j.n_tiles; ++t) m = fmax(m, p[4 * t + 3]);
+      geoms[j.geom].a = sqrt(m);
+    }
+  }
 }
 
 // a3: one CTA per moment job.  Sums the job's tile partials of each component in
@@ -470,14 +480,11 @@ int contract_smem_bytes(int L) {
   return (4 * nq + (L + 1)) * (int)sizeof(double2) + (3 * (2 * L + 1) + nd) * (int)sizeof(double);
 }
 
-int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n_gtiles, double* gpart,
+int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n_gtiles, double* gpart, int* tickets,
                 SysGeom* geoms, cudaStream_t s) {
   if (n_gjobs <= 0) return 0;
-  const int nb = (n_gjobs + 127) / 128;
-  k_geom_sum<<<n_gtiles, kGeomThreads, 0, s>>>(gjobs, gtiles, gpart);
-  k_geom_center<<<nb, 128, 0, s>>>(gjobs, n_gjobs, gpart, geoms);
-  k_geom_rmax<<<n_gtiles, kGeomThreads, 0, s>>>(gjobs, gtiles, geoms, gpart);
-  k_geom_radius<<<nb, 128, 0, s>>>(gjobs, n_gjobs, gpart, geoms);
+  k_geom_centroid<<<n_gtiles, kGeomThreads, 0, s>>>(gjobs, gtiles, gpart, tickets, geoms);
+  k_geom_radius<<<n_gtiles, kGeomThreads, 0, s>>>(gjobs, gtiles, gpart, tickets, geoms);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -287,6 +287,11 @@ int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, 
   return TCM_OK;
 }
 
+// Ticket counters of the a1 kernels: the tail of the gpart buffer (after ngt 4-double rows).
+int* geom_tickets(tcm_ctx* c, int ngt, int) {
+  return reinterpret_cast<int*>(static_cast<char*>(c->gpart.p) + (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64);
+}
+
 // Step a1 for the systems that need it (device only, no host round trip).
 int add_geom_jobs(const tcm_system* systems, int n_systems, const std::vector<char>& used,
                   std::vector<GeomJob>& gjobs, std::vector<GeomTile>& gtiles) {
@@ -515,13 +520,14 @@ int tcm_prepare(tcm_ctx_t c, tcm_system* s) {
   const size_t o_geo = pk.add(geoms), o_gj = pk.add(gjobs), o_gt = pk.add(gtiles);
   char* base = nullptr;
   TRY(upload(c, pk, &base));
-  TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double)));
+  TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
+  TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   {
-    PhaseScope ps(c, TCM_PHASE_GEOM, 4);
+    PhaseScope ps(c, TCM_PHASE_GEOM, 2);
     TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
-                           static_cast<double*>(c->gpart.p), d_geo, c->stream));
+                           static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
   }
   TRY_CUDA(cudaMemcpyAsync(c->pinned_small, d_geo, sizeof(SysGeom), cudaMemcpyDeviceToHost, c->stream));
   TRY_CUDA(cudaStreamSynchronize(c->stream));
@@ -569,11 +575,12 @@ int tcm_moments(tcm_ctx_t c, const tcm_system* s, const double* rot, int lmax, i
   TRY(upload(c, pk, &base));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   if (!gjobs.empty()) {
-    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double)));
-    PhaseScope ps(c, TCM_PHASE_GEOM, 4);
+    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
+    TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
+    PhaseScope ps(c, TCM_PHASE_GEOM, 2);
     TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
-                           static_cast<double*>(c->gpart.p), d_geo, c->stream));
+                           static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
   }
   TRY(run_moments(c, precision, P, reinterpret_cast<MomJob*>(base + o_job), reinterpret_cast<MomTile*>(base + o_tile),
                   d_geo));
@@ -725,11 +732,12 @@ int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int6
   TRY(upload(c, pk, &base));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   if (!gjobs.empty()) {
-    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double)));
-    PhaseScope ps(c, TCM_PHASE_GEOM, 4);
+    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
+    TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
+    PhaseScope ps(c, TCM_PHASE_GEOM, 2);
     TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
-                           static_cast<double*>(c->gpart.p), d_geo, c->stream));
+                           static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
   }
   const MomJob* d_jobs = reinterpret_cast<MomJob*>(base + o_job);
   TRY(run_moments(c, precision, P, d_jobs, reinterpret_cast<MomTile*>(base + o_tile), d_geo));
@@ -766,11 +774,12 @@ int tcm_direct(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, const doub
   TRY(upload(c, pk, &base));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   if (!gjobs.empty()) {
-    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double)));
-    PhaseScope ps(c, TCM_PHASE_GEOM, 4);
+    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
+    TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
+    PhaseScope ps(c, TCM_PHASE_GEOM, 2);
     TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
-                           static_cast<double*>(c->gpart.p), d_geo, c->stream));
+                           static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
   }
   const int nblk = direct_blocks(A->n);
   TRY(dev_ensure(c, c->dpart, (size_t)std::max(nblk, 1) * sizeof(double)));

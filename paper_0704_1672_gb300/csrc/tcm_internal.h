@@ -149,7 +149,7 @@ struct PairDesc {  // one energy: moments of jobA and jobB at lmax L, separation
   double R0[3];
 };
 
-constexpr int kGeomTileAtoms = 16384;
+constexpr int kGeomTileAtoms = 1024;
 
 // ---------------------------------------------------------------------------------
 // Launchers (defined in the .cu files).
@@ -162,7 +162,8 @@ int moments_smem_bytes(int precision, int L);
 int moments_kmax(int precision);
 int moments_nchunks(int precision, int L);
 
-int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n_gtiles, double* gpart,
+// a1 in two launches; tickets: one int per geometry job, zero on entry (left zero on exit).
+int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n_gtiles, double* gpart, int* tickets,
                 SysGeom* geoms, cudaStream_t s);
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms,
                     const int2* cmap, const int* cmap_off, const double* ftab, int kmax, cudaStream_t s);

@@ -208,7 +208,8 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   k_noalloc_prepare<<<1, 256, 0, st>>>(base, job, geom, gj, known ? 0 : gj.n_tiles, nch, tpc);
   if (cudaPeekAtLastError() != cudaSuccess) return na_err(TCM_ECUDA, "tcm_moments_noalloc: launch failed");
   if (!known && launch_geom(reinterpret_cast<GeomJob*>(base + kOffGJob), 1, reinterpret_cast<GeomTile*>(base + kOffGTiles),
-                            gj.n_tiles, reinterpret_cast<double*>(base + kOffGPart), d_geom, st) != 0)
+                            gj.n_tiles, reinterpret_cast<double*>(base + kOffGPart),
+                            reinterpret_cast<int*>(base + kOffCounters) + 32, d_geom, st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: centre/radius launch failed");
   int num_sms = 0;
   if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
