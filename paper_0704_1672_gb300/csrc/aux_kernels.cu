@@ -242,10 +242,9 @@ __device__ __forceinline__ double dget(const double* D, int offl, int mp, int m)
   return flip(D[offl + mp * mp - mp - m], m - mp);  // a = -mp, b = -m
 }
 
-// Rotate the packed moments p (m >= 0, complex in qin) into the frame: writes qout, normalised
-// to Qhat.  Threads stride over (l, m).
-__device__ void rotate_into_frame(const double2* qin, double2* qout, const double* D, const double2* ph, int L,
-                                  const double* ztab) {
+// Rotate moments already multiplied by e^{-i m alpha} (m >= 0, complex in qin) into the
+// frame: writes qout, normalised to Qhat.  Threads stride over (l, m).
+__device__ void rotate_into_frame(const double2* qin, double2* qout, const double* D, int L, const double* ztab) {
   const int nq = (L + 1) * (L + 2) / 2;
   for (int k = threadIdx.x; k < nq; k += blockDim.x) {
     const int l = tri_l(k);
@@ -255,14 +254,10 @@ __device__ void rotate_into_frame(const double2* qin, double2* qout, const doubl
     double re = dget(D, offl, 0, m) * q[0].x;
     double im = 0.0;
     for (int mp = 1; mp <= l; ++mp) {
-      // P = e^{-i mp alpha} Q_l,mp
-      const double2 e = ph[mp];
-      const double px = e.x * q[mp].x - e.y * q[mp].y;
-      const double py = e.x * q[mp].y + e.y * q[mp].x;
       const double d1 = dget(D, offl, mp, m);
       const double d2 = flip(dget(D, offl, -mp, m), mp);
-      re = fma(d1 + d2, px, re);
-      im = fma(d1 - d2, py, im);
+      re = fma(d1 + d2, q[mp].x, re);
+      im = fma(d1 - d2, q[mp].y, im);
     }
     const double f = ztab[kZ_ISF + l * kZN + m];
     qout[k] = make_double2(re * f, im * f);
@@ -274,6 +269,7 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
                                                                const SysGeom* __restrict__ geoms,
                                                                const double* __restrict__ ztab,
                                                                double* __restrict__ E, int32_t* __restrict__ status) {
+  const double* rtab = ztab + ((kZ_TOTAL + 3) / 4 * 4);  // recursion coefficients, 4 doubles per (l, a, b)
   extern __shared__ double2 sm2[];
   __shared__ double sh[32];
   __shared__ double g_cb, g_ch, g_sh, g_iR;
@@ -352,33 +348,46 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     }
   }
   __syncthreads();
-  // Wigner d^l_{ab}, a >= |b|: one thread per (a, b) walks l upward.
+  // P_lm = e^{-i m alpha} Q_lm, once per (l, m), for the sides that are rotated here
+  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+    const int l = tri_l(k);
+    const int m = k - l * (l + 1) / 2;
+    if (m == 0) continue;
+    const double2 e = ph[m];
+    double2 v = qa[k];
+    qa[k] = make_double2(e.x * v.x - e.y * v.y, e.x * v.y + e.y * v.x);
+    if (!b_in_frame) {
+      v = qb[k];
+      qb[k] = make_double2(e.x * v.x - e.y * v.y, e.x * v.y + e.y * v.x);
+    }
+  }
+  // Wigner d^l_{ab}, a >= |b|: one thread per (a, b) walks l upward.  The step
+  //   d_l = A (t d_l-1 - B d_l-2),  t = cos(beta) - ab / (l (l-1)),
+  // uses per-(l, a, b) coefficients (A, A ab / (l (l-1)), A B) from rtab.
   const double cb = g_cb;
   for (int p = threadIdx.x; p < (L + 1) * (L + 1); p += blockDim.x) {
     int a = (int)sqrtf((float)p);
     while (a * a > p) --a;
     while ((a + 1) * (a + 1) <= p) ++a;
     const int b = p - a * a - a;
-    const int ab = b < 0 ? -b : b;
     double d1 = flip(ztab[kZ_SQC + a * 2 * kZN + a + b] * cp[a + b] * sp[a - b], a - b);
     double d2 = 0.0;
     D[a * (a + 1) * (2 * a + 1) / 6 + a * a + a + b] = d1;
-    const double abd = (double)(a * b);
     for (int l = a + 1; l <= L; ++l) {
-      const double A = ztab[kZ_K1 + l * kZN + a] * ztab[kZ_IRS + l * kZN + ab];
-      const double t = fma(-abd, ztab[kZ_ILL + l], cb);
-      double v = t * d1;
-      if (l - 2 >= a) v = fma(-ztab[kZ_K2 + l * kZN + a] * ztab[kZ_RS1 + l * kZN + ab], d2, v);
-      v *= A;
-      D[l * (l + 1) * (2 * l + 1) / 6 + a * a + a + b] = v;
+      const int e = l * (l + 1) * (2 * l + 1) / 6 + a * a + a + b;
+      const double2 c01 = __ldg(reinterpret_cast<const double2*>(rtab) + 2 * e);
+      const double c2 = __ldg(rtab + 4 * e + 2);
+      const double At = fma(c01.x, cb, -c01.y);
+      const double v = fma(At, d1, -(c2 * d2));
+      D[e] = v;
       d2 = d1;
       d1 = v;
     }
   }
   __syncthreads();
-  rotate_into_frame(qa, ra, D, ph, L, ztab);
+  rotate_into_frame(qa, ra, D, L, ztab);
   if (!b_in_frame) {
-    rotate_into_frame(qb, rb, D, ph, L, ztab);
+    rotate_into_frame(qb, rb, D, L, ztab);
   } else {
     for (int k = threadIdx.x; k < nq; k += blockDim.x) {
       const int l = tri_l(k);
@@ -506,7 +515,12 @@ int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const Mo
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-int contract_table_size() { return kZ_TOTAL; }
+// Scalar tables (kZ_TOTAL doubles, rounded up to a 4-double boundary) followed by the
+// recursion coefficients (A, A ab / (l (l-1)), A B, 0) of every (l, a, b), a >= |b|, at
+// index l(l+1)(2l+1)/6 + a^2 + a + b.
+constexpr int kZ_RTAB_OFF = (kZ_TOTAL + 3) / 4 * 4;
+constexpr int kZ_RTAB_N = kZN * (kZN + 1) * (2 * kZN + 1) / 6;
+int contract_table_size() { return kZ_RTAB_OFF + 4 * kZ_RTAB_N; }
 
 void contract_tables(double* t) {
   for (int k = 0; k < kZ_TOTAL; ++k) t[k] = 0.0;
@@ -531,6 +545,24 @@ void contract_tables(double* t) {
       t[kZ_SQC + l * 2 * kZN + l + b] = (double)sqrtl(fact[2 * l] / (fact[l + b] * fact[l - b]));
   }
   for (int k = 0; k < 2 * kZN; ++k) t[kZ_FACT + k] = (double)fact[k];
+  for (int l = 0; l < kZN; ++l)
+    for (int a = 0; a <= l; ++a)
+      for (int b = -a; b <= a; ++b) {
+        double* c = t + kZ_RTAB_OFF + 4 * (l * (l + 1) * (2 * l + 1) / 6 + a * a + a + b);
+        if (l <= a) continue;  // seeds, no step
+        const int ab = b < 0 ? -b : b;
+        const long double A = (long double)(l * (2 * l - 1)) /
+                              (sqrtl((long double)(l * l - a * a)) * sqrtl((long double)(l * l - ab * ab)));
+        const long double ill = l >= 2 ? 1.0L / (long double)(l * (l - 1)) : 0.0L;
+        long double B = 0.0L;
+        if (l - 2 >= a)
+          B = sqrtl((long double)((l - 1) * (l - 1) - a * a)) * sqrtl((long double)((l - 1) * (l - 1) - ab * ab)) /
+              (long double)((l - 1) * (2 * l - 1));
+        c[0] = (double)A;
+        c[1] = (double)(A * (long double)(a * b) * ill);
+        c[2] = (double)(A * B);
+        c[3] = 0.0;
+      }
 }
 
 int direct_blocks(long long na) { return (int)((na + kDirectThreads - 1) / kDirectThreads); }
