@@ -62,6 +62,26 @@ def workload():
     return s, atoms, cfg
 
 
+def captured_traffic(kernel_profile, sources):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel sources are unchanged
+    since that capture (their hash is recorded in the summary); else None."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", kernel_profile)).read()
+    except OSError:
+        return None
+    h = hashlib.sha256()
+    for src in sources:
+        h.update(open(os.path.join(ROOT, "paper_0704_1672_gb300", "csrc", src), "rb").read())
+    fields = dict(line.split(":", 1) for line in text.splitlines() if line.startswith(("source_sha256_16:", "traffic_bytes_per_launch:")))
+    if fields.get("source_sha256_16", "").split()[0:1] != [h.hexdigest()[:16]]:
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch"].strip())
+    except (KeyError, ValueError):
+        return None
+
+
 def moment_instr_per_atom(L):
     """Algorithmic FP32-pipe instructions per atom-moment at order L (3 per real component + 12)."""
     return 3 * (L + 1) ** 2 + 12
@@ -267,8 +287,11 @@ def run_ours(args, rank, world, dist):
     mom_launch_ms = phase_ms["moments"] / max(1, launches["moments"])
     instr = atoms_per_step * moment_instr_per_atom(L) / max(1, launches["moments"] / args.steps)
     achieved = instr / (mom_launch_ms * 1e-3) / 1e12
+    traffic = captured_traffic("k_moments_pes_scan_L20.md", ["moments_kernel.cuh", "tcm_internal.h"]) \
+        if (L == 20 and prec == tcm.TCM_MIXED) else None
     roofline = {"bound": "alu", "kernel": f"k_moments<float,{L}>", "achieved": achieved, "peak": peak_tinstr,
-                "unit": "T FP32-pipe lane-instr/s", "frac": achieved / peak_tinstr, "traffic": None,
+                "unit": "T FP32-pipe lane-instr/s", "frac": achieved / peak_tinstr, "traffic": traffic,
+                "traffic_unit": "DRAM bytes per launch (ncu, profiles/k_moments_pes_scan_L20.md)",
                 "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz (max SM clock of measured)",
                 "algorithmic_instr_per_atom": moment_instr_per_atom(L)}
     phases = {p: phase_ms[p] / args.steps for p in phase_ms}
