@@ -1,0 +1,122 @@
+"""GPU parity at the full sizes of the larger workloads, through the batched C ABI call, with
+the oracle on sampled items (tolerances in tcm_testlib)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_0704_1672_gb300 import synth
+from tcm_testlib import TOL_FP64, TOL_MIX_E, energy_error, energy_error_vs_e, oracle_moments_threaded
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tcm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0704_1672_gb300 import build
+    build.build()
+    from paper_0704_1672_gb300 import tcm as t
+    torch.cuda.set_device(0)
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(tcm):
+    c = tcm.Context(lmax_cap=24)
+    yield c
+    c.close()
+
+
+def f32(a):
+    return a.astype(np.float32).astype(np.float64)
+
+
+def check_items(sysA, sysB, rot, R0, L, E, sample, mixed=True):
+    worst = 0.0
+    for k in sample:
+        A, B = f32(sysA(k)), f32(sysB(k))
+        cA, _ = oracle.center_radius(A)
+        cB, _ = oracle.center_radius(B)
+        QA = oracle_moments_threaded(A, cA, L[k])
+        QB = oracle_moments_threaded(B, cB, L[k], rot=rot[k])
+        Eo = oracle.tcm_energy(L[k], QA, QB, R0[k])
+        err = energy_error(float(E[k]), Eo, oracle.tcm_blocks(L[k], QA, QB, R0[k]), mixed=mixed)
+        print(f"item {k}: L={L[k]} N=({len(A)},{len(B)}) error {err:.3e} of the condition scale, "
+              f"{energy_error_vs_e(float(E[k]), Eo):.3e} of |E|")
+        worst = max(worst, err)
+    return worst
+
+
+def test_uneven_batch_full_size(ctx, tcm):
+    """4,096 uneven pairs (N log-uniform in [100, 1e5], L in {8, 12, 16, 24}) in one batched call."""
+    b = synth.uneven_batch()
+    T = [(torch.tensor(s, dtype=torch.float32, device="cuda"), None, None) for s in b.systems]
+    E, st = ctx.tcm_energy_batch(T, b.pair_a, b.pair_b, b.L, b.R0, rotB=b.rotB, precision=tcm.TCM_MIXED)
+    torch.cuda.synchronize()
+    assert torch.all(st == tcm.TCM_OK)
+    E = E.cpu().numpy()
+    assert np.all(np.isfinite(E))
+    n = np.array([len(s) for s in b.systems])
+    sizes = n[b.pair_a] + n[b.pair_b]
+    # sample: each L, small and large systems
+    sample = []
+    for L in (8, 12, 16, 24):
+        idx = np.where(b.L == L)[0]
+        sample += [int(idx[np.argmin(sizes[idx])]), int(idx[np.argmax(sizes[idx])])]
+    worst = check_items(lambda k: b.systems[b.pair_a[k]], lambda k: b.systems[b.pair_b[k]], b.rotB, b.R0, b.L, E, sample)
+    assert worst < TOL_MIX_E, worst
+    # the same items alone give bit-identical energies
+    for k in sample[:4]:
+        E1, _ = ctx.tcm_energy_batch(T, [b.pair_a[k]], [b.pair_b[k]], [b.L[k]], b.R0[k:k + 1], rotB=b.rotB[k:k + 1],
+                                     precision=tcm.TCM_MIXED)
+        torch.cuda.synchronize()
+        assert float(E1[0]) == E[k]
+
+
+def test_large_assembly_full_size(ctx, tcm):
+    """1e6-charge shell against a 5e4-atom ligand, 10,000 orientations at Lmax = 24, B's moments
+    recomputed per orientation."""
+    a = synth.large_assembly()
+    A = torch.tensor(a.A, dtype=torch.float32, device="cuda")
+    B = torch.tensor(a.B, dtype=torch.float32, device="cuda")
+    k = len(a.R0)
+    E, st = ctx.tcm_energy_batch([(A, None, None), (B, None, None)], np.zeros(k, int), np.ones(k, int),
+                                 np.full(k, a.L), a.R0, rotB=a.rotB, precision=tcm.TCM_MIXED)
+    torch.cuda.synchronize()
+    assert torch.all(st == tcm.TCM_OK)
+    E = E.cpu().numpy()
+    L = np.full(k, a.L)
+    Af, Bf = f32(a.A), f32(a.B)
+    cA, _ = oracle.center_radius(Af)
+    cB, _ = oracle.center_radius(Bf)
+    QA = oracle_moments_threaded(Af, cA, a.L)
+    worst = 0.0
+    for kk in (0, 4321, 9999):
+        QB = oracle_moments_threaded(Bf, cB, a.L, rot=a.rotB[kk])
+        Eo = oracle.tcm_energy(a.L, QA, QB, a.R0[kk])
+        err = energy_error(float(E[kk]), Eo, oracle.tcm_blocks(a.L, QA, QB, a.R0[kk]), mixed=True)
+        print(f"orientation {kk}: error {err:.3e} of the condition scale, {energy_error_vs_e(float(E[kk]), Eo):.3e} of |E|")
+        worst = max(worst, err)
+    assert worst < TOL_MIX_E, worst
+
+
+def test_uneven_batch_fp64_subset(ctx, tcm):
+    """The double path through the same batched call on a slice of the uneven workload."""
+    b = synth.uneven_batch(n_pairs=64, seed=31)
+    T = [(torch.tensor(s, dtype=torch.float64, device="cuda"), None, None) for s in b.systems]
+    E, st = ctx.tcm_energy_batch(T, b.pair_a, b.pair_b, b.L, b.R0, rotB=b.rotB, precision=tcm.TCM_FP64)
+    torch.cuda.synchronize()
+    assert torch.all(st == tcm.TCM_OK)
+    E = E.cpu().numpy()
+    worst = 0.0
+    for k in range(0, 64, 9):
+        A, B = b.systems[b.pair_a[k]], b.systems[b.pair_b[k]]
+        cA, _ = oracle.center_radius(A)
+        cB, _ = oracle.center_radius(B)
+        QA = oracle_moments_threaded(A, cA, b.L[k])
+        QB = oracle_moments_threaded(B, cB, b.L[k], rot=b.rotB[k])
+        Eo = oracle.tcm_energy(b.L[k], QA, QB, b.R0[k])
+        worst = max(worst, energy_error(float(E[k]), Eo, oracle.tcm_blocks(b.L[k], QA, QB, b.R0[k])))
+    assert worst < TOL_FP64, worst
