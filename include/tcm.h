@@ -86,6 +86,12 @@ typedef struct {
                          positions (unit masses) is used */
   double center[3];
   double radius;    /* a = max_i |x_i - c| (any a' >= a is also accepted); < 0: computed */
+  const double* moments; /* optional device cache: packed moments about center (from tcm_moments,
+                            lmax moments_lmax); batches use it for every unrotated side with
+                            lmax <= moments_lmax instead of recomputing; requires has_center and
+                            radius >= 0; NULL = none */
+  int32_t moments_lmax;
+  int32_t pad_;
 } tcm_system;
 
 /* Moments of one system (output of tcm_moments, input of tcm_energy). */
@@ -173,6 +179,7 @@ int tcm_energy(tcm_ctx_t ctx, const tcm_moments_t* A, const tcm_moments_t* B, co
  * on the device (step a1) without a host round trip.
  *   E:      device, n_items doubles (NaN for an item that does not converge)
  *   status: device, n_items int32 (TCM_OK or TCM_ENOTCONV), or NULL
+ * Systems that carry a moment cache (tcm_system.moments) reuse it for their unrotated sides.
  * Returns TCM_ENOTCONV at once if a host-known radius already violates Eq. (mainCond).
  * Asynchronous; results are ready when the context stream reaches this point.
  * Each item's result does not depend on the other items in the batch. */

@@ -99,7 +99,19 @@ struct Regs {
   T g0, p0;             // column 0: H_j, H_j-1
   P2<T> g[NC], p[NC];   // columns m >= 1
   T dr, di;             // running diagonal power u^m
+  T q00, q00e;          // float kernels: Q_00 = sum q as an error-free (sum, error) pair
 };
+
+// Q_00 is the total charge: for a neutral system it is a tiny difference of large partial
+// sums, and a charged partner multiplies its error by its own charge.  The float kernels
+// therefore accumulate it with Knuth's two-sum (the rounding error of every addition goes
+// to q00e) and reduce it across the warp in double.
+__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
+  const float t = s + x;
+  const float bb = t - s;
+  e += (s - (t - bb)) + (x - bb);
+  s = t;
+}
 
 // Column m at degree l: advance its recurrence and accumulate qr * H.
 template <typename T, int L, int M0, int M1, int l, int m>
@@ -120,7 +132,10 @@ __device__ __forceinline__ void col_step(Regs<T, L, M0, M1>& s, T ux, T uy, P2<T
         s.p0 = s.g0;
         s.g0 = n;
       }
-      s.acc0[l] = fmaT(qq.x, s.g0, s.acc0[l]);
+      if constexpr (jj == 0 && sizeof(T) == 4)
+        two_sum_acc(s.q00, s.q00e, qq.x);  // G_00 = 1
+      else
+        s.acc0[l] = fmaT(qq.x, s.g0, s.acc0[l]);
     } else {
       if constexpr (jj == 0) {
         if constexpr (m > M0) {
@@ -270,6 +285,12 @@ __device__ __forceinline__ void warp_reduce_store(const Regs<T, L, M0, M1>& s, T
     const int r = lane + 32 * rr;
     if (r < NACC) out[r] = (double)row_sum32(wb + r * S);
   }
+  if constexpr (M0 == 0 && sizeof(T) == 4) {  // slot 0 is Q_00: exact lane pairs summed in double
+    double v = (double)s.q00 + (double)s.q00e;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) out[0] = v;
+  }
   __syncwarp();
 }
 
@@ -322,6 +343,7 @@ __device__ __forceinline__ void run_chunk(const MomTile& tile, const MomJob* __r
   const void* xyzq = job.xyzq;
   const int dtype = job.dtype;
   R s;
+  s.q00 = s.q00e = (T)0;
 #pragma unroll
   for (int k = 0; k < R::N0; ++k) s.acc0[k] = (T)0;
 #pragma unroll

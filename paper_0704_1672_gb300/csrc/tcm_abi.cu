@@ -196,6 +196,12 @@ int check_system(const tcm_system* s, const char* what) {
   if (s->n > 0 && !aligned16(s->xyzq)) return set_err(TCM_EINVAL, "%s: coordinates must be 16-byte aligned", what);
   if (s->has_center && !(std::isfinite(s->center[0]) && std::isfinite(s->center[1]) && std::isfinite(s->center[2])))
     return set_err(TCM_EINVAL, "%s: non-finite centre", what);
+  if (s->moments) {
+    if (!s->has_center || !(s->radius >= 0.0))
+      return set_err(TCM_EINVAL, "%s: a moment cache needs the centre and radius it was taken with", what);
+    if (s->moments_lmax < 0 || s->moments_lmax > TCM_LMAX_MAX || !aligned16(s->moments))
+      return set_err(TCM_EINVAL, "%s: bad moment cache (lmax or alignment)", what);
+  }
   return TCM_OK;
 }
 
@@ -674,7 +680,20 @@ int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int6
   int next_id = 0;
   size_t moff = 0;
   std::vector<size_t> job_moff;
+  std::vector<MomJob> cached;  // unrotated sides served from a system's moment cache
+  std::map<int, int> cached_of;
   auto get_job = [&](int sys, int L, int rot_item, const double* rot) {
+    if (rot_item < 0 && systems[sys].moments && L <= systems[sys].moments_lmax) {
+      auto c = cached_of.find(sys);
+      if (c != cached_of.end()) return -2 - c->second;
+      MomJob j{};
+      j.L = systems[sys].moments_lmax;
+      j.geom = sys;
+      j.out = const_cast<double*>(systems[sys].moments);
+      cached.push_back(j);
+      cached_of[sys] = (int)cached.size() - 1;
+      return -2 - ((int)cached.size() - 1);
+    }
     JobKey key{sys, L, rot_item};
     auto itr = job_of.find(key);
     if (itr != job_of.end()) return itr->second;
@@ -718,6 +737,14 @@ int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int6
   TRY(dev_ensure(c, c->moms, std::max<size_t>(moff, 1) * sizeof(double)));
   for (size_t ji = 0; ji < P.jobs.size(); ++ji) P.jobs[ji].out = static_cast<double*>(c->moms.p) + job_moff[ji];
   build_tiles(precision, P);
+  // cached sides follow the computed jobs in the descriptor array (not finalised)
+  const int n_computed = (int)P.jobs.size();
+  for (auto& d : pd) {
+    if (d.jobA <= -2) d.jobA = n_computed + (-2 - d.jobA);
+    if (d.jobB <= -2) d.jobB = n_computed + (-2 - d.jobB);
+  }
+  std::vector<MomJob> all_jobs = P.jobs;
+  all_jobs.insert(all_jobs.end(), cached.begin(), cached.end());
   int Lmax_items = 0;
   for (int64_t k = 0; k < n_items; ++k) Lmax_items = std::max(Lmax_items, (int)items[k].lmax);
   std::vector<GeomJob> gjobs;
@@ -726,7 +753,7 @@ int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int6
   std::vector<SysGeom> geoms(std::max(n_systems, 1));
   for (int s = 0; s < n_systems; ++s) geoms[s] = host_geom(systems[s]);
   Packer pk;
-  const size_t o_geo = pk.add(geoms), o_job = pk.add(P.jobs), o_tile = pk.add(P.tiles), o_gj = pk.add(gjobs),
+  const size_t o_geo = pk.add(geoms), o_job = pk.add(all_jobs), o_tile = pk.add(P.tiles), o_gj = pk.add(gjobs),
                o_gt = pk.add(gtiles), o_it = pk.add(pd);
   char* base = nullptr;
   TRY(upload(c, pk, &base));

@@ -34,7 +34,8 @@ class TcmError(RuntimeError):
 
 class tcm_system(ctypes.Structure):
     _fields_ = [("xyzq", ctypes.c_void_p), ("n", ctypes.c_int64), ("dtype", ctypes.c_int32),
-                ("has_center", ctypes.c_int32), ("center", ctypes.c_double * 3), ("radius", ctypes.c_double)]
+                ("has_center", ctypes.c_int32), ("center", ctypes.c_double * 3), ("radius", ctypes.c_double),
+                ("moments", ctypes.c_void_p), ("moments_lmax", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class tcm_moments_t(ctypes.Structure):
@@ -97,8 +98,11 @@ def _dptr(arr):
     return arr.ctypes.data_as(ctypes.c_void_p)
 
 
-def make_system(xyzq: torch.Tensor, center=None, radius=None) -> tcm_system:
-    """Descriptor of one device-resident system: (N, 4) float32 or float64 records (x, y, z, q)."""
+def make_system(xyzq: torch.Tensor, center=None, radius=None, moments: "MomentSet | None" = None) -> tcm_system:
+    """Descriptor of one device-resident system: (N, 4) float32 or float64 records (x, y, z, q).
+
+    ``moments`` (from tcm_moments about the same centre) is a device cache that batches use for the
+    system's unrotated sides."""
     if not isinstance(xyzq, torch.Tensor) or not xyzq.is_cuda:
         raise TcmError(TCM_EINVAL, "coordinates must be a CUDA tensor")
     if xyzq.dim() != 2 or xyzq.shape[1] != 4 or not xyzq.is_contiguous():
@@ -118,6 +122,9 @@ def make_system(xyzq: torch.Tensor, center=None, radius=None) -> tcm_system:
         for k in range(3):
             s.center[k] = float(center[k])
     s.radius = -1.0 if radius is None else float(radius)
+    if moments is not None:
+        s.moments = moments.q.data_ptr()
+        s.moments_lmax = moments.lmax
     return s
 
 

@@ -53,7 +53,7 @@ def test_context_create_fails_cleanly_without_gpu(libpath):
 
 def test_struct_layouts_match_header():
     from paper_0704_1672_gb300 import tcm
-    assert ctypes.sizeof(tcm.tcm_system) == 8 + 8 + 4 + 4 + 24 + 8
+    assert ctypes.sizeof(tcm.tcm_system) == 8 + 8 + 4 + 4 + 24 + 8 + 8 + 4 + 4
     assert ctypes.sizeof(tcm.tcm_moments_t) == 8 + 4 + 4 + 24 + 8
     assert ctypes.sizeof(tcm.tcm_pair_item) == 16 + 72 + 24
     assert tcm.PAIR_ITEM_DTYPE.itemsize == ctypes.sizeof(tcm.tcm_pair_item)
