@@ -307,6 +307,8 @@ __device__ __forceinline__ void atom_loop(Regs<T, L, M0, M1>& s, const Rec* __re
     if (i + 32 < i1) nxt = load_rec(xyzq, i + 32);
     T d0, d1, d2, q, ux, uy, cz, rho;
     centre<T>(cur, xf, cd, d0, d1, d2, q);
+    if constexpr (M0 == 0 && sizeof(T) == 4 && sizeof(Rec) == 32)
+      s.q00e += (T)(cur.b.y - (double)q);  // double input: keep the charge's rounding remainder in Q_00
     setup<T>(d0, d1, d2, xf, ux, uy, cz, rho);
     const P2<T> cc = pair<T>(cz, cz), rr = pair<T>(rho, rho), qq = pair<T>(q, q);
     if constexpr (M0 == 0) {
