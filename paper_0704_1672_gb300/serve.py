@@ -318,6 +318,29 @@ def make_requests(stream, seconds=None):
     return reqs
 
 
+def plain_fp64(ex, reqs):
+    """The same requests one at a time through the single-request FP64 calls (tcm_moments per
+    side and orientation, tcm_energy), no batching; returns (energies/s, atom-moments/s)."""
+    tcm, torch = ex.tcm, ex.torch
+    ctx = tcm.Context(lmax_cap=24)
+    n_e = 0
+    atoms = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs:
+        da, db = ex.descr[r.a], ex.descr[r.b]
+        ma = ctx.tcm_moments(ex.coords[r.a], r.L, precision=tcm.TCM_FP64, center=da.center, radius=da.radius)
+        for k in range(r.n):
+            mb = ctx.tcm_moments(ex.coords[r.b], r.L, precision=tcm.TCM_FP64, rot=r.rot[k], center=db.center,
+                                 radius=db.radius)
+            ctx.tcm_energy(ma, mb, r.R0[k], r.L)
+        n_e += r.n
+        atoms += ex.natoms[r.a] + r.n * ex.natoms[r.b]
+    dt = time.perf_counter() - t0
+    ctx.close()
+    return n_e / dt, atoms / dt
+
+
 def main():
     p = argparse.ArgumentParser(description="serve a Poisson stream of TCM scan requests on one GPU")
     p.add_argument("--seconds", type=float, default=10.0)
@@ -326,6 +349,7 @@ def main():
     p.add_argument("--max-items", type=int, default=2048)
     p.add_argument("--quota", type=int, default=256)
     p.add_argument("--budget-gb", type=float, default=4.0)
+    p.add_argument("--plain-fp64", type=int, default=100, help="requests timed through the plain FP64 path")
     args = p.parse_args()
     from . import synth
     st = synth.serve_stream(n_pool=args.pool, rate=args.rate, seconds=args.seconds)
@@ -338,6 +362,12 @@ def main():
     m["atom_moments_per_s"] = atom_moments / max(m["seconds"], 1e-12)
     m["workload"] = st.name
     m["offered_requests_per_s"] = args.rate
+    m["precision"] = "mixed (float moments, double contraction)"
+    if args.plain_fp64 > 0:
+        sample = make_requests(st)[:args.plain_fp64]
+        e_s, a_s = plain_fp64(ex, sample)
+        m["plain_fp64_gpu"] = {"energies_per_s": e_s, "atom_moments_per_s": a_s, "requests": len(sample),
+                               "how": "one request at a time: tcm_moments (FP64) per side and orientation + tcm_energy"}
     print(json.dumps(m))
 
 
