@@ -296,6 +296,25 @@ def run_ours(args, rank, world, dist):
                 "algorithmic_instr_per_atom": moment_instr_per_atom(L)}
     phases = {p: phase_ms[p] / args.steps for p in phase_ms}
 
+    # the same steps with the library's default launch mode, a replayed CUDA graph of the launch
+    # sequence (phase timing off: no events between the kernels)
+    g_steps = min(args.steps, 500)
+    for _ in range(3):
+        flush.zero_()
+        step()
+    evg = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(g_steps)]
+    torch.cuda.synchronize()
+    for i in range(g_steps):
+        flush.zero_()
+        evg[i][0].record(stream)
+        step()
+        evg[i][1].record(stream)
+    torch.cuda.synchronize()
+    g_ms = float(sum(a.elapsed_time(b) for a, b in evg)) / g_steps
+    g_cap, g_launch = ctx.tcm_ctx_graph_stats()
+    graph_replay = {"ms_per_step": g_ms, "value": world * atoms_per_step / (g_ms * 1e-3), "unit": UNIT,
+                    "steps": g_steps, "graph_captures": g_cap, "graph_launches": g_launch}
+
     # end to end through the C ABI with host buffers: H2D of the coordinates, D2H of the energies
     e2e = None
     if args.e2e_steps > 0:
@@ -349,7 +368,8 @@ def run_ours(args, rank, world, dist):
                 "step_latency_ms": {"p50": p50, "p99": p99},
                 "phase_ms_per_step": phases, "gpu_launches": int(sum(launches.values())),
                 "gpu_launches_per_step": {p: launches[p] / args.steps for p in launches},
-                "roofline": roofline, "clocks": ck, "e2e": e2e, "fp64_plain_gpu": fp64_plain,
+                "roofline": roofline, "clocks": ck, "e2e": e2e, "graph_replay": graph_replay,
+                "fp64_plain_gpu": fp64_plain,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()

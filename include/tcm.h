@@ -142,6 +142,17 @@ typedef enum {
  * atom count, its Lmax and this setting.  Used by the autotuner. */
 int tcm_ctx_set_tiling(tcm_ctx_t ctx, int precision, int atoms_per_lane);
 
+/* CUDA-graph replay of tcm_energy_batch (on by default).  When two calls in a row have the
+ * same launch shapes and buffers (item count, job and tile counts per degree, output pointers),
+ * the second captures its launch sequence into a graph and later calls with that shape replay
+ * it instead of launching kernel by kernel; the descriptors are still uploaded per call, so
+ * the orientations, pairs and systems may change.  Calls of another shape launch directly.
+ * Off while phase timing is on. */
+int tcm_ctx_set_graphs(tcm_ctx_t ctx, int enable);
+
+/* Number of graph captures and graph launches so far (either pointer may be NULL). */
+int tcm_ctx_graph_stats(tcm_ctx_t ctx, int64_t* captures, int64_t* launches);
+
 /* Enable (1) or disable (0) phase timing: the context then records a CUDA event pair on
  * its stream around every phase it queues.  Off by default. */
 int tcm_ctx_set_profiling(tcm_ctx_t ctx, int enable);

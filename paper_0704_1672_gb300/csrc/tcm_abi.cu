@@ -104,6 +104,12 @@ struct tcm_ctx {
   std::vector<Mark> marks;
   std::vector<cudaEvent_t> ev_pool;
   int64_t launches[TCM_NPHASES] = {};
+  // CUDA-graph replay of the batched launch sequence
+  bool graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<long long> gkey, gkey_seen;
+  int64_t graph_captures = 0, graph_launches = 0;
 };
 
 namespace {
@@ -266,12 +272,17 @@ void build_tiles(int precision, Plan& P) {
 }
 
 // Queue the moment pass (step a2/a3) for every job of the plan.
-int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, const MomTile* d_tiles,
-                const SysGeom* d_geoms) {
-  const int kmax = moments_kmax(precision);
-  TRY(dev_ensure(c, c->partials, (size_t)std::max(P.n_tile_ids, 1) * kmax * sizeof(double)));
+int ensure_moment_buffers(tcm_ctx* c, int precision, const Plan& P) {
+  TRY(dev_ensure(c, c->partials, (size_t)std::max(P.n_tile_ids, 1) * moments_kmax(precision) * sizeof(double)));
   TRY(dev_ensure(c, c->counters, 64 * sizeof(int)));
-  TRY_CUDA(cudaMemsetAsync(c->counters.p, 0, 64 * sizeof(int), c->stream));
+  return TCM_OK;
+}
+
+int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, const MomTile* d_tiles,
+                const SysGeom* d_geoms, cudaStream_t st) {
+  const int kmax = moments_kmax(precision);
+  TRY(ensure_moment_buffers(c, precision, P));
+  TRY_CUDA(cudaMemsetAsync(c->counters.p, 0, 64 * sizeof(int), st));
   int* counters = static_cast<int*>(c->counters.p);
   double* parts = static_cast<double*>(c->partials.p);
   int ngroups = 0;
@@ -282,13 +293,13 @@ int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, 
       const int b = P.tile_begin[L], e = P.tile_begin[L + 1];
       if (e == b) continue;
       const int grid = std::min((e - b + kThreads / 32 - 1) / (kThreads / 32), 2 * c->num_sms);  // warp tiles
-      TRY_LAUNCH(launch_moments(precision, L, d_jobs, d_tiles + b, e - b, counters + L, d_geoms, parts, grid, c->stream));
+      TRY_LAUNCH(launch_moments(precision, L, d_jobs, d_tiles + b, e - b, counters + L, d_geoms, parts, grid, st));
     }
   }
   {
     PhaseScope ps(c, TCM_PHASE_FINALIZE, 1);
     TRY_LAUNCH(launch_finalize(d_jobs, (int)P.jobs.size(), parts, d_geoms, c->d_cmap[precision == TCM_FP64 ? 0 : 1],
-                               c->d_cmap_off, c->d_ftab, kmax, c->stream));
+                               c->d_cmap_off, c->d_ftab, kmax, st));
   }
   return TCM_OK;
 }
@@ -417,6 +428,8 @@ void free_ctx(tcm_ctx* c) {
     cudaEventDestroy(m.b);
   }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
 
@@ -461,6 +474,10 @@ int tcm_ctx_create(tcm_ctx_t* out, int lmax_cap, void* cuda_stream) {
       rc = set_err(TCM_ENOMEM, "tcm_ctx_create: cudaHostAlloc failed");
       break;
     }
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      c->cap_stream = nullptr;  // graphs unavailable; calls launch directly
+    }
   } while (0);
   if (rc != TCM_OK) {
     free_ctx(c);
@@ -485,6 +502,19 @@ int tcm_ctx_set_tiling(tcm_ctx_t c, int precision, int atoms_per_lane) {
   if (atoms_per_lane < 1 || atoms_per_lane > 4096)
     return set_err(TCM_EINVAL, "tcm_ctx_set_tiling: atoms_per_lane outside [1, 4096]");
   c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1] = atoms_per_lane;
+  return TCM_OK;
+}
+
+int tcm_ctx_set_graphs(tcm_ctx_t c, int enable) {
+  TRY(check_ctx(c));
+  c->graphs = enable != 0;
+  return TCM_OK;
+}
+
+int tcm_ctx_graph_stats(tcm_ctx_t c, int64_t* captures, int64_t* launches) {
+  TRY(check_ctx(c));
+  if (captures) *captures = c->graph_captures;
+  if (launches) *launches = c->graph_launches;
   return TCM_OK;
 }
 
@@ -589,7 +619,7 @@ int tcm_moments(tcm_ctx_t c, const tcm_system* s, const double* rot, int lmax, i
                            static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
   }
   TRY(run_moments(c, precision, P, reinterpret_cast<MomJob*>(base + o_job), reinterpret_cast<MomTile*>(base + o_tile),
-                  d_geo));
+                  d_geo, c->stream));
   out->lmax = lmax;
   if (!gjobs.empty()) {
     TRY_CUDA(cudaMemcpyAsync(c->pinned_small, d_geo, sizeof(SysGeom), cudaMemcpyDeviceToHost, c->stream));
@@ -755,24 +785,78 @@ int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int6
   Packer pk;
   const size_t o_geo = pk.add(geoms), o_job = pk.add(all_jobs), o_tile = pk.add(P.tiles), o_gj = pk.add(gjobs),
                o_gt = pk.add(gtiles), o_it = pk.add(pd);
+  // every buffer the launches touch is sized before anything is queued (no reallocation
+  // may happen while a graph is being captured)
+  if (!gjobs.empty())
+    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
+  TRY(ensure_moment_buffers(c, precision, P));
   char* base = nullptr;
   TRY(upload(c, pk, &base));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
-  if (!gjobs.empty()) {
-    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
-    TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
-    PhaseScope ps(c, TCM_PHASE_GEOM, 2);
-    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
-                           reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
-                           static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
-  }
   const MomJob* d_jobs = reinterpret_cast<MomJob*>(base + o_job);
-  TRY(run_moments(c, precision, P, d_jobs, reinterpret_cast<MomTile*>(base + o_tile), d_geo));
-  {
+  int ngroups = 0;
+  for (int L = 0; L <= kLmaxMax; ++L) ngroups += P.tile_begin[L + 1] > P.tile_begin[L];
+  auto enqueue = [&](cudaStream_t st) -> int {
+    if (!gjobs.empty()) {
+      TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), st));
+      PhaseScope ps(c, TCM_PHASE_GEOM, 2);
+      TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
+                             reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
+                             static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, st));
+    }
+    TRY(run_moments(c, precision, P, d_jobs, reinterpret_cast<MomTile*>(base + o_tile), d_geo, st));
     PhaseScope ps(c, TCM_PHASE_CONTRACT, 1);
     TRY_LAUNCH(launch_contract(reinterpret_cast<PairDesc*>(base + o_it), (int)n_items, Lmax_items, d_jobs, d_geo,
-                               c->d_ztab, E, status, c->stream));
+                               c->d_ztab, E, status, st));
+    return TCM_OK;
+  };
+  if (!c->graphs || c->prof || !c->cap_stream) return enqueue(c->stream);
+  // Replay a captured graph of the launch sequence when this call has the same shape and
+  // buffers as the captured one (only the uploaded descriptor contents differ).
+  std::vector<long long> key = {precision, ngt, (long long)gjobs.size(), (long long)P.jobs.size(), P.n_tile_ids,
+                                (long long)n_items, Lmax_items, (long long)o_geo, (long long)o_job, (long long)o_tile,
+                                (long long)o_gj, (long long)o_gt, (long long)o_it, (long long)(uintptr_t)base,
+                                (long long)(uintptr_t)c->gpart.p, (long long)(uintptr_t)c->partials.p,
+                                (long long)(uintptr_t)c->counters.p, (long long)(uintptr_t)E,
+                                (long long)(uintptr_t)status};
+  for (int L = 0; L <= kLmaxMax + 1; ++L) key.push_back(P.tile_begin[L]);
+  if (!c->gexec || key != c->gkey) {
+    // capture only a shape seen twice in a row: a stream of changing shapes (continuous
+    // batching) launches directly instead of paying a capture per call
+    if (key != c->gkey_seen) {
+      c->gkey_seen = key;
+      return enqueue(c->stream);
+    }
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    TRY_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t saved[TCM_NPHASES] = {c->launches[0], c->launches[1], c->launches[2], c->launches[3], c->launches[4]};
+    const int rc = enqueue(c->cap_stream);
+    for (int k = 0; k < TCM_NPHASES; ++k) c->launches[k] = saved[k];
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &g);
+    if (rc != TCM_OK || ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return rc != TCM_OK ? rc : set_err(TCM_ECUDA, "graph capture failed: %s", cudaGetErrorString(ec));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      c->gexec = nullptr;
+      return set_err(TCM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+    }
+    c->gkey = key;
+    ++c->graph_captures;
   }
+  TRY_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+  ++c->graph_launches;
+  c->launches[TCM_PHASE_GEOM] += gjobs.empty() ? 0 : 2;
+  c->launches[TCM_PHASE_MOMENTS] += ngroups;
+  c->launches[TCM_PHASE_FINALIZE] += 1;
+  c->launches[TCM_PHASE_CONTRACT] += 1;
   return TCM_OK;
 }
 

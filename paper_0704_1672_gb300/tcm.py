@@ -77,10 +77,12 @@ def lib():
         L.tcm_moments_noalloc.argtypes = [ctypes.POINTER(tcm_system), P, i32, i32, P, P, P]
         L.tcm_ctx_set_profiling.argtypes = [P, i32]
         L.tcm_ctx_set_tiling.argtypes = [P, i32, i32]
+        L.tcm_ctx_set_graphs.argtypes = [P, i32]
+        L.tcm_ctx_graph_stats.argtypes = [P, P, P]
         L.tcm_ctx_read_profile.argtypes = [P, P, P]
         for name in ("tcm_ctx_create", "tcm_ctx_set_stream", "tcm_prepare", "tcm_moments", "tcm_energy",
                      "tcm_energy_batch", "tcm_direct", "tcm_ctx_set_profiling", "tcm_ctx_read_profile",
-                     "tcm_moments_noalloc", "tcm_ctx_set_tiling"):
+                     "tcm_moments_noalloc", "tcm_ctx_set_tiling", "tcm_ctx_set_graphs", "tcm_ctx_graph_stats"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -175,6 +177,14 @@ class Context:
 
     def tcm_ctx_set_tiling(self, precision, atoms_per_lane):
         _check(lib().tcm_ctx_set_tiling(self._h, int(precision), int(atoms_per_lane)))
+
+    def tcm_ctx_set_graphs(self, enable: bool):
+        _check(lib().tcm_ctx_set_graphs(self._h, 1 if enable else 0))
+
+    def tcm_ctx_graph_stats(self):
+        cap, lau = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().tcm_ctx_graph_stats(self._h, ctypes.byref(cap), ctypes.byref(lau)))
+        return cap.value, lau.value
 
     def tcm_ctx_set_profiling(self, enable: bool):
         _check(lib().tcm_ctx_set_profiling(self._h, 1 if enable else 0))
