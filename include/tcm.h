@@ -136,11 +136,20 @@ typedef enum {
   TCM_NPHASES = 5
 } tcm_phase;
 
-/* Tiling of the moment pass for one precision: each warp of the moment kernels takes
- * tiles of 32 x atoms_per_lane atoms (1..4096; defaults 64 for TCM_MIXED, 32 for
+/* Tiling of the moment pass for one precision, every degree: each warp of the moment kernels
+ * takes tiles of 32 x atoms_per_lane atoms (1..4096; defaults 64 for TCM_MIXED, 32 for
  * TCM_FP64).  A system's tiles, and so the rounding of its moments, depend only on its
  * atom count, its Lmax and this setting.  Used by the autotuner. */
 int tcm_ctx_set_tiling(tcm_ctx_t ctx, int precision, int atoms_per_lane);
+
+/* The moment-pass tiling of one degree lmax in [0, TCM_LMAX_MAX] at one precision: atoms per
+ * lane of a warp tile (as above) and the resident CTAs per SM, in [1, 2], that the persistent
+ * grid of that degree's launch is sized for (grid = min(work, ctas_per_sm x SMs) CTAs of four
+ * warps).  Defaults: 32 (FP64) or 64 (mixed) atoms per lane, 2 CTAs per SM.  Set by the
+ * autotuner; results stay within the stated tolerances for any setting (only the summation
+ * order of the atom sums changes).  tcm_ctx_get_tiling_l reads the current setting. */
+int tcm_ctx_set_tiling_l(tcm_ctx_t ctx, int precision, int lmax, int atoms_per_lane, int ctas_per_sm);
+int tcm_ctx_get_tiling_l(tcm_ctx_t ctx, int precision, int lmax, int* atoms_per_lane, int* ctas_per_sm);
 
 /* CUDA-graph replay of tcm_energy_batch (on by default).  When two calls in a row have the
  * same launch shapes and buffers (item count, job and tile counts per degree, output pointers),

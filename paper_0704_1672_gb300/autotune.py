@@ -1,0 +1,155 @@
+"""Autotuner of the moment pass (steps a2/a3): per degree L and precision it chooses the warp-tile
+size (atoms per lane) and the persistent grid's CTAs per SM by timing the caller's own batch.
+
+For every degree present in the batch, the items of that degree (at most ``max_items_per_l`` of
+them) form a sub-batch; each candidate setting is applied with ``tcm_ctx_set_tiling_l``, the
+sub-batch is run once untimed and ``reps`` times timed, and the median time of the moment phase
+(the library's CUDA-event phase profile: the moment kernels of that degree, nothing else) is
+kept.  The fastest candidate is applied to the context and returned.  Results can be saved to a
+JSON file keyed by device name, library build and precision, and loaded into a later context.
+
+The tiling changes only the order in which atom contributions are summed, so every candidate
+gives results within the stated tolerances; the choice is made on time alone.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+DEFAULT_ATOMS_PER_LANE = (16, 32, 64, 128, 256)
+DEFAULT_CTAS_PER_SM = (1, 2)
+
+
+@dataclass
+class TuneResult:
+    precision: int
+    best: dict = field(default_factory=dict)     # L -> (atoms_per_lane, ctas_per_sm)
+    timings: dict = field(default_factory=dict)  # L -> {(atoms_per_lane, ctas_per_sm): median ms}
+
+    def to_json(self):
+        return {"precision": int(self.precision),
+                "best": {str(L): list(v) for L, v in self.best.items()},
+                "timings": {str(L): {f"{a}x{c}": ms for (a, c), ms in t.items()} for L, t in self.timings.items()}}
+
+    @classmethod
+    def from_json(cls, d):
+        r = cls(int(d["precision"]))
+        r.best = {int(L): (int(v[0]), int(v[1])) for L, v in d["best"].items()}
+        r.timings = {int(L): {tuple(int(x) for x in k.split("x")): float(ms) for k, ms in t.items()}
+                     for L, t in d.get("timings", {}).items()}
+        return r
+
+
+def choose(timings: dict):
+    """The candidate with the smallest median time (ties: the first in candidate order)."""
+    best, best_ms = None, float("inf")
+    for cand, ms in timings.items():
+        if ms < best_ms:
+            best, best_ms = cand, ms
+    return best
+
+
+def degree_groups(lmax, max_items_per_l):
+    """Indices of the items of each degree, at most max_items_per_l per degree (evenly strided)."""
+    lmax = np.asarray(lmax)
+    out = {}
+    for L in sorted(set(int(x) for x in lmax)):
+        idx = np.nonzero(lmax == L)[0]
+        if len(idx) > max_items_per_l:
+            idx = idx[np.linspace(0, len(idx) - 1, max_items_per_l).round().astype(int)]
+        out[L] = idx
+    return out
+
+
+def moment_phase_ms(ctx, run, reps):
+    """Median over reps of the moment-phase time of run() (one untimed call first)."""
+    run()
+    ctx.tcm_ctx_set_profiling(True)
+    ctx.tcm_ctx_read_profile()
+    times = []
+    for _ in range(reps):
+        run()
+        ms, _ = ctx.tcm_ctx_read_profile()
+        times.append(ms["moments"])
+    ctx.tcm_ctx_set_profiling(False)
+    return float(np.median(times))
+
+
+def tune(ctx, systems, a, b, lmax, R0, rotB=None, precision=None, atoms_per_lane=DEFAULT_ATOMS_PER_LANE,
+         ctas_per_sm=DEFAULT_CTAS_PER_SM, reps=3, max_items_per_l=512, measure=None) -> TuneResult:
+    """Tune the moment pass on this batch (arguments as for ``Context.tcm_energy_batch``).
+
+    ``measure(L, run) -> ms`` replaces the CUDA-event measurement (used by the host-side tests).
+    The best setting per degree is applied to ``ctx`` before returning.
+    """
+    from . import tcm
+    if precision is None:
+        precision = tcm.TCM_MIXED
+    a, b, lmax = np.asarray(a), np.asarray(b), np.asarray(lmax)
+    R0 = np.asarray(R0, dtype=np.float64).reshape(-1, 3)
+    rot = None if rotB is None else np.asarray(rotB, dtype=np.float64).reshape(-1, 3, 3)
+    res = TuneResult(int(precision))
+    for L, idx in degree_groups(lmax, max_items_per_l).items():
+        pb = tcm.pack_batch(systems, a[idx], b[idx], lmax[idx], R0[idx], None if rot is None else rot[idx])
+
+        def run(pb=pb):
+            ctx.tcm_energy_batch_packed(pb, precision)
+
+        default = ctx.tcm_ctx_get_tiling_l(precision, L)
+        t = {}
+        for apl in atoms_per_lane:
+            for cps in ctas_per_sm:
+                ctx.tcm_ctx_set_tiling_l(precision, L, apl, cps)
+                t[(apl, cps)] = measure(L, run) if measure else moment_phase_ms(ctx, run, reps)
+        best = choose(t) or default
+        ctx.tcm_ctx_set_tiling_l(precision, L, *best)
+        res.best[L] = best
+        res.timings[L] = t
+    return res
+
+
+def apply(ctx, result: TuneResult):
+    for L, (apl, cps) in result.best.items():
+        ctx.tcm_ctx_set_tiling_l(result.precision, L, apl, cps)
+
+
+def library_key(lib_path=None, device_name=None):
+    """Device name and a hash of the built library: a tuning is reused only on the same pair."""
+    if lib_path is None:
+        from . import tcm
+        lib_path = tcm.LIB_PATH
+    h = hashlib.sha256(open(lib_path, "rb").read()).hexdigest()[:16]
+    if device_name is None:
+        import torch
+        device_name = torch.cuda.get_device_name()
+    return f"{device_name}|{h}"
+
+
+def save(path, result: TuneResult, key: str):
+    data = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+    data.setdefault(key, {})[str(result.precision)] = result.to_json()
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def load(ctx, path, precision, key: str):
+    """Apply a saved tuning for (key, precision) if there is one; returns it or None."""
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        data = json.load(f)
+    d = data.get(key, {}).get(str(int(precision)))
+    if d is None:
+        return None
+    r = TuneResult.from_json(d)
+    apply(ctx, r)
+    return r

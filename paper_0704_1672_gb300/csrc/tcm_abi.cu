@@ -94,7 +94,10 @@ struct tcm_ctx {
   Stage stage[kStages];
   int stage_next = 0;
   void* pinned_small = nullptr;  // 256 B for small device->host reads
-  int atoms_per_thread[2] = {32, 64};  // atoms per lane of a warp tile, [TCM_FP64, TCM_MIXED]
+  // moment-pass tiling per [TCM_FP64, TCM_MIXED][L]: atoms per lane of a warp tile, and the
+  // resident CTAs per SM the persistent grid is sized for
+  int atoms_per_thread[2][kLmaxMax + 1];
+  int ctas_per_sm[2][kLmaxMax + 1];
   // phase profiling
   bool prof = false;
   struct Mark {
@@ -230,7 +233,7 @@ struct Plan {
 
 void plan_job(tcm_ctx* c, int precision, MomJob& j, int& next_id) {
   const int nch = moments_nchunks(precision, j.L);
-  const long long per_tile = 32LL * c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1];  // one warp
+  const long long per_tile = 32LL * c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1][j.L];  // one warp
   long long tpc = (j.n + per_tile - 1) / per_tile;
   if (tpc < 1) tpc = 1;
   j.tiles_per_chunk = (int)tpc;
@@ -292,7 +295,8 @@ int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, 
     for (int L = 0; L <= kLmaxMax; ++L) {
       const int b = P.tile_begin[L], e = P.tile_begin[L + 1];
       if (e == b) continue;
-      const int grid = std::min((e - b + kThreads / 32 - 1) / (kThreads / 32), 2 * c->num_sms);  // warp tiles
+      const int cps = c->ctas_per_sm[precision == TCM_FP64 ? 0 : 1][L];
+      const int grid = std::min((e - b + kThreads / 32 - 1) / (kThreads / 32), cps * c->num_sms);  // warp tiles
       TRY_LAUNCH(launch_moments(precision, L, d_jobs, d_tiles + b, e - b, counters + L, d_geoms, parts, grid, st));
     }
   }
@@ -454,6 +458,11 @@ int tcm_ctx_create(tcm_ctx_t* out, int lmax_cap, void* cuda_stream) {
     return set_err(TCM_EINVAL, "tcm_ctx_create: lmax_cap %d outside [0, %d]", lmax_cap, TCM_LMAX_MAX);
   tcm_ctx* c = new (std::nothrow) tcm_ctx();
   if (!c) return set_err(TCM_ENOMEM, "tcm_ctx_create: host allocation failed");
+  for (int L = 0; L <= kLmaxMax; ++L) {
+    c->atoms_per_thread[0][L] = 32;  // FP64: 32 atoms per lane (1,024 per warp tile)
+    c->atoms_per_thread[1][L] = 64;  // mixed: 64 atoms per lane (2,048 per warp tile)
+    c->ctas_per_sm[0][L] = c->ctas_per_sm[1][L] = TCM_MOMENT_CTAS_PER_SM;
+  }
   int rc = TCM_OK;
   do {
     if (cudaGetDevice(&c->device) != cudaSuccess ||
@@ -501,7 +510,29 @@ int tcm_ctx_set_tiling(tcm_ctx_t c, int precision, int atoms_per_lane) {
   if (precision != TCM_FP64 && precision != TCM_MIXED) return set_err(TCM_EINVAL, "tcm_ctx_set_tiling: bad precision");
   if (atoms_per_lane < 1 || atoms_per_lane > 4096)
     return set_err(TCM_EINVAL, "tcm_ctx_set_tiling: atoms_per_lane outside [1, 4096]");
-  c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1] = atoms_per_lane;
+  for (int L = 0; L <= kLmaxMax; ++L) c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1][L] = atoms_per_lane;
+  return TCM_OK;
+}
+
+int tcm_ctx_set_tiling_l(tcm_ctx_t c, int precision, int lmax, int atoms_per_lane, int ctas_per_sm) {
+  TRY(check_ctx(c));
+  if (precision != TCM_FP64 && precision != TCM_MIXED) return set_err(TCM_EINVAL, "tcm_ctx_set_tiling_l: bad precision");
+  if (lmax < 0 || lmax > kLmaxMax) return set_err(TCM_EINVAL, "tcm_ctx_set_tiling_l: lmax outside [0, %d]", kLmaxMax);
+  if (atoms_per_lane < 1 || atoms_per_lane > 4096)
+    return set_err(TCM_EINVAL, "tcm_ctx_set_tiling_l: atoms_per_lane outside [1, 4096]");
+  if (ctas_per_sm < 1 || ctas_per_sm > TCM_MOMENT_CTAS_PER_SM)
+    return set_err(TCM_EINVAL, "tcm_ctx_set_tiling_l: ctas_per_sm outside [1, %d]", TCM_MOMENT_CTAS_PER_SM);
+  c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1][lmax] = atoms_per_lane;
+  c->ctas_per_sm[precision == TCM_FP64 ? 0 : 1][lmax] = ctas_per_sm;
+  return TCM_OK;
+}
+
+int tcm_ctx_get_tiling_l(tcm_ctx_t c, int precision, int lmax, int* atoms_per_lane, int* ctas_per_sm) {
+  TRY(check_ctx(c));
+  if (precision != TCM_FP64 && precision != TCM_MIXED) return set_err(TCM_EINVAL, "tcm_ctx_get_tiling_l: bad precision");
+  if (lmax < 0 || lmax > kLmaxMax) return set_err(TCM_EINVAL, "tcm_ctx_get_tiling_l: lmax outside [0, %d]", kLmaxMax);
+  if (atoms_per_lane) *atoms_per_lane = c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1][lmax];
+  if (ctas_per_sm) *ctas_per_sm = c->ctas_per_sm[precision == TCM_FP64 ? 0 : 1][lmax];
   return TCM_OK;
 }
 

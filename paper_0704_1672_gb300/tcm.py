@@ -77,12 +77,15 @@ def lib():
         L.tcm_moments_noalloc.argtypes = [ctypes.POINTER(tcm_system), P, i32, i32, P, P, P]
         L.tcm_ctx_set_profiling.argtypes = [P, i32]
         L.tcm_ctx_set_tiling.argtypes = [P, i32, i32]
+        L.tcm_ctx_set_tiling_l.argtypes = [P, i32, i32, i32, i32]
+        L.tcm_ctx_get_tiling_l.argtypes = [P, i32, i32, P, P]
         L.tcm_ctx_set_graphs.argtypes = [P, i32]
         L.tcm_ctx_graph_stats.argtypes = [P, P, P]
         L.tcm_ctx_read_profile.argtypes = [P, P, P]
         for name in ("tcm_ctx_create", "tcm_ctx_set_stream", "tcm_prepare", "tcm_moments", "tcm_energy",
                      "tcm_energy_batch", "tcm_direct", "tcm_ctx_set_profiling", "tcm_ctx_read_profile",
-                     "tcm_moments_noalloc", "tcm_ctx_set_tiling", "tcm_ctx_set_graphs", "tcm_ctx_graph_stats"):
+                     "tcm_moments_noalloc", "tcm_ctx_set_tiling", "tcm_ctx_set_graphs", "tcm_ctx_graph_stats",
+                     "tcm_ctx_set_tiling_l", "tcm_ctx_get_tiling_l"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -177,6 +180,14 @@ class Context:
 
     def tcm_ctx_set_tiling(self, precision, atoms_per_lane):
         _check(lib().tcm_ctx_set_tiling(self._h, int(precision), int(atoms_per_lane)))
+
+    def tcm_ctx_set_tiling_l(self, precision, lmax, atoms_per_lane, ctas_per_sm):
+        _check(lib().tcm_ctx_set_tiling_l(self._h, int(precision), int(lmax), int(atoms_per_lane), int(ctas_per_sm)))
+
+    def tcm_ctx_get_tiling_l(self, precision, lmax):
+        apl, cps = ctypes.c_int(), ctypes.c_int()
+        _check(lib().tcm_ctx_get_tiling_l(self._h, int(precision), int(lmax), ctypes.byref(apl), ctypes.byref(cps)))
+        return apl.value, cps.value
 
     def tcm_ctx_set_graphs(self, enable: bool):
         _check(lib().tcm_ctx_set_graphs(self._h, 1 if enable else 0))

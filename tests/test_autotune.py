@@ -1,0 +1,125 @@
+"""The autotuner's host logic on CPU: degree grouping, the sweep over candidates, choosing and
+applying the fastest, and the JSON cache, with a fake context whose 'time' is a known function
+of the tiling (no GPU).  The GPU test tunes a real uneven batch and checks the results still
+match the oracle."""
+import numpy as np
+import pytest
+
+from paper_0704_1672_gb300 import autotune, synth, tcm
+
+
+class FakeCtx:
+    def __init__(self):
+        self.tiling = {}
+        self.calls = 0
+
+    def tcm_ctx_get_tiling_l(self, precision, L):
+        return self.tiling.get((precision, L), (64, 2))
+
+    def tcm_ctx_set_tiling_l(self, precision, L, apl, cps):
+        self.tiling[(precision, L)] = (apl, cps)
+
+    def tcm_energy_batch_packed(self, pb, precision, E=None, status=None):
+        self.calls += 1
+
+
+def cost(L, apl, cps):
+    # a made-up landscape with its minimum at apl = 2**(3 + L // 8), cps = 1 for odd L
+    return abs(np.log2(apl) - (3 + L // 8)) + (0.5 if (cps == 1) != (L % 2 == 1) else 0.0) + 0.01 * L
+
+
+def systems(n):
+    return [tcm.tcm_system() for _ in range(n)]
+
+
+def test_degree_groups_cap_and_cover():
+    lmax = np.array([8, 12, 8, 24, 8, 12, 8])
+    g = autotune.degree_groups(lmax, 2)
+    assert sorted(g) == [8, 12, 24]
+    assert list(g[12]) == [1, 5] and list(g[24]) == [3]
+    assert len(g[8]) == 2 and set(g[8]) <= {0, 2, 4, 6} and g[8][0] == 0 and g[8][-1] == 6
+
+
+def test_tune_picks_the_fastest_per_degree_and_applies_it():
+    ctx = FakeCtx()
+    rng = np.random.default_rng(0)
+    k = 40
+    L = rng.choice([8, 13, 16, 24], k)
+    R0 = rng.normal(size=(k, 3)) + 50.0
+
+    def measure(Ldeg, run):
+        run()
+        apl, cps = ctx.tcm_ctx_get_tiling_l(tcm.TCM_MIXED, Ldeg)
+        return cost(Ldeg, apl, cps)
+
+    res = autotune.tune(ctx, systems(3), rng.integers(0, 3, k), rng.integers(0, 3, k), L, R0,
+                        rotB=synth.random_rotations(rng, k), precision=tcm.TCM_MIXED, measure=measure)
+    for Ldeg in (8, 13, 16, 24):
+        grid = {(a, c): cost(Ldeg, a, c) for a in autotune.DEFAULT_ATOMS_PER_LANE for c in autotune.DEFAULT_CTAS_PER_SM}
+        want = min(grid, key=grid.get)
+        assert res.best[Ldeg] == want
+        assert ctx.tiling[(tcm.TCM_MIXED, Ldeg)] == want
+        assert res.timings[Ldeg] == pytest.approx(grid)
+    assert ctx.calls == 4 * len(autotune.DEFAULT_ATOMS_PER_LANE) * len(autotune.DEFAULT_CTAS_PER_SM)
+
+
+def test_cache_round_trip(tmp_path):
+    ctx = FakeCtx()
+    r = autotune.TuneResult(tcm.TCM_MIXED, best={8: (32, 1), 24: (128, 2)},
+                            timings={8: {(32, 1): 0.1, (64, 2): 0.2}, 24: {(128, 2): 0.3}})
+    path = str(tmp_path / "tiling.json")
+    autotune.save(path, r, "GB300|abc")
+    autotune.save(path, autotune.TuneResult(tcm.TCM_FP64, best={8: (16, 2)}), "GB300|abc")
+    assert autotune.load(ctx, path, tcm.TCM_MIXED, "other|key") is None
+    got = autotune.load(ctx, path, tcm.TCM_MIXED, "GB300|abc")
+    assert got.best == r.best and got.timings == r.timings
+    assert ctx.tiling == {(tcm.TCM_MIXED, 8): (32, 1), (tcm.TCM_MIXED, 24): (128, 2)}
+    assert autotune.load(ctx, path, tcm.TCM_FP64, "GB300|abc").best == {8: (16, 2)}
+
+
+@pytest.mark.gpu
+def test_tuned_uneven_batch_matches_oracle():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_0704_1672_gb300 import build
+    build.build()
+    from tcm_testlib import TOL_MIX_E, energy_error, oracle_moments_threaded
+    rng = np.random.default_rng(31)
+    sizes = [150, 900, 4000, 15000, 30000]
+    sys_np, T, rad = [], [], []
+    for n in sizes:
+        xyz = synth.random_walk(rng, n, 1.9 * n ** (1 / 3))
+        S = synth.pack(xyz, synth.charges_normal_net_zero(rng, n))
+        sys_np.append(S)
+        T.append((torch.tensor(S, dtype=torch.float32, device="cuda"), None, None))
+        rad.append(oracle.center_radius(S.astype(np.float32).astype(np.float64))[1])
+    k = 48
+    a = rng.integers(0, len(sizes), k)
+    b = rng.integers(0, len(sizes), k)
+    L = rng.choice([8, 12, 16, 24], k)
+    R0 = np.array([synth.unit_vectors(rng, 1)[0] * rng.uniform(1.2, 3.0) * (rad[i] + rad[j]) for i, j in zip(a, b)])
+    rot = synth.random_rotations(rng, k)
+    ctx = tcm.Context(lmax_cap=24)
+    try:
+        res = autotune.tune(ctx, T, a, b, L, R0, rotB=rot, reps=2)
+        assert sorted(res.best) == [8, 12, 16, 24]
+        for Ldeg, best in res.best.items():
+            assert ctx.tcm_ctx_get_tiling_l(tcm.TCM_MIXED, Ldeg) == best
+            assert res.timings[Ldeg][best] == min(res.timings[Ldeg].values())
+        print({Ldeg: (best, round(res.timings[Ldeg][best], 4)) for Ldeg, best in res.best.items()})
+        E, st = ctx.tcm_energy_batch(T, a, b, L, R0, rotB=rot)
+        torch.cuda.synchronize()
+        assert bool(torch.all(st == 0))
+        for i in range(0, k, 7):
+            A = sys_np[a[i]].astype(np.float32).astype(np.float64)
+            B = sys_np[b[i]].astype(np.float32).astype(np.float64)
+            cA, cB = oracle.center_radius(A)[0], oracle.center_radius(B)[0]
+            QA = oracle_moments_threaded(A, cA, int(L[i]))
+            QB = oracle_moments_threaded(B, cB, int(L[i]), rot=rot[i])
+            Eo = oracle.tcm_energy(int(L[i]), QA, QB, R0[i])
+            err = energy_error(float(E[i]), Eo, oracle.tcm_blocks(int(L[i]), QA, QB, R0[i]), mixed=True)
+            assert err < TOL_MIX_E, (i, err)
+    finally:
+        ctx.close()

@@ -51,9 +51,18 @@ def check_items(sysA, sysB, rot, R0, L, E, sample, mixed=True):
 
 def test_uneven_batch_full_size(ctx, tcm):
     """4,096 uneven pairs (N log-uniform in [100, 1e5], L in {8, 12, 16, 24}) in one batched call."""
+    from paper_0704_1672_gb300 import autotune
     b = synth.uneven_batch()
     T = [(torch.tensor(s, dtype=torch.float32, device="cuda"), None, None) for s in b.systems]
-    E, st = ctx.tcm_energy_batch(T, b.pair_a, b.pair_b, b.L, b.R0, rotB=b.rotB, precision=tcm.TCM_MIXED)
+    pb = tcm.pack_batch(T, b.pair_a, b.pair_b, b.L, b.R0, rotB=b.rotB)
+    t_default = autotune.moment_phase_ms(ctx, lambda: ctx.tcm_energy_batch_packed(pb, tcm.TCM_MIXED), 3)
+    # autotuned tiling (per degree, on a sample of the batch's own items), then the full batch
+    res = autotune.tune(ctx, T, b.pair_a, b.pair_b, b.L, b.R0, rotB=b.rotB, precision=tcm.TCM_MIXED,
+                        reps=2, max_items_per_l=256)
+    t_tuned = autotune.moment_phase_ms(ctx, lambda: ctx.tcm_energy_batch_packed(pb, tcm.TCM_MIXED), 3)
+    print(f"moment phase of the full batch: default tiling {t_default:.3f} ms, tuned {t_tuned:.3f} ms; "
+          f"choice per L {res.best}")
+    E, st = ctx.tcm_energy_batch_packed(pb, tcm.TCM_MIXED)
     torch.cuda.synchronize()
     assert torch.all(st == tcm.TCM_OK)
     E = E.cpu().numpy()
@@ -73,6 +82,8 @@ def test_uneven_batch_full_size(ctx, tcm):
                                      precision=tcm.TCM_MIXED)
         torch.cuda.synchronize()
         assert float(E1[0]) == E[k]
+    for L in res.best:  # later tests in this module run with the default tiling
+        ctx.tcm_ctx_set_tiling_l(tcm.TCM_MIXED, L, 64, 2)
 
 
 def test_large_assembly_full_size(ctx, tcm):
