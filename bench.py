@@ -315,6 +315,33 @@ def run_ours(args, rank, world, dist):
     graph_replay = {"ms_per_step": g_ms, "value": world * atoms_per_step / (g_ms * 1e-3), "unit": UNIT,
                     "steps": g_steps, "graph_captures": g_cap, "graph_launches": g_launch}
 
+    # the same orientations with B's moments rotated from a cache (Wigner rotation in the
+    # contraction kernel) instead of recomputed from its atoms: moments of A and B once, outside
+    # the timed steps
+    rc_ctx = tcm.Context(lmax_cap=L, stream=stream)
+    mA = rc_ctx.tcm_moments(A, L, precision=prec)
+    mB = rc_ctx.tcm_moments(B, L, precision=prec)
+    rc_pb = tcm.pack_batch([tcm.make_system(A, mA.center, mA.radius, moments=mA),
+                            tcm.make_system(B, mB.center, mB.radius, moments=mB)],
+                           np.zeros(k, int), np.ones(k, int), np.full(k, L), s.R0, rotB=s.rotB)
+    rc_ctx.tcm_ctx_set_rotate_cached(True)
+    for _ in range(3):
+        flush.zero_()
+        rc_ctx.tcm_energy_batch_packed(rc_pb, prec, E, st)
+    evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(g_steps)]
+    torch.cuda.synchronize()
+    for i in range(g_steps):
+        flush.zero_()
+        evr[i][0].record(stream)
+        rc_ctx.tcm_energy_batch_packed(rc_pb, prec, E, st)
+        evr[i][1].record(stream)
+    torch.cuda.synchronize()
+    rc_ms = float(sum(a.elapsed_time(b) for a, b in evr)) / g_steps
+    rotate_cached = {"ms_per_step": rc_ms, "energies_per_s": world * k / (rc_ms * 1e-3), "steps": g_steps,
+                     "how": "B's cached moments rotated per orientation by Wigner matrices in the contraction "
+                            "kernel (O(L^3)); no atom pass per step"}
+    rc_ctx.close()
+
     # end to end through the C ABI with host buffers: H2D of the coordinates, D2H of the energies
     e2e = None
     if args.e2e_steps > 0:
@@ -369,6 +396,7 @@ def run_ours(args, rank, world, dist):
                 "phase_ms_per_step": phases, "gpu_launches": int(sum(launches.values())),
                 "gpu_launches_per_step": {p: launches[p] / args.steps for p in launches},
                 "roofline": roofline, "clocks": ck, "e2e": e2e, "graph_replay": graph_replay,
+                "rotate_cached": rotate_cached,
                 "fp64_plain_gpu": fp64_plain,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -192,6 +192,28 @@ int tcm_moments(tcm_ctx_t ctx, const tcm_system* s, const double* rot, int lmax,
 int tcm_energy(tcm_ctx_t ctx, const tcm_moments_t* A, const tcm_moments_t* B, const double* R0,
                int lmax, double* E);
 
+/* Rotation of cached moments (the moments of a system turned about its centre, without its
+ * atoms): for each of the n sets, out[i].q receives the moments, 0 <= l <= out[i].lmax, of the
+ * system whose lab-frame moments are in[i].q after the rotation rot + 9 i (row-major 3x3 host
+ * array) about its centre -- what tcm_moments with that rotation gives, up to rounding, in
+ * O(lmax^3) per set instead of O(atoms x lmax^2).  Each degree l is rotated with its Wigner
+ * matrix D^l (Section II: the solid harmonics of a given l transform among themselves); the
+ * Euler angles are taken from the rotation's quaternion.
+ *   in[i].q, out[i].q: device, packed as tcm_moments_t; out[i].lmax <= in[i].lmax and <= the
+ *   context cap; out[i].q may equal in[i].q (in place), sets must not otherwise overlap.
+ *   out[i].center and out[i].radius are copied from in[i] (a rotation about the centre changes
+ *   neither).
+ * Asynchronous on the context stream. */
+int tcm_rotate_moments(tcm_ctx_t ctx, int64_t n, const tcm_moments_t* in, const double* rot,
+                       tcm_moments_t* out);
+
+/* Rotated sides of tcm_energy_batch from the moment cache (off by default): when on, an item
+ * with has_rot whose system b carries a moment cache with moments_lmax >= the item's lmax
+ * takes B's moments from that cache, rotated inside the contraction kernel by the Wigner
+ * matrices of (frame rotation) x rotB, instead of recomputing them from B's atoms.  The
+ * energies agree with the recomputed ones within the stated tolerances. */
+int tcm_ctx_set_rotate_cached(tcm_ctx_t ctx, int enable);
+
 /* Batched Eq. (multipole) + Eq. (Formula): for every item, the moments of system a
  * and of system b (rotated by rotB about its centre) at the item's lmax and their
  * two-center energy at R0.  Moment sets shared by several items (same system, lmax
@@ -199,7 +221,8 @@ int tcm_energy(tcm_ctx_t ctx, const tcm_moments_t* A, const tcm_moments_t* B, co
  * on the device (step a1) without a host round trip.
  *   E:      device, n_items doubles (NaN for an item that does not converge)
  *   status: device, n_items int32 (TCM_OK or TCM_ENOTCONV), or NULL
- * Systems that carry a moment cache (tcm_system.moments) reuse it for their unrotated sides.
+ * Systems that carry a moment cache (tcm_system.moments) reuse it for their unrotated sides
+ * (and for rotated sides too under tcm_ctx_set_rotate_cached).
  * Returns TCM_ENOTCONV at once if a host-known radius already violates Eq. (mainCond).
  * Asynchronous; results are ready when the context stream reaches this point.
  * Each item's result does not depend on the other items in the batch. */

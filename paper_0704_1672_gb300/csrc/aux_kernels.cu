@@ -7,7 +7,7 @@
 //   a6  exact pairwise Coulomb sum in double                             (Eq. (Coulomb))
 #include <cuda_runtime.h>
 
-#include "tcm_internal.h"
+#include "contract.h"
 
 namespace tcm {
 
@@ -242,9 +242,12 @@ __device__ __forceinline__ double dget(const double* D, int offl, int mp, int m)
   return flip(D[offl + mp * mp - mp - m], m - mp);  // a = -mp, b = -m
 }
 
-// Rotate moments already multiplied by e^{-i m alpha} (m >= 0, complex in qin) into the
-// frame: writes qout, normalised to Qhat.  Threads stride over (l, m).
-__device__ void rotate_into_frame(const double2* qin, double2* qout, const double* D, int L, const double* ztab) {
+// Rotate moments already multiplied by e^{-i m alpha} (m >= 0, complex in qin) by R_y(-beta)
+// with the half table D of beta; optionally multiply the result by phg[m] = e^{-i m gamma}
+// (the last factor of R_z(-gamma) R_y(-beta) R_z(-alpha)) and normalise to Qhat.  Threads
+// stride over (l, m).
+__device__ void rotate_d(const double2* qin, double2* qout, const double* D, int L, const double* ztab,
+                         const double2* phg, bool hat) {
   const int nq = (L + 1) * (L + 2) / 2;
   for (int k = threadIdx.x; k < nq; k += blockDim.x) {
     const int l = tri_l(k);
@@ -259,112 +262,27 @@ __device__ void rotate_into_frame(const double2* qin, double2* qout, const doubl
       re = fma(d1 + d2, q[mp].x, re);
       im = fma(d1 - d2, q[mp].y, im);
     }
-    const double f = ztab[kZ_ISF + l * kZN + m];
-    qout[k] = make_double2(re * f, im * f);
+    if (hat) {
+      const double f = ztab[kZ_ISF + l * kZN + m];
+      re *= f;
+      im *= f;
+    }
+    if (phg && m > 0) {
+      const double2 e = phg[m];
+      const double r2 = e.x * re - e.y * im;
+      im = e.x * im + e.y * re;
+      re = r2;
+    }
+    qout[k] = make_double2(re, im);
   }
 }
 
-__global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* __restrict__ items,
-                                                               const MomJob* __restrict__ jobs,
-                                                               const SysGeom* __restrict__ geoms,
-                                                               const double* __restrict__ ztab,
-                                                               double* __restrict__ E, int32_t* __restrict__ status) {
-  const double* rtab = ztab + ((kZ_TOTAL + 3) / 4 * 4);  // recursion coefficients, 4 doubles per (l, a, b)
-  extern __shared__ double2 sm2[];
-  __shared__ double sh[32];
-  __shared__ double g_cb, g_ch, g_sh, g_iR;
-  const PairDesc d = items[blockIdx.x];
-  const int L = d.L;
-  const double x = d.R0[0], y = d.R0[1], z = d.R0[2];
-  const double R = sqrt(x * x + y * y + z * z);
-  const double aA = geoms[d.geomA].a, aB = geoms[d.geomB].a;
-  if (!(R > aA + aB)) {  // Eq. (mainCond) violated: the expansion does not converge
-    if (threadIdx.x == 0) {
-      E[blockIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
-      if (status) status[blockIdx.x] = TCM_ENOTCONV;
-    }
-    return;
-  }
-  const int nq = (L + 1) * (L + 2) / 2;
-  const int nd = (L + 1) * (L + 2) * (2 * L + 3) / 6;  // sum of (l+1)^2
-  double2* qa = sm2;           // lab frame, then reused
-  double2* qb = qa + nq;
-  double2* ra = qb + nq;       // Qhat' of A
-  double2* rb = ra + nq;       // Qhat' of B
-  double2* ph = rb + nq;       // e^{-i m alpha}, m <= L
-  double* cp = reinterpret_cast<double*>(ph + (L + 1));  // cos^k(beta/2), k <= 2L
-  double* sp = cp + 2 * L + 1;                             // sin^k(beta/2)
-  double* rp = sp + 2 * L + 1;                             // R^-(k+1), k <= 2L
-  double* D = rp + 2 * L + 1;                              // half Wigner table, nd entries
-  const double* pa = jobs[d.jobA].out;
-  const double* pb = jobs[d.jobB].out;
-  const bool b_in_frame = d.b_in_frame != 0;
-  // geometry of the frame; half angles without cancellation
-  if (threadIdx.x == 0) {
-    const double rho2 = x * x + y * y;
-    double opc, omc;  // 1 + cos b, 1 - cos b
-    if (z >= 0.0) {
-      opc = (R + z) / R;
-      omc = rho2 / (R * (R + z));
-    } else {
-      omc = (R - z) / R;
-      opc = rho2 / (R * (R - z));
-    }
-    g_cb = z / R;
-    g_ch = sqrt(0.5 * opc);
-    g_sh = sqrt(0.5 * omc);
-    g_iR = 1.0 / R;
-  }
-  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
-    const int l = tri_l(k);
-    const int m = k - l * (l + 1) / 2;
-    qa[k] = m == 0 ? make_double2(pa[l * l], 0.0) : make_double2(pa[l * l + 2 * m - 1], pa[l * l + 2 * m]);
-    qb[k] = m == 0 ? make_double2(pb[l * l], 0.0) : make_double2(pb[l * l + 2 * m - 1], pb[l * l + 2 * m]);
-  }
-  __syncthreads();
-  if (threadIdx.x == 32) {  // e^{-i m alpha}
-    const double rho = sqrt(x * x + y * y);
-    const double ca = rho > 0.0 ? x / rho : 1.0, sa = rho > 0.0 ? y / rho : 0.0;
-    double er = 1.0, ei = 0.0;
-    for (int m = 0; m <= L; ++m) {
-      ph[m] = make_double2(er, ei);
-      const double nr = er * ca + ei * sa;
-      ei = ei * ca - er * sa;
-      er = nr;
-    }
-  } else if (threadIdx.x == 64) {
-    double c = 1.0, s = 1.0;
-    for (int k = 0; k <= 2 * L; ++k) {
-      cp[k] = c;
-      sp[k] = s;
-      c *= g_ch;
-      s *= g_sh;
-    }
-  } else if (threadIdx.x == 96) {
-    double r = g_iR;
-    for (int k = 0; k <= 2 * L; ++k) {
-      rp[k] = r;
-      r *= g_iR;
-    }
-  }
-  __syncthreads();
-  // P_lm = e^{-i m alpha} Q_lm, once per (l, m), for the sides that are rotated here
-  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
-    const int l = tri_l(k);
-    const int m = k - l * (l + 1) / 2;
-    if (m == 0) continue;
-    const double2 e = ph[m];
-    double2 v = qa[k];
-    qa[k] = make_double2(e.x * v.x - e.y * v.y, e.x * v.y + e.y * v.x);
-    if (!b_in_frame) {
-      v = qb[k];
-      qb[k] = make_double2(e.x * v.x - e.y * v.y, e.x * v.y + e.y * v.x);
-    }
-  }
-  // Wigner d^l_{ab}, a >= |b|: one thread per (a, b) walks l upward.  The step
-  //   d_l = A (t d_l-1 - B d_l-2),  t = cos(beta) - ab / (l (l-1)),
-  // uses per-(l, a, b) coefficients (A, A ab / (l (l-1)), A B) from rtab.
-  const double cb = g_cb;
+// Wigner d^l_{ab}(beta), a >= |b|, l <= L: one thread per (a, b) walks l upward from the seed
+//   d^a_{ab} = (-1)^(a-b) sqrt(C(2a, a+b)) cos^(a+b)(beta/2) sin^(a-b)(beta/2);
+// the step d_l = A (t d_l-1 - B d_l-2), t = cos(beta) - ab / (l (l-1)), uses per-(l, a, b)
+// coefficients (A, A ab / (l (l-1)), A B) from rtab.  cp/sp hold the powers of cos/sin(beta/2).
+__device__ void wigner_half_table(double* D, const double* cp, const double* sp, double cb, int L,
+                                  const double* ztab, const double* rtab) {
   for (int p = threadIdx.x; p < (L + 1) * (L + 1); p += blockDim.x) {
     int a = (int)sqrtf((float)p);
     while (a * a > p) --a;
@@ -384,17 +302,179 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
       d1 = v;
     }
   }
-  __syncthreads();
-  rotate_into_frame(qa, ra, D, L, ztab);
-  if (!b_in_frame) {
-    rotate_into_frame(qb, rb, D, L, ztab);
+}
+
+// Euler angles of a rotation M = R_z(-gamma) R_y(-beta) R_z(-alpha), beta in [0, pi], through
+// its unit quaternion (largest-component extraction): with q = (w, x, y, z),
+//   cos(beta/2) = |(w, z)|,  sin(beta/2) = |(x, y)|,
+//   e^{i(alpha+gamma)/2} = (w - i z) / cos(beta/2),  e^{i(alpha-gamma)/2} = (-y + i x) / sin(beta/2),
+// which stays accurate near beta = 0 and pi (where only alpha+gamma, resp. alpha-gamma, matters).
+struct Euler {
+  double cb, ch, sh;  // cos(beta), cos(beta/2), sin(beta/2)
+  double2 ea, eg;     // e^{i alpha}, e^{i gamma}
+};
+
+__device__ Euler euler_zyz(const double* M) {
+  const double t = M[0] + M[4] + M[8];
+  double w, x, y, z;
+  if (t > 0.0) {
+    const double s = 2.0 * sqrt(t + 1.0);
+    w = 0.25 * s; x = (M[7] - M[5]) / s; y = (M[2] - M[6]) / s; z = (M[3] - M[1]) / s;
+  } else if (M[0] > M[4] && M[0] > M[8]) {
+    const double s = 2.0 * sqrt(1.0 + M[0] - M[4] - M[8]);
+    w = (M[7] - M[5]) / s; x = 0.25 * s; y = (M[1] + M[3]) / s; z = (M[2] + M[6]) / s;
+  } else if (M[4] > M[8]) {
+    const double s = 2.0 * sqrt(1.0 + M[4] - M[0] - M[8]);
+    w = (M[2] - M[6]) / s; x = (M[1] + M[3]) / s; y = 0.25 * s; z = (M[5] + M[7]) / s;
   } else {
+    const double s = 2.0 * sqrt(1.0 + M[8] - M[0] - M[4]);
+    w = (M[3] - M[1]) / s; x = (M[2] + M[6]) / s; y = (M[5] + M[7]) / s; z = 0.25 * s;
+  }
+  const double n = 1.0 / sqrt(w * w + x * x + y * y + z * z);
+  w *= n; x *= n; y *= n; z *= n;
+  Euler e;
+  e.ch = sqrt(w * w + z * z);
+  e.sh = sqrt(x * x + y * y);
+  e.cb = (e.ch - e.sh) * (e.ch + e.sh);
+  const double2 p = e.ch > 0.0 ? make_double2(w / e.ch, -z / e.ch) : make_double2(1.0, 0.0);
+  const double2 q = e.sh > 0.0 ? make_double2(-y / e.sh, x / e.sh) : make_double2(1.0, 0.0);
+  e.ea = make_double2(p.x * q.x - p.y * q.y, p.x * q.y + p.y * q.x);  // p q
+  e.eg = make_double2(p.x * q.x + p.y * q.y, p.y * q.x - p.x * q.y);  // p conj(q)
+  return e;
+}
+
+__device__ void phase_powers(double2* ph, double2 e, int L) {  // ph[m] = conj(e)^m, m <= L
+  double er = 1.0, ei = 0.0;
+  for (int m = 0; m <= L; ++m) {
+    ph[m] = make_double2(er, ei);
+    const double nr = er * e.x + ei * e.y;
+    ei = ei * e.x - er * e.y;
+    er = nr;
+  }
+}
+
+__device__ void half_angle_powers(double* cp, double* sp, double ch, double sh, int L) {  // k <= 2L
+  double c = 1.0, s = 1.0;
+  for (int k = 0; k <= 2 * L; ++k) {
+    cp[k] = c;
+    sp[k] = s;
+    c *= ch;
+    s *= sh;
+  }
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* __restrict__ items,
+                                                               const MomJob* __restrict__ jobs,
+                                                               const SysGeom* __restrict__ geoms,
+                                                               const double* __restrict__ ztab,
+                                                               double* __restrict__ E, int32_t* __restrict__ status) {
+  const double* rtab = ztab + ((kZ_TOTAL + 3) / 4 * 4);  // recursion coefficients, 4 doubles per (l, a, b)
+  extern __shared__ double2 sm2[];
+  __shared__ double sh[32];
+  __shared__ double g_cb, g_ch, g_sh, g_iR;
+  __shared__ Euler g_eb;
+  const PairDesc d = items[blockIdx.x];
+  const int L = d.L;
+  const double x = d.R0[0], y = d.R0[1], z = d.R0[2];
+  const double R = sqrt(x * x + y * y + z * z);
+  const double aA = geoms[d.geomA].a, aB = geoms[d.geomB].a;
+  if (!(R > aA + aB)) {  // Eq. (mainCond) violated: the expansion does not converge
+    if (threadIdx.x == 0) {
+      E[blockIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
+      if (status) status[blockIdx.x] = TCM_ENOTCONV;
+    }
+    return;
+  }
+  const int nq = (L + 1) * (L + 2) / 2;
+  double2* qa = sm2;           // lab frame, then reused
+  double2* qb = qa + nq;
+  double2* ra = qb + nq;       // Qhat' of A
+  double2* rb = ra + nq;       // Qhat' of B
+  double2* ph = rb + nq;       // e^{-i m alpha}, m <= L
+  double2* pha = ph + (L + 1); // B's own rotation (mode TCM_B_ROTATE): e^{-i m alpha_B}
+  double2* phg = pha + (L + 1);//                                      e^{-i m gamma_B}
+  double* cp = reinterpret_cast<double*>(phg + (L + 1));  // cos^k(beta/2), k <= 2L
+  double* sp = cp + 2 * L + 1;                             // sin^k(beta/2)
+  double* rp = sp + 2 * L + 1;                             // R^-(k+1), k <= 2L
+  double* D = rp + 2 * L + 1;                              // half Wigner table, sum (l+1)^2 entries
+  const double* pa = jobs[d.jobA].out;
+  const double* pb = jobs[d.jobB].out;
+  const int bmode = d.b_mode;
+  // geometry of the frame; half angles without cancellation
+  if (threadIdx.x == 0) {
+    const double rho2 = x * x + y * y;
+    double opc, omc;  // 1 + cos b, 1 - cos b
+    if (z >= 0.0) {
+      opc = (R + z) / R;
+      omc = rho2 / (R * (R + z));
+    } else {
+      omc = (R - z) / R;
+      opc = rho2 / (R * (R - z));
+    }
+    g_cb = z / R;
+    g_ch = sqrt(0.5 * opc);
+    g_sh = sqrt(0.5 * omc);
+    g_iR = 1.0 / R;
+  } else if (threadIdx.x == 128 && bmode == kBRotate) {
+    g_eb = euler_zyz(items[blockIdx.x].Mb);
+  }
+  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+    const int l = tri_l(k);
+    const int m = k - l * (l + 1) / 2;
+    qa[k] = m == 0 ? make_double2(pa[l * l], 0.0) : make_double2(pa[l * l + 2 * m - 1], pa[l * l + 2 * m]);
+    qb[k] = m == 0 ? make_double2(pb[l * l], 0.0) : make_double2(pb[l * l + 2 * m - 1], pb[l * l + 2 * m]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 32) {  // e^{-i m alpha}
+    const double rho = sqrt(x * x + y * y);
+    const double ca = rho > 0.0 ? x / rho : 1.0, sa = rho > 0.0 ? y / rho : 0.0;
+    phase_powers(ph, make_double2(ca, sa), L);
+  } else if (threadIdx.x == 64) {
+    half_angle_powers(cp, sp, g_ch, g_sh, L);
+  } else if (threadIdx.x == 96) {
+    double r = g_iR;
+    for (int k = 0; k <= 2 * L; ++k) {
+      rp[k] = r;
+      r *= g_iR;
+    }
+  } else if (threadIdx.x == 128 && bmode == kBRotate) {
+    phase_powers(pha, g_eb.ea, L);
+  } else if (threadIdx.x == 160 && bmode == kBRotate) {
+    phase_powers(phg, g_eb.eg, L);
+  }
+  __syncthreads();
+  // P_lm = e^{-i m alpha} Q_lm, once per (l, m), for the sides that are rotated here
+  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+    const int l = tri_l(k);
+    const int m = k - l * (l + 1) / 2;
+    if (m == 0) continue;
+    qa[k] = cmul(ph[m], qa[k]);
+    if (bmode == kBLab) qb[k] = cmul(ph[m], qb[k]);
+    else if (bmode == kBRotate) qb[k] = cmul(pha[m], qb[k]);
+  }
+  wigner_half_table(D, cp, sp, g_cb, L, ztab, rtab);
+  __syncthreads();
+  rotate_d(qa, ra, D, L, ztab, nullptr, true);
+  if (bmode == kBLab) {
+    rotate_d(qb, rb, D, L, ztab, nullptr, true);
+  } else if (bmode == kBInFrame) {
     for (int k = threadIdx.x; k < nq; k += blockDim.x) {
       const int l = tri_l(k);
       const int m = k - l * (l + 1) / 2;
       const double f = ztab[kZ_ISF + l * kZN + m];
       rb[k] = make_double2(qb[k].x * f, qb[k].y * f);
     }
+  } else {  // B's cached lab-frame moments by its own rotation M_B = R_z(-gamma) R_y(-beta) R_z(-alpha)
+    __syncthreads();  // every thread is done with the frame's table
+    if (threadIdx.x == 64) half_angle_powers(cp, sp, g_eb.ch, g_eb.sh, L);
+    __syncthreads();
+    wigner_half_table(D, cp, sp, g_eb.cb, L, ztab, rtab);
+    __syncthreads();
+    rotate_d(qb, rb, D, L, ztab, phg, true);
   }
   __syncthreads();
   // z-axis contraction: one thread per (l1, l2)
@@ -414,6 +494,55 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
   if (threadIdx.x == 0) {
     E[blockIdx.x] = acc;
     if (status) status[blockIdx.x] = TCM_OK;
+  }
+}
+
+// Moments of a system rotated by M about its centre, from its lab-frame moments: the Wigner
+// rotation R_z(-gamma) R_y(-beta) R_z(-alpha) = M applied degree by degree (one CTA per set).
+__global__ void __launch_bounds__(kContractThreads) k_rotate_moments(const RotDesc* __restrict__ sets,
+                                                                     const double* __restrict__ ztab) {
+  const double* rtab = ztab + ((kZ_TOTAL + 3) / 4 * 4);
+  extern __shared__ double2 sm2[];
+  __shared__ Euler g_e;
+  const RotDesc d = sets[blockIdx.x];
+  const int L = d.L;
+  const int nq = (L + 1) * (L + 2) / 2;
+  double2* q = sm2;
+  double2* r = q + nq;
+  double2* pha = r + nq;
+  double2* phg = pha + (L + 1);
+  double* cp = reinterpret_cast<double*>(phg + (L + 1));
+  double* sp = cp + 2 * L + 1;
+  double* D = sp + 2 * L + 1;
+  if (threadIdx.x == 0) g_e = euler_zyz(sets[blockIdx.x].M);
+  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+    const int l = tri_l(k);
+    const int m = k - l * (l + 1) / 2;
+    q[k] = m == 0 ? make_double2(d.in[l * l], 0.0) : make_double2(d.in[l * l + 2 * m - 1], d.in[l * l + 2 * m]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) phase_powers(pha, g_e.ea, L);
+  else if (threadIdx.x == 32) phase_powers(phg, g_e.eg, L);
+  else if (threadIdx.x == 64) half_angle_powers(cp, sp, g_e.ch, g_e.sh, L);
+  __syncthreads();
+  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+    const int l = tri_l(k);
+    const int m = k - l * (l + 1) / 2;
+    if (m > 0) q[k] = cmul(pha[m], q[k]);
+  }
+  wigner_half_table(D, cp, sp, g_e.cb, L, ztab, rtab);
+  __syncthreads();
+  rotate_d(q, r, D, L, ztab, phg, false);
+  __syncthreads();
+  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+    const int l = tri_l(k);
+    const int m = k - l * (l + 1) / 2;
+    if (m == 0) {
+      d.out[l * l] = r[k].x;
+    } else {
+      d.out[l * l + 2 * m - 1] = r[k].x;
+      d.out[l * l + 2 * m] = r[k].y;
+    }
   }
 }
 
@@ -486,7 +615,24 @@ __global__ void k_direct_final(const double* __restrict__ part, int nblk, double
 int contract_smem_bytes(int L) {
   const int nq = (L + 1) * (L + 2) / 2;
   const int nd = (L + 1) * (L + 2) * (2 * L + 3) / 6;
-  return (4 * nq + (L + 1)) * (int)sizeof(double2) + (3 * (2 * L + 1) + nd) * (int)sizeof(double);
+  return (4 * nq + 3 * (L + 1)) * (int)sizeof(double2) + (3 * (2 * L + 1) + nd) * (int)sizeof(double);
+}
+
+int rotate_smem_bytes(int L) {
+  const int nq = (L + 1) * (L + 2) / 2;
+  const int nd = (L + 1) * (L + 2) * (2 * L + 3) / 6;
+  return (2 * nq + 2 * (L + 1)) * (int)sizeof(double2) + (2 * (2 * L + 1) + nd) * (int)sizeof(double);
+}
+
+int launch_rotate_moments(const RotDesc* sets, int n_sets, int Lmax_sets, const double* ztab, cudaStream_t s) {
+  if (n_sets <= 0) return 0;
+  const int smem = rotate_smem_bytes(Lmax_sets);
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(k_rotate_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      return -1;
+  }
+  k_rotate_moments<<<n_sets, kContractThreads, smem, s>>>(sets, ztab);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n_gtiles, double* gpart, int* tickets,

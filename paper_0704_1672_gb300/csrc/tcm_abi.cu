@@ -12,7 +12,7 @@
 #include <tuple>
 #include <vector>
 
-#include "tcm_internal.h"
+#include "contract.h"
 
 using namespace tcm;
 
@@ -108,6 +108,7 @@ struct tcm_ctx {
   std::vector<cudaEvent_t> ev_pool;
   int64_t launches[TCM_NPHASES] = {};
   // CUDA-graph replay of the batched launch sequence
+  bool rotate_cached = false;  // rotated B sides from the moment cache by Wigner rotation
   bool graphs = true;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -685,7 +686,7 @@ int tcm_energy(tcm_ctx_t c, const tcm_moments_t* A, const tcm_moments_t* B, cons
   geoms[0].a = A->radius;
   geoms[1].a = B->radius;
   std::vector<PairDesc> items(1);
-  items[0] = PairDesc{0, 1, 0, 1, lmax, 0, {R0[0], R0[1], R0[2]}};
+  items[0] = PairDesc{0, 1, 0, 1, lmax, kBLab, {R0[0], R0[1], R0[2]}, {}};
   Packer pk;
   const size_t o_job = pk.add(jobs), o_geo = pk.add(geoms), o_it = pk.add(items);
   char* base = nullptr;
@@ -701,6 +702,44 @@ int tcm_energy(tcm_ctx_t c, const tcm_moments_t* A, const tcm_moments_t* B, cons
   TRY_CUDA(cudaMemcpyAsync(c->pinned_small, dE, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   TRY_CUDA(cudaStreamSynchronize(c->stream));
   *E = *static_cast<const double*>(c->pinned_small);
+  return TCM_OK;
+}
+
+int tcm_rotate_moments(tcm_ctx_t c, int64_t n, const tcm_moments_t* in, const double* rot, tcm_moments_t* out) {
+  TRY(check_ctx(c));
+  if (n < 0) return set_err(TCM_EINVAL, "tcm_rotate_moments: negative count");
+  if (n == 0) return TCM_OK;
+  if (!in || !rot || !out) return set_err(TCM_EINVAL, "tcm_rotate_moments: null argument");
+  if (n > (1LL << 30)) return set_err(TCM_EINVAL, "tcm_rotate_moments: too many sets");
+  std::vector<RotDesc> sets(n);
+  int Lmax = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!in[i].q || !out[i].q) return set_err(TCM_EINVAL, "tcm_rotate_moments: set %lld has a null moment pointer", (long long)i);
+    if (out[i].lmax < 0 || out[i].lmax > c->lmax_cap || out[i].lmax > in[i].lmax)
+      return set_err(TCM_EINVAL, "tcm_rotate_moments: set %lld: output lmax %d outside [0, min(input lmax %d, cap %d)]",
+                     (long long)i, out[i].lmax, in[i].lmax, c->lmax_cap);
+    for (int k = 0; k < 9; ++k)
+      if (!std::isfinite(rot[9 * i + k])) return set_err(TCM_EINVAL, "tcm_rotate_moments: set %lld: non-finite rotation", (long long)i);
+    sets[i].in = in[i].q;
+    sets[i].out = out[i].q;
+    sets[i].L = out[i].lmax;
+    std::memcpy(sets[i].M, rot + 9 * i, 9 * sizeof(double));
+    Lmax = std::max(Lmax, out[i].lmax);
+    for (int d = 0; d < 3; ++d) out[i].center[d] = in[i].center[d];
+    out[i].radius = in[i].radius;
+  }
+  Packer pk;
+  const size_t o_set = pk.add(sets);
+  char* base = nullptr;
+  TRY(upload(c, pk, &base));
+  PhaseScope ps(c, TCM_PHASE_CONTRACT, 1);
+  TRY_LAUNCH(launch_rotate_moments(reinterpret_cast<RotDesc*>(base + o_set), (int)n, Lmax, c->d_ztab, c->stream));
+  return TCM_OK;
+}
+
+int tcm_ctx_set_rotate_cached(tcm_ctx_t c, int enable) {
+  TRY(check_ctx(c));
+  c->rotate_cached = enable != 0;
   return TCM_OK;
 }
 
@@ -780,6 +819,17 @@ int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int6
     const tcm_pair_item& it = items[k];
     const int ja = get_job(it.a, it.lmax, -1, nullptr);
     int jb;
+    if (it.has_rot && c->rotate_cached && systems[it.b].moments && it.lmax <= systems[it.b].moments_lmax) {
+      // B's cached lab-frame moments, taken into the frame by W rotB inside the contraction
+      double W[9];
+      frame_rotation(it.R0, W);
+      jb = get_job(it.b, it.lmax, -1, nullptr);
+      pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, kBRotate, {it.R0[0], it.R0[1], it.R0[2]}, {}};
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          pd[k].Mb[3 * i + j] = W[3 * i + 0] * it.rotB[0 + j] + W[3 * i + 1] * it.rotB[3 + j] + W[3 * i + 2] * it.rotB[6 + j];
+      continue;
+    }
     if (it.has_rot) {
       // B is moved per item anyway: fold the rotation W that takes R0hat to z into its
       // atom transform, so the contraction receives B's moments already in that frame.
@@ -792,7 +842,7 @@ int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int6
     } else {
       jb = get_job(it.b, it.lmax, -1, nullptr);
     }
-    pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, it.has_rot ? 1 : 0, {it.R0[0], it.R0[1], it.R0[2]}};
+    pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, it.has_rot ? kBInFrame : kBLab, {it.R0[0], it.R0[1], it.R0[2]}, {}};
   }
   P.n_tile_ids = next_id;
   TRY(dev_ensure(c, c->moms, std::max<size_t>(moff, 1) * sizeof(double)));

@@ -141,14 +141,6 @@ struct GeomTile {
   int t;
 };
 
-struct PairDesc {  // one energy: moments of jobA and jobB at lmax L, separation R0
-  int jobA, jobB;
-  int geomA, geomB;
-  int L;
-  int b_in_frame;  // nonzero: jobB's moments are already in the frame where R0hat = z
-  double R0[3];
-};
-
 constexpr int kGeomTileAtoms = 1024;
 
 // ---------------------------------------------------------------------------------
@@ -167,11 +159,7 @@ int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n
                 SysGeom* geoms, cudaStream_t s);
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms,
                     const int2* cmap, const int* cmap_off, const double* ftab, int kmax, cudaStream_t s);
-int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const MomJob* jobs,
-                    const SysGeom* geoms, const double* ztab, double* E, int32_t* status, cudaStream_t s);
-int contract_smem_bytes(int L);
-int contract_table_size();
-void contract_tables(double* t);  // host: fills contract_table_size() doubles
+
 
 // Rotation W = R_y(-beta) R_z(-alpha) taking R0hat to the z axis (row-major).
 __host__ __device__ inline void frame_rotation(const double* R0, double* W) {

@@ -227,7 +227,7 @@ class GpuExecutor:
     """Runs batches through tcm_energy_batch on a CUDA stream; results come back through pinned
     buffers and an event per batch."""
 
-    def __init__(self, systems, lmax_cap=24, precision=None, device=0, ring=4):
+    def __init__(self, systems, lmax_cap=24, precision=None, device=0, ring=4, rotate_cached=False):
         import torch
 
         from . import tcm
@@ -236,6 +236,9 @@ class GpuExecutor:
         self.stream = torch.cuda.Stream()
         self.precision = tcm.TCM_MIXED if precision is None else precision
         self.ctx = tcm.Context(lmax_cap=lmax_cap, stream=self.stream)
+        # rotated sides from the moment cache (Wigner rotation) instead of B's atoms
+        self.rotate_cached = bool(rotate_cached)
+        self.ctx.tcm_ctx_set_rotate_cached(self.rotate_cached)
         self.coords = []
         self.descr = []
         self.cache = []
@@ -298,7 +301,10 @@ class GpuExecutor:
         return sl["Eh"][:k].numpy().copy(), sl["sth"][:k].numpy().copy()
 
     def item_bytes(self, req):
-        """Device bytes of one in-flight item: B's moment set, its tile partials, the energy."""
+        """Device bytes of one in-flight item: B's moment set, its tile partials, the energy (only
+        the descriptor and the energy when B's moments come rotated from the cache)."""
+        if self.rotate_cached:
+            return 128 + 16 + 256
         nch = max(1, ((req.L + 1) ** 2 + 159) // 160)
         tiles = max(1, -(-int(self.natoms[req.b]) // 2048))
         return 8 * (req.L + 1) ** 2 + 8 * 160 * nch * tiles + 16 + 256
@@ -350,19 +356,22 @@ def main():
     p.add_argument("--quota", type=int, default=256)
     p.add_argument("--budget-gb", type=float, default=4.0)
     p.add_argument("--plain-fp64", type=int, default=100, help="requests timed through the plain FP64 path")
+    p.add_argument("--rotate-cached", action="store_true",
+                   help="rotate B's cached moments per orientation instead of recomputing them from its atoms")
     args = p.parse_args()
     from . import synth
     st = synth.serve_stream(n_pool=args.pool, rate=args.rate, seconds=args.seconds)
-    ex = GpuExecutor(st.systems)
+    ex = GpuExecutor(st.systems, rotate_cached=args.rotate_cached)
     eng = Engine(ex, ex.item_bytes, budget_bytes=int(args.budget_gb * (1 << 30)), max_items=args.max_items,
                  quota=args.quota)
     reqs = make_requests(st)
     atom_moments = sum(r.n * ex.natoms[r.b] for r in reqs)
     m = eng.run_stream(reqs)
-    m["atom_moments_per_s"] = atom_moments / max(m["seconds"], 1e-12)
+    m["atom_moments_per_s"] = None if args.rotate_cached else atom_moments / max(m["seconds"], 1e-12)
     m["workload"] = st.name
     m["offered_requests_per_s"] = args.rate
     m["precision"] = "mixed (float moments, double contraction)"
+    m["b_moments"] = "rotated from the cache (Wigner)" if args.rotate_cached else "recomputed from B's atoms"
     if args.plain_fp64 > 0:
         sample = make_requests(st)[:args.plain_fp64]
         e_s, a_s = plain_fp64(ex, sample)

@@ -80,12 +80,15 @@ def lib():
         L.tcm_ctx_set_tiling_l.argtypes = [P, i32, i32, i32, i32]
         L.tcm_ctx_get_tiling_l.argtypes = [P, i32, i32, P, P]
         L.tcm_ctx_set_graphs.argtypes = [P, i32]
+        L.tcm_ctx_set_rotate_cached.argtypes = [P, i32]
+        L.tcm_rotate_moments.argtypes = [P, ctypes.c_int64, P, P, P]
         L.tcm_ctx_graph_stats.argtypes = [P, P, P]
         L.tcm_ctx_read_profile.argtypes = [P, P, P]
         for name in ("tcm_ctx_create", "tcm_ctx_set_stream", "tcm_prepare", "tcm_moments", "tcm_energy",
                      "tcm_energy_batch", "tcm_direct", "tcm_ctx_set_profiling", "tcm_ctx_read_profile",
                      "tcm_moments_noalloc", "tcm_ctx_set_tiling", "tcm_ctx_set_graphs", "tcm_ctx_graph_stats",
-                     "tcm_ctx_set_tiling_l", "tcm_ctx_get_tiling_l"):
+                     "tcm_ctx_set_tiling_l", "tcm_ctx_get_tiling_l",
+                     "tcm_ctx_set_rotate_cached", "tcm_rotate_moments"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -188,6 +191,38 @@ class Context:
         apl, cps = ctypes.c_int(), ctypes.c_int()
         _check(lib().tcm_ctx_get_tiling_l(self._h, int(precision), int(lmax), ctypes.byref(apl), ctypes.byref(cps)))
         return apl.value, cps.value
+
+    def tcm_ctx_set_rotate_cached(self, enable: bool):
+        _check(lib().tcm_ctx_set_rotate_cached(self._h, 1 if enable else 0))
+
+    def tcm_rotate_moments(self, moms, rot, lmax=None, out=None):
+        """Moments of rotated systems from their moments (Wigner rotation, no atoms).
+
+        moms: a MomentSet or a list of them; rot: (3, 3) or (n, 3, 3).  Returns MomentSet(s) at
+        ``lmax`` (default: each input's lmax); asynchronous on the context stream."""
+        single = isinstance(moms, MomentSet)
+        ms = [moms] if single else list(moms)
+        R = np.ascontiguousarray(np.asarray(rot, dtype=np.float64).reshape(-1, 9))
+        if len(R) != len(ms):
+            raise TcmError(TCM_EINVAL, "one rotation per moment set")
+        outs = [] if out is None else ([out] if single else list(out))
+        ins = (tcm_moments_t * max(len(ms), 1))()
+        res = (tcm_moments_t * max(len(ms), 1))()
+        for i, m in enumerate(ms):
+            L = m.lmax if lmax is None else int(lmax)
+            if out is None:
+                outs.append(MomentSet(torch.empty((L + 1) ** 2, dtype=torch.float64, device=m.q.device), L,
+                                      np.array(m.center, dtype=np.float64), float(m.radius)))
+            ins[i] = m.struct()
+            res[i] = outs[i].struct()
+            res[i].lmax = L
+        _check(lib().tcm_rotate_moments(self._h, len(ms), ctypes.cast(ins, ctypes.c_void_p),
+                                        R.ctypes.data_as(ctypes.c_void_p), ctypes.cast(res, ctypes.c_void_p)))
+        for i, o in enumerate(outs):
+            o.lmax = res[i].lmax
+            o.center = np.array([res[i].center[k] for k in range(3)])
+            o.radius = res[i].radius
+        return outs[0] if single else outs
 
     def tcm_ctx_set_graphs(self, enable: bool):
         _check(lib().tcm_ctx_set_graphs(self._h, 1 if enable else 0))

@@ -125,7 +125,8 @@ def test_not_converged_items_report_status():
 
 
 @pytest.mark.gpu
-def test_gpu_engine_results_same_alone_and_in_mix():
+@pytest.mark.parametrize("rotate_cached", [False, True])
+def test_gpu_engine_results_same_alone_and_in_mix(rotate_cached):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -136,7 +137,7 @@ def test_gpu_engine_results_same_alone_and_in_mix():
     from tcm_testlib import TOL_MIX_E, energy_error, oracle_moments_threaded
 
     st = synth.serve_stream(seed=9, n_pool=12, n_lo=300, n_hi=6000, rate=4000.0, seconds=0.05, orient_hi=24)
-    ex = GpuExecutor(st.systems, lmax_cap=24)
+    ex = GpuExecutor(st.systems, lmax_cap=24, rotate_cached=rotate_cached)
     reqs = make_requests(st)
     eng = Engine(ex, ex.item_bytes, max_items=256, quota=32)
     m = eng.run_stream(reqs)
