@@ -14,6 +14,10 @@
 //   * Eq. (Formula)  : U_mult = sum_{l1,l2<=Lmax} sum_{m1,m2} (-1)^(l1+M) R0^-(L+1)
 //                        sqrt(4 pi (2L)! / ((2l1)! (2l2)!)) 3j(l1 l2 L; m1 m2 -M)
 //                        Q^A_l1m1 Q^B_l2m2 Y*_LM(R0hat),  L = l1+l2, M = m1+m2
+//   * forces and torques (the paper names them as a use of Eq. (Formula) but prints no
+//     formula): the gradient of Eq. (Formula) in R0 through the textbook derivatives of
+//     Y_LM, the derivative of Eq. (multipole) under a rotation of a system about its
+//     centre, and the exact pairwise forces and torques of Eq. (Coulomb)
 // Spherical harmonics are orthonormal with the Condon-Shortley phase (the
 // convention of Varshalovich, which the paper follows); Y_lm for m >= 0 comes
 // from std::sph_legendre and Y_l,-m = (-1)^m conj(Y_lm).
@@ -124,11 +128,64 @@ void rel_pos(const double* xyzq, int64_t i, const double* c, const double* rot, 
 
 int idx(int l, int m) { return l * l + l + m; }
 
+// Angular derivatives of Y_lm for the gradients (Section II gives no force formula; these are
+// the textbook derivatives of the orthonormal harmonics):
+//   dY_lm/dtheta = 1/2 [ c+ e^{-i phi} Y_l,m+1 - c- e^{+i phi} Y_l,m-1 ],
+//   c+ = sqrt((l-m)(l+m+1)), c- = sqrt((l+m)(l-m+1))   (ladder form, regular at the poles);
+//   (1/sin theta) dY_lm/dphi = i m Y_lm / sin theta, taken near the poles from the sum of the
+//   two ladder terms:  m Y_lm / sin theta = -[ c+ e^{-i phi} Y_l,m+1 + c- e^{i phi} Y_l,m-1 ] / (2 cos theta).
+void ladder_terms(int l, int m, double th, double ph, double* ar, double* ai, double* br, double* bi) {
+  // (ar, ai) = c+ e^{-i phi} Y_l,m+1 ; (br, bi) = c- e^{i phi} Y_l,m-1
+  double cp = std::sqrt((double)(l - m) * (l + m + 1)), cm = std::sqrt((double)(l + m) * (l - m + 1));
+  double ur = 0.0, ui = 0.0, dr = 0.0, di = 0.0;
+  if (m + 1 <= l) ylm(l, m + 1, th, ph, &ur, &ui);
+  if (m - 1 >= -l) ylm(l, m - 1, th, ph, &dr, &di);
+  const double c = std::cos(ph), s = std::sin(ph);
+  *ar = cp * (c * ur + s * ui);
+  *ai = cp * (c * ui - s * ur);
+  *br = cm * (c * dr - s * di);
+  *bi = cm * (c * di + s * dr);
+}
+
+void ylm_dtheta(int l, int m, double th, double ph, double* re, double* im) {
+  double ar, ai, br, bi;
+  ladder_terms(l, m, th, ph, &ar, &ai, &br, &bi);
+  *re = 0.5 * (ar - br);
+  *im = 0.5 * (ai - bi);
+}
+
+void ylm_dphi_over_sin(int l, int m, double th, double ph, double* re, double* im) {
+  const double st = std::sin(th);
+  double vr, vi;  // m Y / sin theta
+  if (st > 0.5) {
+    double yr, yi;
+    ylm(l, m, th, ph, &yr, &yi);
+    vr = m * yr / st;
+    vi = m * yi / st;
+  } else {
+    double ar, ai, br, bi;
+    ladder_terms(l, m, th, ph, &ar, &ai, &br, &bi);
+    const double k = -1.0 / (2.0 * std::cos(th));
+    vr = k * (ar + br);
+    vi = k * (ai + bi);
+  }
+  *re = -vi;  // i (vr + i vi)
+  *im = vr;
+}
+
+// Spherical unit vectors at (theta, phi).
+void sph_frame(double th, double ph, double* rh, double* th_hat, double* ph_hat) {
+  const double st = std::sin(th), ct = std::cos(th), sp = std::sin(ph), cp = std::cos(ph);
+  rh[0] = st * cp; rh[1] = st * sp; rh[2] = ct;
+  th_hat[0] = ct * cp; th_hat[1] = ct * sp; th_hat[2] = -st;
+  ph_hat[0] = -sp; ph_hat[1] = cp; ph_hat[2] = 0.0;
+}
+
 }  // namespace
 
 extern "C" {
 
-int oracle_abi_version(void) { return 1; }
+int oracle_abi_version(void) { return 2; }
 
 // Centre = centroid of positions (unit masses); radius a = max_i |x_i - c|.
 void oracle_center_radius(int64_t n, const double* xyzq, double* center, double* radius) {
@@ -241,6 +298,147 @@ double oracle_tcm_energy(int L, const double* qa_re, const double* qa_im, const 
   }
   if (im_out) *im_out = si.value();
   return s.value();
+}
+
+// Force on B, F = -grad_R0 U_mult, from Eq. (Formula) as printed: the separation factor
+// Y*_LM(R0hat) / R0^(L+1) is replaced by its gradient
+//   -(L+1) Y*/R^(L+2) Rhat + (dY/dtheta)*/R^(L+2) thetahat + (i M Y / sin theta)*/R^(L+2) phihat.
+// force[3] gets the real force; block_norm[l1*(L+1)+l2] (optional) the length of each
+// (l1, l2) block's force vector, the scale of its rounding.
+void oracle_tcm_force(int L, const double* qa_re, const double* qa_im, const double* qb_re, const double* qb_im,
+                      const double* R0, double* force, double* block_norm) {
+  double R = std::sqrt(R0[0] * R0[0] + R0[1] * R0[1] + R0[2] * R0[2]);
+  double theta = std::acos(std::fmax(-1.0, std::fmin(1.0, R0[2] / R)));
+  double phi = std::atan2(R0[1], R0[0]);
+  double rh[3], thh[3], phh[3];
+  sph_frame(theta, phi, rh, thh, phh);
+  CSum tot[3];
+  for (int l1 = 0; l1 <= L; ++l1) {
+    for (int l2 = 0; l2 <= L; ++l2) {
+      int LL = l1 + l2;
+      long double pref = std::sqrt(4.0L * (long double)kPi * fact(2 * LL) / (fact(2 * l1) * fact(2 * l2)));
+      double scale = (double)pref / std::pow(R, LL + 2);
+      CSum g[3];
+      for (int m1 = -l1; m1 <= l1; ++m1) {
+        for (int m2 = -l2; m2 <= l2; ++m2) {
+          int M = m1 + m2;
+          double tj = threej(l1, l2, LL, m1, m2, -M);
+          if (tj == 0.0) continue;
+          double sgn = (((l1 + M) % 2) + 2) % 2 ? -1.0 : 1.0;
+          double yr, yi, tr, ti, pr_, pi_;
+          ylm(LL, M, theta, phi, &yr, &yi);
+          ylm_dtheta(LL, M, theta, phi, &tr, &ti);
+          ylm_dphi_over_sin(LL, M, theta, phi, &pr_, &pi_);
+          // the separation harmonic enters conjugated
+          yi = -yi;
+          ti = -ti;
+          pi_ = -pi_;
+          double ar = qa_re[idx(l1, m1)], ai = qa_im[idx(l1, m1)];
+          double br = qb_re[idx(l2, m2)], bi = qb_im[idx(l2, m2)];
+          double qr = ar * br - ai * bi, qi = ar * bi + ai * br;
+          double f = sgn * scale * tj;
+          // Re[(qr + i qi) v] for v = -(L+1) Y*, (dY/dtheta)*, (i M Y / sin theta)*
+          double vR = -(LL + 1) * (qr * yr - qi * yi);
+          double vT = qr * tr - qi * ti;
+          double vP = qr * pr_ - qi * pi_;
+          for (int d = 0; d < 3; ++d) g[d].add(f * (vR * rh[d] + vT * thh[d] + vP * phh[d]));
+        }
+      }
+      double bn = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        double v = g[d].value();
+        tot[d].add(-v);  // force = -gradient
+        bn += v * v;
+      }
+      if (block_norm) block_norm[l1 * (L + 1) + l2] = std::sqrt(bn);
+    }
+  }
+  for (int d = 0; d < 3; ++d) force[d] = tot[d].value();
+}
+
+// Derivative of Eq. (multipole) under a rotation of the system about its centre: with every
+// position moved to r + eps n x r, dQ_lm/deps = sum_i q_i sqrt(4 pi/(2l+1)) n . (r x grad)(r^l Y_lm)
+// and (r x grad)(r^l Y) = r^l [ phihat dY/dtheta - thetahat (1/sin theta) dY/dphi ].
+// Positions are taken about the centre, after the optional rotation rot.
+void oracle_moments_rotderiv(int64_t n, const double* xyzq, const double* center, const double* rot, int L,
+                             const double* axis, double* d_re, double* d_im) {
+  const int ncomp = (L + 1) * (L + 1);
+  std::vector<CSum> acc_re(ncomp), acc_im(ncomp);
+  for (int64_t i = 0; i < n; ++i) {
+    double r3[3];
+    rel_pos(xyzq, i, center, rot, r3);
+    double q = xyzq[4 * i + 3];
+    double r = std::sqrt(r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2]);
+    if (r == 0.0) continue;  // n x r = 0: the atom does not move
+    double theta = std::acos(std::fmax(-1.0, std::fmin(1.0, r3[2] / r)));
+    double phi = std::atan2(r3[1], r3[0]);
+    double rh[3], thh[3], phh[3];
+    sph_frame(theta, phi, rh, thh, phh);
+    const double nphi = axis[0] * phh[0] + axis[1] * phh[1] + axis[2] * phh[2];
+    const double nth = axis[0] * thh[0] + axis[1] * thh[1] + axis[2] * thh[2];
+    for (int l = 0; l <= L; ++l) {
+      double w = q * std::pow(r, l) * std::sqrt(4.0 * kPi / (2 * l + 1));
+      for (int m = -l; m <= l; ++m) {
+        double tr, ti, pr_, pi_;
+        ylm_dtheta(l, m, theta, phi, &tr, &ti);
+        ylm_dphi_over_sin(l, m, theta, phi, &pr_, &pi_);
+        acc_re[idx(l, m)].add(w * (nphi * tr - nth * pr_));
+        acc_im[idx(l, m)].add(w * (nphi * ti - nth * pi_));
+      }
+    }
+  }
+  for (int k = 0; k < ncomp; ++k) {
+    d_re[k] = acc_re[k].value();
+    d_im[k] = acc_im[k].value();
+  }
+}
+
+// Eq. (Coulomb) differentiated: the exact force on B, F_B = sum_ij q_i q_j d_ij / |d_ij|^3 with
+// d_ij = R0 + r_j^B - r_i^A, and the torques on A and on B about their centres,
+// tau_A = sum_i r_i^A x (-F_i), tau_B = sum_j r_j^B x F_j (r^B rotated by rotB).
+// out[9] = F_B, tau_A, tau_B.  *abs_out (optional) = sum_ij |q_i q_j| / |d_ij|^2.
+void oracle_direct_forces(int64_t na, const double* a, const double* ca, int64_t nb, const double* b,
+                          const double* cb, const double* rotb, const double* R0, double* out, double* abs_out) {
+  std::vector<double> rb(3 * (size_t)nb);
+  for (int64_t j = 0; j < nb; ++j) rel_pos(b, j, cb, rotb, &rb[3 * j]);
+  std::vector<CSum> fj(3 * (size_t)nb);
+  CSum TA[3], sa;
+  for (int64_t i = 0; i < na; ++i) {
+    double ra[3];
+    rel_pos(a, i, ca, nullptr, ra);
+    double qi = a[4 * i + 3];
+    CSum fi[3];
+    for (int64_t j = 0; j < nb; ++j) {
+      double d[3] = {R0[0] + rb[3 * j + 0] - ra[0], R0[1] + rb[3 * j + 1] - ra[1], R0[2] + rb[3 * j + 2] - ra[2]};
+      double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      double r = std::sqrt(r2);
+      double w = qi * b[4 * j + 3] / (r2 * r);
+      for (int k = 0; k < 3; ++k) {
+        fj[3 * j + k].add(w * d[k]);
+        fi[k].add(-w * d[k]);
+      }
+      sa.add(std::fabs(qi * b[4 * j + 3]) / r2);
+    }
+    double f[3] = {fi[0].value(), fi[1].value(), fi[2].value()};
+    TA[0].add(ra[1] * f[2] - ra[2] * f[1]);
+    TA[1].add(ra[2] * f[0] - ra[0] * f[2]);
+    TA[2].add(ra[0] * f[1] - ra[1] * f[0]);
+  }
+  CSum F[3], TB[3];
+  for (int64_t j = 0; j < nb; ++j) {
+    double f[3] = {fj[3 * j].value(), fj[3 * j + 1].value(), fj[3 * j + 2].value()};
+    const double* r = &rb[3 * j];
+    for (int k = 0; k < 3; ++k) F[k].add(f[k]);
+    TB[0].add(r[1] * f[2] - r[2] * f[1]);
+    TB[1].add(r[2] * f[0] - r[0] * f[2]);
+    TB[2].add(r[0] * f[1] - r[1] * f[0]);
+  }
+  for (int k = 0; k < 3; ++k) {
+    out[k] = F[k].value();
+    out[3 + k] = TA[k].value();
+    out[6 + k] = TB[k].value();
+  }
+  if (abs_out) *abs_out = sa.value();
 }
 
 // Eq. (Coulomb): U = sum_i sum_j q_i q_j / |R0 + r_j^B - r_i^A|, with r^A about
