@@ -229,6 +229,18 @@ int tcm_ctx_set_rotate_cached(tcm_ctx_t ctx, int enable);
 int tcm_energy_batch(tcm_ctx_t ctx, int n_systems, const tcm_system* systems, int64_t n_items,
                      const tcm_pair_item* items, int precision, double* E, int32_t* status);
 
+/* Forces and torques with the batched energies (the paper names forces as a use of Eq.
+ * (Formula) but prints no formula; these are the exact derivatives of the truncated energy):
+ * as tcm_energy_batch, and for every item G[9 k .. 9 k + 8] (device doubles) receives
+ *   F_B   = -grad_R0 E   (force on B; the force on A is -F_B),
+ *   tau_A = torque on A about its centre,  tau_B = torque on B about its centre,
+ * all in the lab frame, as minus the derivative of E under a rotation of that system about
+ * its own centre.  With the square truncation tau_A + tau_B + R0 x F_B = 0.  Computed in the
+ * frame where R0hat = z from the same moments (O(Lmax^3) per item); NaN for an item that does
+ * not converge.  E may be the same buffer tcm_energy_batch would take. */
+int tcm_gradients_batch(tcm_ctx_t ctx, int n_systems, const tcm_system* systems, int64_t n_items,
+                        const tcm_pair_item* items, int precision, double* E, double* G, int32_t* status);
+
 /* Eq. (Coulomb): exact pairwise energy of A and B (B rotated by rotB about its centre,
  * NULL = identity) with the centre of B at the centre of A plus R0, in double
  * precision.  Writes the host double *E.  Synchronous. */

@@ -367,14 +367,45 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// Sum of N values over the block; thread 0 gets the totals in v.  sh holds N * 32 doubles.
+template <int N>
+__device__ void block_sum_n(double (&v)[N], double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const double t = warp_sum(v[k]);
+    if (lane == 0) sh[k * 32 + w] = t;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = warp_sum(lane < nw ? sh[k * 32 + lane] : 0.0);
+  }
+  __syncthreads();
+}
+
+// Eq. (Formula) for one (pair, orientation) per CTA, in the frame where R0hat = z.  With kGrad
+// it also writes, per item, the force on B (-grad_R0 E) and the torques on A and on B about
+// their centres, from the same frame moments:
+//   in the frame, with c = (-1)^l2 L!/R^(L+1), c' = (-1)^l2 (L+1)!/R^(L+2), L = l1 + l2,
+//   T0 = sum_m Qa_m Qb_-m,  S+ = sum_{m1+m2=1} Qa_m1 Qb_m2,  P = sum_{m1+m2=1} (l2+m2) Qa_m1 Qb_m2,
+//   Z = sum_{m>=1} (-1)^m 2m Im(Qa_m conj Qb_m)  (Qhat normalisation throughout):
+//   grad E = -sum c' (Re S+, Im S+, T0)       (only J_L,0 and J_L,+-1 have a first-order
+//                                                derivative on the z axis);
+//   tau_B = sum c (Im P, -Re P, -Z),  tau_A = sum c (Im P', -Re P', Z),  P' = (L+1) S+ - P
+//   (infinitesimal rotations act on Qhat_lm through L_z and the ladder operators with the
+//   integer weights (l+m+1), (l-m+1)).  The vectors go back to the lab frame with W^T.
+template <bool kGrad>
 __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* __restrict__ items,
                                                                const MomJob* __restrict__ jobs,
                                                                const SysGeom* __restrict__ geoms,
                                                                const double* __restrict__ ztab,
-                                                               double* __restrict__ E, int32_t* __restrict__ status) {
+                                                               double* __restrict__ E, int32_t* __restrict__ status,
+                                                               double* __restrict__ G) {
   const double* rtab = ztab + ((kZ_TOTAL + 3) / 4 * 4);  // recursion coefficients, 4 doubles per (l, a, b)
   extern __shared__ double2 sm2[];
-  __shared__ double sh[32];
+  __shared__ double sh[(kGrad ? 9 : 1) * 32];
   __shared__ double g_cb, g_ch, g_sh, g_iR;
   __shared__ Euler g_eb;
   const PairDesc d = items[blockIdx.x];
@@ -387,6 +418,7 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
       E[blockIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
       if (status) status[blockIdx.x] = TCM_ENOTCONV;
     }
+    if (kGrad && threadIdx.x < 9) G[9LL * blockIdx.x + threadIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
     return;
   }
   const int nq = (L + 1) * (L + 2) / 2;
@@ -399,8 +431,8 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
   double2* phg = pha + (L + 1);//                                      e^{-i m gamma_B}
   double* cp = reinterpret_cast<double*>(phg + (L + 1));  // cos^k(beta/2), k <= 2L
   double* sp = cp + 2 * L + 1;                             // sin^k(beta/2)
-  double* rp = sp + 2 * L + 1;                             // R^-(k+1), k <= 2L
-  double* D = rp + 2 * L + 1;                              // half Wigner table, sum (l+1)^2 entries
+  double* rp = sp + 2 * L + 1;                             // R^-(k+1), k <= 2L + 1
+  double* D = rp + 2 * L + 2;                              // half Wigner table, sum (l+1)^2 entries
   const double* pa = jobs[d.jobA].out;
   const double* pb = jobs[d.jobB].out;
   const int bmode = d.b_mode;
@@ -437,7 +469,7 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     half_angle_powers(cp, sp, g_ch, g_sh, L);
   } else if (threadIdx.x == 96) {
     double r = g_iR;
-    for (int k = 0; k <= 2 * L; ++k) {
+    for (int k = 0; k <= 2 * L + 1; ++k) {
       rp[k] = r;
       r *= g_iR;
     }
@@ -479,6 +511,7 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
   __syncthreads();
   // z-axis contraction: one thread per (l1, l2)
   double acc = 0.0;
+  double gx = 0.0, gy = 0.0, gz = 0.0, tbx = 0.0, tby = 0.0, tbz = 0.0, tax = 0.0, tay = 0.0;
   for (int p = threadIdx.x; p < (L + 1) * (L + 1); p += blockDim.x) {
     const int l1 = p / (L + 1);
     const int l2 = p - l1 * (L + 1);
@@ -488,12 +521,71 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     double s = 0.0;
     for (int m = 1; m <= mm; ++m) s += flip(fma(a[m].x, b[m].x, a[m].y * b[m].y), m);
     s = fma(2.0, s, a[0].x * b[0].x);
-    acc = fma(flip(ztab[kZ_FACT + l1 + l2] * rp[l1 + l2], l2), s, acc);
+    const double c = flip(ztab[kZ_FACT + l1 + l2] * rp[l1 + l2], l2);
+    acc = fma(c, s, acc);
+    if (kGrad) {
+      // S+ and P: pairs (m1, m2) = (m, 1 - m), m >= 1, and (-m, m + 1), m >= 0
+      double spr = 0.0, spi = 0.0, pr = 0.0, pi = 0.0, z = 0.0;
+      const int m1a = l1 < l2 + 1 ? l1 : l2 + 1;
+      for (int m = 1; m <= m1a; ++m) {  // (-1)^(m-1) a_m conj(b_(m-1)), weight l2 + 1 - m
+        const double2 x = a[m], y = b[m - 1];
+        const double re = flip(fma(x.x, y.x, x.y * y.y), m - 1);
+        const double im = flip(fma(x.y, y.x, -(x.x * y.y)), m - 1);
+        const double w = (double)(l2 + 1 - m);
+        spr += re;
+        spi += im;
+        pr = fma(w, re, pr);
+        pi = fma(w, im, pi);
+      }
+      const int m1b = l1 < l2 - 1 ? l1 : l2 - 1;
+      for (int m = 0; m <= m1b; ++m) {  // (-1)^m conj(a_m) b_(m+1), weight l2 + 1 + m
+        const double2 x = a[m], y = b[m + 1];
+        const double re = flip(fma(x.x, y.x, x.y * y.y), m);
+        const double im = flip(fma(x.x, y.y, -(x.y * y.x)), m);
+        const double w = (double)(l2 + 1 + m);
+        spr += re;
+        spi += im;
+        pr = fma(w, re, pr);
+        pi = fma(w, im, pi);
+      }
+      for (int m = 1; m <= mm; ++m) z += flip((double)(2 * m) * fma(a[m].y, b[m].x, -(a[m].x * b[m].y)), m);
+      const double c1 = flip(ztab[kZ_FACT + l1 + l2 + 1] * rp[l1 + l2 + 1], l2);
+      const double L1 = (double)(l1 + l2 + 1);
+      gx = fma(-c1, spr, gx);
+      gy = fma(-c1, spi, gy);
+      gz = fma(-c1, s, gz);
+      tbx = fma(c, pi, tbx);
+      tby = fma(-c, pr, tby);
+      tbz = fma(-c, z, tbz);
+      tax = fma(c, fma(L1, spi, -pi), tax);
+      tay = fma(-c, fma(L1, spr, -pr), tay);
+    }
   }
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) {
-    E[blockIdx.x] = acc;
-    if (status) status[blockIdx.x] = TCM_OK;
+  if (!kGrad) {
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+      E[blockIdx.x] = acc;
+      if (status) status[blockIdx.x] = TCM_OK;
+    }
+  } else {
+    double v[9] = {acc, gx, gy, gz, tbx, tby, tbz, tax, tay};
+    block_sum_n<9>(v, sh);
+    if (threadIdx.x == 0) {
+      E[blockIdx.x] = v[0];
+      if (status) status[blockIdx.x] = TCM_OK;
+      double W[9];
+      frame_rotation(d.R0, W);
+      // frame -> lab: v_lab = W^T v_frame; force = -grad; tau_A,z = -tau_B,z
+      const double f[3] = {-v[1], -v[2], -v[3]};
+      const double ta[3] = {v[7], v[8], -v[6]};
+      const double tb[3] = {v[4], v[5], v[6]};
+      double* o = G + 9LL * blockIdx.x;
+      for (int i = 0; i < 3; ++i) {
+        o[i] = W[i] * f[0] + W[3 + i] * f[1] + W[6 + i] * f[2];
+        o[3 + i] = W[i] * ta[0] + W[3 + i] * ta[1] + W[6 + i] * ta[2];
+        o[6 + i] = W[i] * tb[0] + W[3 + i] * tb[1] + W[6 + i] * tb[2];
+      }
+    }
   }
 }
 
@@ -615,7 +707,7 @@ __global__ void k_direct_final(const double* __restrict__ part, int nblk, double
 int contract_smem_bytes(int L) {
   const int nq = (L + 1) * (L + 2) / 2;
   const int nd = (L + 1) * (L + 2) * (2 * L + 3) / 6;
-  return (4 * nq + 3 * (L + 1)) * (int)sizeof(double2) + (3 * (2 * L + 1) + nd) * (int)sizeof(double);
+  return (4 * nq + 3 * (L + 1)) * (int)sizeof(double2) + (3 * (2 * L + 1) + 1 + nd) * (int)sizeof(double);
 }
 
 int rotate_smem_bytes(int L) {
@@ -651,13 +743,20 @@ int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, cons
 }
 
 int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const MomJob* jobs, const SysGeom* geoms,
-                    const double* ztab, double* E, int32_t* status, cudaStream_t s) {
+                    const double* ztab, double* E, int32_t* status, double* G, cudaStream_t s) {
   if (n_items <= 0) return 0;
   const int smem = contract_smem_bytes(Lmax_items);
-  if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return -1;
+  if (G) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      return -1;
+    k_contract<true><<<n_items, kContractThreads, smem, s>>>(items, jobs, geoms, ztab, E, status, G);
+  } else {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      return -1;
+    k_contract<false><<<n_items, kContractThreads, smem, s>>>(items, jobs, geoms, ztab, E, status, nullptr);
   }
-  k_contract<<<n_items, kContractThreads, smem, s>>>(items, jobs, geoms, ztab, E, status);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -30,8 +30,10 @@ struct RotDesc {  // one moment set rotated about its centre: out = moments of (
   double M[9];
 };
 
+// G (optional, device, 9 doubles per item): force on B, torque on A, torque on B (lab frame).
 int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const MomJob* jobs,
-                    const SysGeom* geoms, const double* ztab, double* E, int32_t* status, cudaStream_t s);
+                    const SysGeom* geoms, const double* ztab, double* E, int32_t* status, double* G,
+                    cudaStream_t s);
 int contract_smem_bytes(int L);
 int rotate_smem_bytes(int L);
 int launch_rotate_moments(const RotDesc* sets, int n_sets, int Lmax_sets, const double* ztab, cudaStream_t s);

@@ -697,7 +697,7 @@ int tcm_energy(tcm_ctx_t c, const tcm_moments_t* A, const tcm_moments_t* B, cons
     PhaseScope ps(c, TCM_PHASE_CONTRACT, 1);
     TRY_LAUNCH(launch_contract(reinterpret_cast<PairDesc*>(base + o_it), 1, lmax,
                                reinterpret_cast<MomJob*>(base + o_job), reinterpret_cast<SysGeom*>(base + o_geo),
-                               c->d_ztab, dE, nullptr, c->stream));
+                               c->d_ztab, dE, nullptr, nullptr, c->stream));
   }
   TRY_CUDA(cudaMemcpyAsync(c->pinned_small, dE, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   TRY_CUDA(cudaStreamSynchronize(c->stream));
@@ -743,8 +743,25 @@ int tcm_ctx_set_rotate_cached(tcm_ctx_t c, int enable) {
   return TCM_OK;
 }
 
+namespace {
+int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t n_items, const tcm_pair_item* items,
+                 int precision, double* E, int32_t* status, double* G);
+}
+
 int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t n_items, const tcm_pair_item* items,
                      int precision, double* E, int32_t* status) {
+  return energy_batch(c, n_systems, systems, n_items, items, precision, E, status, nullptr);
+}
+
+int tcm_gradients_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t n_items,
+                        const tcm_pair_item* items, int precision, double* E, double* G, int32_t* status) {
+  if (n_items > 0 && !G) return set_err(TCM_EINVAL, "tcm_gradients_batch: null gradient output");
+  return energy_batch(c, n_systems, systems, n_items, items, precision, E, status, G);
+}
+
+namespace {
+int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t n_items, const tcm_pair_item* items,
+                 int precision, double* E, int32_t* status, double* G) {
   TRY(check_ctx(c));
   if (n_items < 0 || n_systems < 0) return set_err(TCM_EINVAL, "tcm_energy_batch: negative count");
   if (n_items == 0) return TCM_OK;
@@ -888,13 +905,13 @@ int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int6
     TRY(run_moments(c, precision, P, d_jobs, reinterpret_cast<MomTile*>(base + o_tile), d_geo, st));
     PhaseScope ps(c, TCM_PHASE_CONTRACT, 1);
     TRY_LAUNCH(launch_contract(reinterpret_cast<PairDesc*>(base + o_it), (int)n_items, Lmax_items, d_jobs, d_geo,
-                               c->d_ztab, E, status, st));
+                               c->d_ztab, E, status, G, st));
     return TCM_OK;
   };
   if (!c->graphs || c->prof || !c->cap_stream) return enqueue(c->stream);
   // Replay a captured graph of the launch sequence when this call has the same shape and
   // buffers as the captured one (only the uploaded descriptor contents differ).
-  std::vector<long long> key = {precision, ngt, (long long)gjobs.size(), (long long)P.jobs.size(), P.n_tile_ids,
+  std::vector<long long> key = {precision, G != nullptr, (long long)(uintptr_t)G, ngt, (long long)gjobs.size(), (long long)P.jobs.size(), P.n_tile_ids,
                                 (long long)n_items, Lmax_items, (long long)o_geo, (long long)o_job, (long long)o_tile,
                                 (long long)o_gj, (long long)o_gt, (long long)o_it, (long long)(uintptr_t)base,
                                 (long long)(uintptr_t)c->gpart.p, (long long)(uintptr_t)c->partials.p,
@@ -940,6 +957,7 @@ int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int6
   c->launches[TCM_PHASE_CONTRACT] += 1;
   return TCM_OK;
 }
+}  // namespace
 
 int tcm_direct(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, const double* rotB, const double* R0, double* E) {
   TRY(check_ctx(c));

@@ -81,6 +81,7 @@ def lib():
         L.tcm_ctx_get_tiling_l.argtypes = [P, i32, i32, P, P]
         L.tcm_ctx_set_graphs.argtypes = [P, i32]
         L.tcm_ctx_set_rotate_cached.argtypes = [P, i32]
+        L.tcm_gradients_batch.argtypes = [P, i32, P, ctypes.c_int64, P, i32, P, P, P]
         L.tcm_rotate_moments.argtypes = [P, ctypes.c_int64, P, P, P]
         L.tcm_ctx_graph_stats.argtypes = [P, P, P]
         L.tcm_ctx_read_profile.argtypes = [P, P, P]
@@ -88,7 +89,7 @@ def lib():
                      "tcm_energy_batch", "tcm_direct", "tcm_ctx_set_profiling", "tcm_ctx_read_profile",
                      "tcm_moments_noalloc", "tcm_ctx_set_tiling", "tcm_ctx_set_graphs", "tcm_ctx_graph_stats",
                      "tcm_ctx_set_tiling_l", "tcm_ctx_get_tiling_l",
-                     "tcm_ctx_set_rotate_cached", "tcm_rotate_moments"):
+                     "tcm_ctx_set_rotate_cached", "tcm_rotate_moments", "tcm_gradients_batch"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -296,6 +297,26 @@ class Context:
                                       pb.items.ctypes.data_as(ctypes.c_void_p), int(precision),
                                       ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(status.data_ptr())))
         return E, status
+
+    def tcm_gradients_batch(self, systems, a, b, lmax, R0, rotB=None, precision=TCM_MIXED, E=None, G=None,
+                            status=None):
+        """Batched energies with the force on B and the torques on A and B (lab frame).
+
+        Returns (E, G, status): G is a (k, 9) device tensor [F_B, tau_A, tau_B] per item."""
+        pb = pack_batch(systems, a, b, lmax, R0, rotB)
+        k = len(pb.items)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if E is None:
+            E = torch.empty(k, dtype=torch.float64, device=dev)
+        if G is None:
+            G = torch.empty((k, 9), dtype=torch.float64, device=dev)
+        if status is None:
+            status = torch.empty(k, dtype=torch.int32, device=dev)
+        _check(lib().tcm_gradients_batch(self._h, pb.n_systems, ctypes.cast(pb.sys_arr, ctypes.c_void_p), k,
+                                         pb.items.ctypes.data_as(ctypes.c_void_p), int(precision),
+                                         ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(G.data_ptr()),
+                                         ctypes.c_void_p(status.data_ptr())))
+        return E, G, status
 
     # ---------------------------------------------------------------- Eq. (Coulomb)
     def tcm_direct(self, A, B, R0, rotB=None, cA=None, cB=None) -> float:
