@@ -20,7 +20,8 @@
 //     centre, and the exact pairwise forces and torques of Eq. (Coulomb)
 // Spherical harmonics are orthonormal with the Condon-Shortley phase (the
 // convention of Varshalovich, which the paper follows); Y_lm for m >= 0 comes
-// from std::sph_legendre and Y_l,-m = (-1)^m conj(Y_lm).
+// from std::sph_legendre (from the hypergeometric series within 1.1 degrees of a
+// pole, where the library loses digits) and Y_l,-m = (-1)^m conj(Y_lm).
 //
 // Readings of the paper taken here:
 //   * moments use Y_lm (not its conjugate), as Eq. (multipole) prints them, and
@@ -74,10 +75,34 @@ const FactTable& facts() {
 }
 long double fact(int n) { return facts().f[n]; }
 
+// Y_lm(theta, 0), 0 <= m <= l, within sin^2(theta/2) < 1e-4 of the north pole, where the
+// library function (which works from cos theta) loses the digits of sin^m theta.  From the
+// Ferrers function as a terminating hypergeometric series in s = sin^2(theta/2):
+//   P_l^m(cos t) = (-1)^m sin^m t (l+m)! / (2^m m! (l-m)!) 2F1(m-l, l+m+1; m+1; s),
+// whose terms fall by a factor <= l^2 s / (m+1) < 0.25 here for l <= 48 (no cancellation beyond a digit in long double).
+double ylm0_near_pole(int l, int m, double sin_t, double s) {
+  long double f = 1.0L, t = 1.0L;
+  for (int k = 0; k < l - m; ++k) {
+    t *= (long double)(m - l + k) * (l + m + 1 + k) / ((long double)(m + 1 + k) * (k + 1)) * s;
+    f += t;
+  }
+  long double norm = std::sqrt((2 * l + 1) / (4.0L * (long double)kPi) * fact(l + m) / fact(l - m)) /
+                     (std::pow(2.0L, m) * fact(m));
+  long double v = norm * std::pow((long double)sin_t, m) * f;
+  return (double)((m % 2) ? -v : v);
+}
+
 // Orthonormal Y_lm(theta, phi) with Condon-Shortley phase, any m in [-l, l].
 void ylm(int l, int m, double theta, double phi, double* re, double* im) {
   int am = m < 0 ? -m : m;
-  double p = std::sph_legendre((unsigned)l, (unsigned)am, theta);  // Y_l|m|(theta, 0)
+  const double sh = std::sin(0.5 * theta), ch = std::cos(0.5 * theta);
+  double p;  // Y_l|m|(theta, 0)
+  if (sh * sh < 1e-4)
+    p = ylm0_near_pole(l, am, std::sin(theta), sh * sh);
+  else if (ch * ch < 1e-4)  // Y_lm(pi - t, 0) = (-1)^(l+m) Y_lm(t, 0)
+    p = ((l + am) % 2 ? -1.0 : 1.0) * ylm0_near_pole(l, am, std::sin(theta), ch * ch);
+  else
+    p = std::sph_legendre((unsigned)l, (unsigned)am, theta);
   double cr = p * std::cos(am * phi), ci = p * std::sin(am * phi);
   if (m < 0) {  // Y_l,-m = (-1)^m conj(Y_lm)
     double sgn = (am % 2) ? -1.0 : 1.0;
@@ -127,6 +152,10 @@ void rel_pos(const double* xyzq, int64_t i, const double* c, const double* rot, 
 }
 
 int idx(int l, int m) { return l * l + l + m; }
+
+// Polar angle of v as atan2(|(x, y)|, z): the same angle as acos(z/|v|), without the loss of
+// half the digits near the poles that acos has (acos(1 - d) ~ sqrt(2 d)).  0 for v = 0.
+double polar_angle(const double* v) { return std::atan2(std::hypot(v[0], v[1]), v[2]); }
 
 // Angular derivatives of Y_lm for the gradients (Section II gives no force formula; these are
 // the textbook derivatives of the orthonormal harmonics):
@@ -229,7 +258,7 @@ void oracle_moments(int64_t n, const double* xyzq, const double* center, const d
     rel_pos(xyzq, i, center, rot, r3);
     double q = xyzq[4 * i + 3];
     double r = std::sqrt(r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2]);
-    double theta = r > 0.0 ? std::acos(std::fmax(-1.0, std::fmin(1.0, r3[2] / r))) : 0.0;
+    double theta = polar_angle(r3);
     double phi = std::atan2(r3[1], r3[0]);
     for (int l = 0; l <= L; ++l) {
       double w = q * std::pow(r, l) * std::sqrt(4.0 * kPi / (2 * l + 1));
@@ -252,7 +281,7 @@ void oracle_moments(int64_t n, const double* xyzq, const double* center, const d
 void oracle_tcm_blocks(int L, const double* qa_re, const double* qa_im, const double* qb_re,
                        const double* qb_im, const double* R0, double* blocks, double* blocks_im) {
   double R = std::sqrt(R0[0] * R0[0] + R0[1] * R0[1] + R0[2] * R0[2]);
-  double theta = std::acos(std::fmax(-1.0, std::fmin(1.0, R0[2] / R)));
+  double theta = polar_angle(R0);
   double phi = std::atan2(R0[1], R0[0]);
   for (int l1 = 0; l1 <= L; ++l1) {
     for (int l2 = 0; l2 <= L; ++l2) {
@@ -308,7 +337,7 @@ double oracle_tcm_energy(int L, const double* qa_re, const double* qa_im, const 
 void oracle_tcm_force(int L, const double* qa_re, const double* qa_im, const double* qb_re, const double* qb_im,
                       const double* R0, double* force, double* block_norm) {
   double R = std::sqrt(R0[0] * R0[0] + R0[1] * R0[1] + R0[2] * R0[2]);
-  double theta = std::acos(std::fmax(-1.0, std::fmin(1.0, R0[2] / R)));
+  double theta = polar_angle(R0);
   double phi = std::atan2(R0[1], R0[0]);
   double rh[3], thh[3], phh[3];
   sph_frame(theta, phi, rh, thh, phh);
@@ -370,7 +399,7 @@ void oracle_moments_rotderiv(int64_t n, const double* xyzq, const double* center
     double q = xyzq[4 * i + 3];
     double r = std::sqrt(r3[0] * r3[0] + r3[1] * r3[1] + r3[2] * r3[2]);
     if (r == 0.0) continue;  // n x r = 0: the atom does not move
-    double theta = std::acos(std::fmax(-1.0, std::fmin(1.0, r3[2] / r)));
+    double theta = polar_angle(r3);
     double phi = std::atan2(r3[1], r3[0]);
     double rh[3], thh[3], phh[3];
     sph_frame(theta, phi, rh, thh, phh);

@@ -94,6 +94,15 @@ def test_force_through_dipole_order_closed_form():
     assert np.allclose(F0, QAt * QBt * R0 / R ** 3, rtol=1e-14, atol=0)
 
 
+def test_monopole_force_direction_near_the_pole():
+    A = np.array([[0.0, 0.0, 0.0, 0.8]])
+    B = np.array([[0.0, 0.0, 0.0, -0.6]])
+    for R0 in (np.array([1e-9, 0.0, 25.0]), np.array([0.0, -2e-10, -25.0])):
+        F = oracle.tcm_force(0, oracle.moments(A, np.zeros(3), 0), oracle.moments(B, np.zeros(3), 0), R0)
+        R = np.linalg.norm(R0)
+        assert np.allclose(F, 0.8 * -0.6 * R0 / R ** 3, rtol=0, atol=1e-15 * 0.48 / R ** 2)
+
+
 def test_rotation_derivative_of_moments_matches_finite_differences():
     B = ball_system(7, 9, 1.5)
     B = np.vstack([B, [[1e-3, 2e-3, 1.0, 0.4], [0.0, 0.0, -0.8, -0.4]]])  # atoms at the poles

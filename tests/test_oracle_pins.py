@@ -77,6 +77,19 @@ def test_ylm_matches_scipy_and_closed_forms():
     assert abs(oracle.ylm(1, 1, th, ph) - (-math.sqrt(3 / (8 * math.pi)) * math.sin(th) * complex(math.cos(ph), math.sin(ph)))) < 1e-15
     assert abs(oracle.ylm(1, 0, th, ph) - math.sqrt(3 / (4 * math.pi)) * math.cos(th)) < 1e-15
     assert abs(oracle.ylm(2, -2, th, ph) - math.sqrt(15 / (32 * math.pi)) * math.sin(th) ** 2 * complex(math.cos(2 * ph), -math.sin(2 * ph))) < 1e-15
+    # near the poles (the oracle's series branch): closed forms, and scipy where both are accurate
+    for th in (1e-9, 3e-3, math.pi - 3e-3, math.pi - 1e-9):
+        st, ct = math.sin(th), math.cos(th)
+        e = complex(math.cos(ph), math.sin(ph))
+        assert abs(oracle.ylm(1, 1, th, ph) - (-math.sqrt(3 / (8 * math.pi)) * st * e)) < 1e-15 * max(st, 1e-300) + 1e-300
+        assert abs(oracle.ylm(2, 1, th, ph) - (-math.sqrt(15 / (8 * math.pi)) * st * ct * e)) <= 1e-15 * st
+        assert abs(oracle.ylm(3, 3, th, ph) - (-math.sqrt(35 / (64 * math.pi)) * st ** 3 * e ** 3)) <= 1e-14 * st ** 3
+        assert abs(oracle.ylm(4, 0, th, ph) - 3 / (16 * math.sqrt(math.pi)) * (35 * ct ** 4 - 30 * ct ** 2 + 3)) < 1e-14
+    for th in (0.012, 0.02, math.pi - 0.015):
+        for l in (7, 24, 48):
+            for m in (0, 1, 2, 5):
+                ref = complex(sp.sph_harm_y(l, m, th, ph))
+                assert abs(oracle.ylm(l, m, th, ph) - ref) <= 1e-12 * max(1.0, abs(ref)), (th, l, m)
 
 
 # ----------------------------------------------------------------------------- moments, Eq. (multipole)
@@ -86,6 +99,8 @@ def test_moments_low_order_closed_forms():
     rng = np.random.default_rng(11)
     S = rand_system(rng, 37, 3.0, net_zero=False)
     c = np.array([0.3, -0.2, 0.1])
+    # atoms within 1e-9 of the poles: their polar angle must keep its digits
+    S = np.vstack([S, [[c[0] + 1e-9, c[1] + 2e-9, c[2] + 1.3, 0.7], [c[0] - 3e-10, c[1] + 1e-10, c[2] - 0.7, -0.4]]])
     Q = oracle.moments(S, c, 3)
     x, y, z = (S[:, :3] - c).T
     q = S[:, 3]
@@ -106,6 +121,8 @@ def test_moments_low_order_closed_forms():
     }
     for (l, m), v in exp.items():
         assert abs(Q[idx(l, m)] - v) <= 1e-13 * max(1.0, abs(v)), (l, m)
+    one = oracle.moments(np.array([[1e-9, 2e-9, 1.3, 1.0]]), np.zeros(3), 1)
+    assert abs(one[idx(1, 1)] - (-(1e-9 + 2e-9j) / math.sqrt(2))) < 1e-24
 
 
 def test_moments_addition_theorem_and_rotation():
