@@ -247,6 +247,14 @@ int tcm_gradients_batch(tcm_ctx_t ctx, int n_systems, const tcm_system* systems,
 int tcm_direct(tcm_ctx_t ctx, const tcm_system* A, const tcm_system* B, const double* rotB,
                const double* R0, double* E);
 
+/* Eq. (Coulomb) for many placements of B against A (a potential-energy-surface scan, Section
+ * IV): for item k, B rotated by rotB + 9 k (host row-major 3x3 array per item, or NULL for
+ * none) about its centre, with its centre at A's centre plus R0 + 3 k (host).  E: device,
+ * n_items doubles.  Double precision, one CTA per (item, 256 atoms of A), fixed-order sums.
+ * Asynchronous on the context stream. */
+int tcm_direct_batch(tcm_ctx_t ctx, const tcm_system* A, const tcm_system* B, int64_t n_items,
+                     const double* rotB, const double* R0, double* E);
+
 /* Largest atom count accepted by tcm_moments_noalloc. */
 #define TCM_NOALLOC_MAX_ATOMS 262144
 

@@ -650,8 +650,9 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const void* __restric
   __shared__ double sh[32];
   const double* cA = geo[0].c;
   const double* cB = geo[1].c;
-  const double* rot = xf;
-  const double* R0 = xf + 9;
+  const double* rot = xf + 12LL * blockIdx.y;  // this item's rotation of B and separation
+  const double* R0 = rot + 9;
+  part += (long long)blockIdx.y * gridDim.x;
   const long long i = (long long)blockIdx.x * kDirectThreads + threadIdx.x;
   double ax = 0.0, ay = 0.0, az = 0.0, qa = 0.0;
   if (i < na) {
@@ -691,15 +692,17 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const void* __restric
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
+// One CTA per item: each thread sums a contiguous stripe of the item's block partials, then a
+// fixed-order block sum.
 __global__ void k_direct_final(const double* __restrict__ part, int nblk, double* __restrict__ E) {
   __shared__ double sh[32];
+  part += (long long)blockIdx.x * nblk;
   double s = 0.0;
-  // each thread sums a contiguous stripe, then a fixed-order block sum
   const int per = (nblk + blockDim.x - 1) / blockDim.x;
   const int b0 = threadIdx.x * per;
   for (int k = b0; k < min(nblk, b0 + per); ++k) s += part[k];
   s = block_sum(s, sh);
-  if (threadIdx.x == 0) *E = s;
+  if (threadIdx.x == 0) E[blockIdx.x] = s;
 }
 
 }  // namespace
@@ -813,9 +816,13 @@ void contract_tables(double* t) {
 int direct_blocks(long long na) { return (int)((na + kDirectThreads - 1) / kDirectThreads); }
 
 int launch_direct(const void* a, long long na, int dta, const void* b, long long nb, int dtb, const SysGeom* geo,
-                  const double* xf, double* part, int nblk, double* E, cudaStream_t s) {
-  if (nblk > 0) k_direct<<<nblk, kDirectThreads, 0, s>>>(a, na, dta, b, nb, dtb, geo, xf, part);
-  k_direct_final<<<1, 256, 0, s>>>(part, nblk, E);
+                  const double* xf, int n_items, double* part, int nblk, double* E, cudaStream_t s) {
+  for (int i0 = 0; i0 < n_items; i0 += 65535) {  // grid.y limit
+    const int n = min(65535, n_items - i0);
+    if (nblk > 0) k_direct<<<dim3(nblk, n), kDirectThreads, 0, s>>>(a, na, dta, b, nb, dtb, geo, xf + 12LL * i0,
+                                                                    part + (long long)i0 * nblk);
+    k_direct_final<<<n, 128, 0, s>>>(part + (long long)i0 * nblk, nblk, E + i0);
+  }
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -959,11 +959,11 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
 }
 }  // namespace
 
-int tcm_direct(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, const double* rotB, const double* R0, double* E) {
-  TRY(check_ctx(c));
-  TRY(check_system(A, "tcm_direct A"));
-  TRY(check_system(B, "tcm_direct B"));
-  if (!R0 || !E) return set_err(TCM_EINVAL, "tcm_direct: null argument");
+namespace {
+// Eq. (Coulomb) for n items (B rotated by rotB[9 k] about its centre, at separation R0[3 k]);
+// energies to the device array dE.  Asynchronous.
+int direct_items(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, int64_t n, const double* rotB,
+                 const double* R0, double* dE) {
   tcm_system sys[2] = {*A, *B};
   for (auto& s : sys)
     if (s.has_center) s.radius = std::max(s.radius, 0.0);  // the direct sum needs centres only
@@ -972,39 +972,65 @@ int tcm_direct(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, const doub
   std::vector<GeomTile> gtiles;
   const int ngt = add_geom_jobs(sys, 2, used, gjobs, gtiles);
   std::vector<SysGeom> geoms{host_geom(sys[0]), host_geom(sys[1])};
-  std::vector<double> xf(12);
-  if (rotB)
-    std::memcpy(xf.data(), rotB, 9 * sizeof(double));
-  else
-    identity(xf.data());
-  for (int d = 0; d < 3; ++d) xf[9 + d] = R0[d];
+  std::vector<double> xf(12 * (size_t)n);
+  for (int64_t k = 0; k < n; ++k) {
+    if (rotB)
+      std::memcpy(&xf[12 * k], rotB + 9 * k, 9 * sizeof(double));
+    else
+      identity(&xf[12 * k]);
+    for (int d = 0; d < 3; ++d) xf[12 * k + 9 + d] = R0[3 * k + d];
+  }
   Packer pk;
   const size_t o_geo = pk.add(geoms), o_xf = pk.add(xf), o_gj = pk.add(gjobs), o_gt = pk.add(gtiles);
+  const int nblk = direct_blocks(A->n);
+  if (!gjobs.empty())
+    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
+  TRY(dev_ensure(c, c->dpart, (size_t)std::max<int64_t>(nblk * n, 1) * sizeof(double)));
   char* base = nullptr;
   TRY(upload(c, pk, &base));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   if (!gjobs.empty()) {
-    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
     TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
     PhaseScope ps(c, TCM_PHASE_GEOM, 2);
     TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
                            static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
   }
-  const int nblk = direct_blocks(A->n);
-  TRY(dev_ensure(c, c->dpart, (size_t)std::max(nblk, 1) * sizeof(double)));
+  const int nlaunch = (int)((n + 65534) / 65535) * (nblk > 0 ? 2 : 1);
+  PhaseScope ps(c, TCM_PHASE_DIRECT, nlaunch);
+  TRY_LAUNCH(launch_direct(A->xyzq, A->n, A->dtype, B->xyzq, B->n, B->dtype, d_geo,
+                           reinterpret_cast<double*>(base + o_xf), (int)n, static_cast<double*>(c->dpart.p), nblk, dE,
+                           c->stream));
+  return TCM_OK;
+}
+}  // namespace
+
+int tcm_direct(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, const double* rotB, const double* R0, double* E) {
+  TRY(check_ctx(c));
+  TRY(check_system(A, "tcm_direct A"));
+  TRY(check_system(B, "tcm_direct B"));
+  if (!R0 || !E) return set_err(TCM_EINVAL, "tcm_direct: null argument");
   TRY(dev_ensure(c, c->escr, 64));
   double* dE = static_cast<double*>(c->escr.p);
-  {
-    PhaseScope ps(c, TCM_PHASE_DIRECT, nblk > 0 ? 2 : 1);
-    TRY_LAUNCH(launch_direct(A->xyzq, A->n, A->dtype, B->xyzq, B->n, B->dtype, d_geo,
-                             reinterpret_cast<double*>(base + o_xf), static_cast<double*>(c->dpart.p), nblk, dE,
-                             c->stream));
-  }
+  TRY(direct_items(c, A, B, 1, rotB, R0, dE));
   TRY_CUDA(cudaMemcpyAsync(c->pinned_small, dE, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   TRY_CUDA(cudaStreamSynchronize(c->stream));
   *E = *static_cast<const double*>(c->pinned_small);
   return TCM_OK;
+}
+
+int tcm_direct_batch(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, int64_t n_items, const double* rotB,
+                     const double* R0, double* E) {
+  TRY(check_ctx(c));
+  TRY(check_system(A, "tcm_direct_batch A"));
+  TRY(check_system(B, "tcm_direct_batch B"));
+  if (n_items < 0) return set_err(TCM_EINVAL, "tcm_direct_batch: negative count");
+  if (n_items == 0) return TCM_OK;
+  if (!R0 || !E) return set_err(TCM_EINVAL, "tcm_direct_batch: null argument");
+  if (n_items > (1LL << 30)) return set_err(TCM_EINVAL, "tcm_direct_batch: too many items");
+  if ((int64_t)direct_blocks(A->n) * n_items > (1LL << 34))
+    return set_err(TCM_EINVAL, "tcm_direct_batch: A's blocks x items exceeds the partial-sum buffer limit");
+  return direct_items(c, A, B, n_items, rotB, R0, E);
 }
 
 }  // extern "C"

@@ -161,23 +161,5 @@ int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, cons
                     const int2* cmap, const int* cmap_off, const double* ftab, int kmax, cudaStream_t s);
 
 
-// Rotation W = R_y(-beta) R_z(-alpha) taking R0hat to the z axis (row-major).
-__host__ __device__ inline void frame_rotation(const double* R0, double* W) {
-  const double x = R0[0], y = R0[1], z = R0[2];
-  const double R = sqrt(x * x + y * y + z * z);
-  const double rho = sqrt(x * x + y * y);
-  const double cb = z / R, sb = rho / R;
-  const double ca = rho > 0.0 ? x / rho : 1.0, sa = rho > 0.0 ? y / rho : 0.0;
-  W[0] = cb * ca; W[1] = cb * sa; W[2] = -sb;
-  W[3] = -sa;     W[4] = ca;      W[5] = 0.0;
-  W[6] = sb * ca; W[7] = sb * sa; W[8] = cb;
-}
-int launch_direct(const void* a, long long na, int dta, const void* b, long long nb, int dtb,
-                  const SysGeom* geo /* device: [A, B] centres */, const double* xf /* device: rot[9], R0[3] */,
-                  double* part, int nblk, double* E, cudaStream_t s);
-int direct_blocks(long long na);
-
-// Sets the calling thread's tcm_last_error() message; returns code.
-int record_error(int code, const char* msg);
 
 }  // namespace tcm

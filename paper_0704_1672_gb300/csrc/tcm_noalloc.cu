@@ -21,7 +21,7 @@
 #include <mutex>
 #include <vector>
 
-#include "tcm_internal.h"
+#include "contract.h"
 
 using namespace tcm;
 

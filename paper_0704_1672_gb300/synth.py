@@ -263,3 +263,39 @@ def request_orientations(seed, k, a_sum, r_lo=1.2, r_hi=3.0):
     rot = random_rotations(rng, k)
     R0 = unit_vectors(rng, k) * (rng.uniform(r_lo, r_hi, k) * a_sum)[:, None]
     return rot, R0
+
+
+@dataclass
+class PesGrid:
+    """Two fixed systems and a grid of separations in the xy-plane: R0 = R (cos T, sin T, 0)."""
+    A: np.ndarray
+    B: np.ndarray
+    R: np.ndarray       # (nR,) centre distances
+    theta: np.ndarray   # (nT,) angles from the x axis, degrees
+    lmax: tuple
+    name: str = ""
+
+    def R0(self):
+        """(nR * nT, 3) separations, R-major."""
+        t = np.radians(self.theta)
+        RR, TT = np.meshgrid(self.R, t, indexing="ij")
+        return np.stack([RR * np.cos(TT), RR * np.sin(TT), np.zeros_like(RR)], axis=-1).reshape(-1, 3)
+
+
+def pes_grid_pair(seed=6, n_a=3260, n_b=2587, r_lo=58.0, r_hi=100.0, dr=1.0, dtheta=1.0,
+                  lmax=(1, 2, 3, 4, 6, 8, 10)):
+    """The shape of the protein-protein surface scan of Section IV: two protein-sized systems
+    (5,847 atoms together, split as 223 : 177 residues) fixed in space, the centre of B moved
+    over R0 in [r_lo, r_hi] A and Theta in [0, 360) degrees in the xy-plane, energies at several
+    Lmax.  Synthetic stand-ins: compact random-walk chains (bond 1.5 A) confined to spheres of
+    radius 1.75 N^(1/3) A, N(0, 0.3) net-zero charges."""
+    rng = np.random.default_rng(seed)
+    pa, pb = random_walk_chains(rng, [n_a, n_b], [1.75 * n_a ** (1 / 3), 1.75 * n_b ** (1 / 3)])
+    A = pack(pa, charges_normal_net_zero(rng, n_a))
+    B = pack(pb, charges_normal_net_zero(rng, n_b))
+    R = np.arange(r_lo, r_hi + 0.5 * dr, dr)
+    theta = np.arange(0.0, 360.0, dtheta)
+    return PesGrid(A, B, R, theta, tuple(lmax),
+                   name=f"surface scan, {n_a} + {n_b} random-walk atoms, R0 in [{r_lo},{r_hi}] A x {len(theta)} angles "
+                        f"in the xy-plane, Lmax in {tuple(lmax)}")
+

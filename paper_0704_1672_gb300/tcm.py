@@ -82,6 +82,7 @@ def lib():
         L.tcm_ctx_set_graphs.argtypes = [P, i32]
         L.tcm_ctx_set_rotate_cached.argtypes = [P, i32]
         L.tcm_gradients_batch.argtypes = [P, i32, P, ctypes.c_int64, P, i32, P, P, P]
+        L.tcm_direct_batch.argtypes = [P, P, P, ctypes.c_int64, P, P, P]
         L.tcm_rotate_moments.argtypes = [P, ctypes.c_int64, P, P, P]
         L.tcm_ctx_graph_stats.argtypes = [P, P, P]
         L.tcm_ctx_read_profile.argtypes = [P, P, P]
@@ -89,7 +90,8 @@ def lib():
                      "tcm_energy_batch", "tcm_direct", "tcm_ctx_set_profiling", "tcm_ctx_read_profile",
                      "tcm_moments_noalloc", "tcm_ctx_set_tiling", "tcm_ctx_set_graphs", "tcm_ctx_graph_stats",
                      "tcm_ctx_set_tiling_l", "tcm_ctx_get_tiling_l",
-                     "tcm_ctx_set_rotate_cached", "tcm_rotate_moments", "tcm_gradients_batch"):
+                     "tcm_ctx_set_rotate_cached", "tcm_rotate_moments", "tcm_gradients_batch",
+                     "tcm_direct_batch"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -327,6 +329,20 @@ class Context:
         E = ctypes.c_double()
         _check(lib().tcm_direct(self._h, ctypes.byref(sa), ctypes.byref(sb), _dptr(r), _dptr(R), ctypes.byref(E)))
         return E.value
+
+    def tcm_direct_batch(self, A, B, R0, rotB=None, cA=None, cB=None, E=None):
+        """Eq. (Coulomb) for k placements of B (R0: (k, 3); rotB: (k, 3, 3) or None); returns the
+        (k,) device tensor of energies (asynchronous)."""
+        sa = make_system(A, center=cA)
+        sb = make_system(B, center=cB)
+        R = np.ascontiguousarray(R0, dtype=np.float64).reshape(-1, 3)
+        k = len(R)
+        r = None if rotB is None else np.ascontiguousarray(rotB, dtype=np.float64).reshape(k, 9)
+        if E is None:
+            E = torch.empty(k, dtype=torch.float64, device=A.device)
+        _check(lib().tcm_direct_batch(self._h, ctypes.byref(sa), ctypes.byref(sb), k, _dptr(r), _dptr(R),
+                                      ctypes.c_void_p(E.data_ptr())))
+        return E
 
 
 NOALLOC_MAX_ATOMS = 262144
