@@ -31,6 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "atom-moments/s and TCM energies/s vs plain FP64 GPU path at stated error; p50/p99"
 UNIT = "atom-moments/s"
 FP32_LANES_PER_SM = 128
+FP64_PER_SM_CLK = 2          # FP64 pipe results per SM per clock (GB300)
+DIRECT_FP64_PER_PAIR = 10    # algorithmic FP64 operations per pair of Eq. (Coulomb), besides the rsqrt
 
 
 def parse():
@@ -44,6 +46,7 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--no-pes-grid", action="store_true", help="skip the surface-scan measurement")
     return p.parse_args()
 
 
@@ -342,6 +345,12 @@ def run_ours(args, rank, world, dist):
                             "kernel (O(L^3)); no atom pass per step"}
     rc_ctx.close()
 
+    # the surface scan of Section IV: every grid point at several Lmax from cached moments,
+    # and the exact energy of every grid point by the batched direct-sum kernel
+    pes_grid = None
+    if not args.no_pes_grid and rank == 0:
+        pes_grid = run_pes_grid(torch, tcm, prec, n_sm, sm_max_mhz(), stream)
+
     # end to end through the C ABI with host buffers: H2D of the coordinates, D2H of the energies
     e2e = None
     if args.e2e_steps > 0:
@@ -396,11 +405,49 @@ def run_ours(args, rank, world, dist):
                 "phase_ms_per_step": phases, "gpu_launches": int(sum(launches.values())),
                 "gpu_launches_per_step": {p: launches[p] / args.steps for p in launches},
                 "roofline": roofline, "clocks": ck, "e2e": e2e, "graph_replay": graph_replay,
-                "rotate_cached": rotate_cached,
+                "rotate_cached": rotate_cached, "pes_grid": pes_grid,
                 "fp64_plain_gpu": fp64_plain,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def sm_max_mhz():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", 2070.0))
+    except (OSError, ValueError):
+        return 2070.0
+
+
+def run_pes_grid(torch, tcm, prec, n_sm, sm_mhz, stream):
+    """Surface scan (Section IV shapes): 43 x 360 grid in the xy-plane, Lmax in {1,2,3,4,6,8,10},
+    TCM energies from cached moments and exact energies at every point."""
+    from paper_0704_1672_gb300 import pes, synth
+    g = synth.pes_grid_pair()
+    A = torch.tensor(g.A, device="cuda")
+    B = torch.tensor(g.B, device="cuda")
+    R0 = g.R0()
+    ctx = tcm.Context(lmax_cap=max(g.lmax), stream=stream)
+    try:
+        pes.scan(ctx, A, B, R0[:64], g.lmax, precision=prec)  # warm-up (kernel attributes, buffers)
+        res = pes.scan(ctx, A, B, R0, g.lmax, precision=prec)
+    finally:
+        ctx.close()
+    n = len(R0)
+    t = res.timings_ms
+    pairs = n * len(g.A) * len(g.B)
+    achieved = pairs * DIRECT_FP64_PER_PAIR / (t["direct"] * 1e-3) / 1e9
+    peak = n_sm * FP64_PER_SM_CLK * sm_mhz * 1e6 / 1e9
+    return {"workload": g.name, "points": n, "lmax": list(g.lmax),
+            "tcm_energies": n * len(g.lmax), "tcm_ms": t["tcm_energies"], "moments_ms": t["moments"],
+            "tcm_energies_per_s": n * len(g.lmax) / (t["tcm_energies"] * 1e-3),
+            "direct_ms": t["direct"], "direct_pairs_per_s": pairs / (t["direct"] * 1e-3),
+            "direct_roofline": {"bound": "fp64", "kernel": "k_direct", "achieved": achieved, "peak": peak,
+                                "unit": "G FP64 op/s", "frac": achieved / peak,
+                                "algorithmic_fp64_per_pair": DIRECT_FP64_PER_PAIR,
+                                "peak_source": f"{n_sm} SMs x {FP64_PER_SM_CLK} FP64/clk x {sm_mhz:.0f} MHz"},
+            "eq_error_percent_median": {str(L): float(np.median(res.eta(L))) for L in g.lmax},
+            "eq_error_percent_max": {str(L): float(np.max(res.eta(L))) for L in g.lmax}}
 
 
 def plain_fp64(ctx, tcm, torch, A, B, s, steps):
