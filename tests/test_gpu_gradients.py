@@ -82,7 +82,8 @@ def test_degrees_and_directions_fp64(ctx, tcm, L):
     rng = np.random.default_rng(40 + L)
     A = synth.pack(synth.uniform_ball(rng, 300, 5.0), synth.charges_uniform_net_zero(rng, 300))
     B = synth.pack(synth.uniform_ball(rng, 250, 4.0), synth.charges_uniform_net_zero(rng, 250))
-    A[:, 3] += 0.05  # nonzero monopoles too
+    A[:, 3] += 0.05  # nonzero monopoles too (the L = 0 force is their product)
+    B[:, 3] -= 0.04
     dirs = np.array([[0, 0, 1.0], [0, 0, -1.0], [1e-9, 0, 1.0], [0.3, -0.4, 0.5], [-1.0, 0.0, 0.0]])
     R0 = dirs / np.linalg.norm(dirs, axis=1)[:, None] * 25.0
     k = len(R0)
