@@ -85,8 +85,9 @@ __device__ __forceinline__ P2<T> pair(T a, T b) {
 // Register state of one column chunk [M0, M1).  The kernels carry H_j = sigma_j G_{m+j}
 // (sigma = +, +, -, -, +, +, ... along each column), for which the recurrence reads
 //   H_{j+1} = (-1)^j k_{m+j,m} c H_j + H_{j-1}
-// without a subtraction, so a complex step is one packed multiply (t, t) = (k', k') (c, c),
-// one packed FMA for the recurrence and one packed FMA for the accumulation.  The sign
+// without a subtraction.  Complex columns go in pairs (acc_slot in tcm_internal.h): one packed
+// multiply (k_a c, k_b c), two packed FMAs for the recurrences of both columns and two packed
+// FMAs for their accumulation, 5 packed instructions per two complex steps.  The sign
 // sigma_{l-m} is part of the finalisation factor.
 template <typename T, int L, int M0, int M1>
 struct Regs {
@@ -113,50 +114,137 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
   s = t;
 }
 
-// Column m at degree l: advance its recurrence and accumulate qr * H.
+// The signed recurrence coefficient of step jj (>= 2) along column m at degree l.
+template <typename T, int l, int m>
+__device__ __forceinline__ constexpr T kstep() {
+  return (T)((((l - m) - 1) & 1) ? -kcoef(l - 1, m) : kcoef(l - 1, m));
+}
+
+// Recurrence coefficients as pair operands in constant memory, so that the packed multiply
+// (t_a, t_b) = (k_a, k_b) (c, c) reads them straight from the constant bank instead of
+// building each pair in registers:
+//   two[l][m]  = (k of column m, k of column m + 1) at degree l (1 for column m+1's first
+//                step, jj = 1, which is G = c G), for a column pair (m, m+1) with l >= m + 2;
+//   one[l][m]  = (k, k) of a single column m at degree l >= m + 2.
+template <typename T>
+struct KPairs {
+  P2<T> two[kLmaxMax + 1][kLmaxMax + 1];
+  P2<T> one[kLmaxMax + 1][kLmaxMax + 1];
+  constexpr KPairs() : two(), one() {
+    for (int l = 0; l <= kLmaxMax; ++l)
+      for (int m = 0; m <= kLmaxMax; ++m) {
+        if (l < m + 2) continue;
+        const T ka = (T)((((l - m) - 1) & 1) ? -kcoef(l - 1, m) : kcoef(l - 1, m));
+        const T kb = l == m + 2 ? (T)1 : (T)((((l - m - 1) - 1) & 1) ? -kcoef(l - 1, m + 1) : kcoef(l - 1, m + 1));
+        two[l][m].x = ka;
+        two[l][m].y = kb;
+        one[l][m].x = ka;
+        one[l][m].y = ka;
+      }
+  }
+};
+static_assert(KPairs<float>().two[5][1].x != 0.0f && KPairs<float>().two[3][1].y == 1.0f,
+              "the coefficient table must be a constant expression");
+static __constant__ KPairs<float> c_kpairs_f = KPairs<float>();
+static __constant__ KPairs<double> c_kpairs_d = KPairs<double>();
+template <typename T>
+__device__ __forceinline__ const KPairs<T>& kpairs();
+template <>
+__device__ __forceinline__ const KPairs<float>& kpairs<float>() { return c_kpairs_f; }
+template <>
+__device__ __forceinline__ const KPairs<double>& kpairs<double>() { return c_kpairs_d; }
+
+// Advance the running diagonal power (dr, di) = u^m to the next column.
+template <typename T, int L, int M0, int M1>
+__device__ __forceinline__ void next_power(Regs<T, L, M0, M1>& s, T ux, T uy) {
+  const T nr = s.dr * ux - s.di * uy;
+  const T ni = s.dr * uy + s.di * ux;
+  s.dr = nr;
+  s.di = ni;
+}
+
+// Column 0 (real) at degree l.
+template <typename T, int L, int M0, int M1, int l>
+__device__ __forceinline__ void col0_step(Regs<T, L, M0, M1>& s, P2<T> cc, P2<T> qq) {
+  if constexpr (l == 0) {
+    s.g0 = (T)1;
+  } else if constexpr (l == 1) {
+    s.p0 = s.g0;
+    s.g0 = cc.x;
+  } else {
+    const T t = kstep<T, l, 0>() * cc.x;
+    const T n = fmaT(t, s.g0, s.p0);
+    s.p0 = s.g0;
+    s.g0 = n;
+  }
+  if constexpr (l == 0 && sizeof(T) == 4)
+    two_sum_acc(s.q00, s.q00e, qq.x);  // G_00 = 1
+  else
+    s.acc0[l] = fmaT(qq.x, s.g0, s.acc0[l]);
+}
+
+// A single complex column m at degree l: (Re, Im) in one pair register.
 template <typename T, int L, int M0, int M1, int l, int m>
-__device__ __forceinline__ void col_step(Regs<T, L, M0, M1>& s, T ux, T uy, P2<T> cc, P2<T> qq) {
+__device__ __forceinline__ void single_step(Regs<T, L, M0, M1>& s, T ux, T uy, P2<T> cc, P2<T> qq) {
   if constexpr (m <= l) {
     constexpr int j = m - M0;
-    constexpr int jj = l - m;  // index along the column
-    if constexpr (m == 0) {
-      if constexpr (jj == 0) {
-        s.g0 = (T)1;
-      } else if constexpr (jj == 1) {
-        s.p0 = s.g0;
-        s.g0 = cc.x;
-      } else {
-        constexpr T k = (T)(((jj - 1) & 1) ? -kcoef(l - 1, 0) : kcoef(l - 1, 0));
-        const T t = k * cc.x;
-        const T n = fmaT(t, s.g0, s.p0);
-        s.p0 = s.g0;
-        s.g0 = n;
-      }
-      if constexpr (jj == 0 && sizeof(T) == 4)
-        two_sum_acc(s.q00, s.q00e, qq.x);  // G_00 = 1
-      else
-        s.acc0[l] = fmaT(qq.x, s.g0, s.acc0[l]);
+    if constexpr (l == m) {
+      if constexpr (m > M0) next_power(s, ux, uy);
+      s.g[j] = pair<T>(s.dr, s.di);
+    } else if constexpr (l == m + 1) {
+      s.p[j] = s.g[j];
+      s.g[j] = mul2(cc, s.g[j]);
     } else {
-      if constexpr (jj == 0) {
-        if constexpr (m > M0) {
-          const T nr = s.dr * ux - s.di * uy;
-          const T ni = s.dr * uy + s.di * ux;
-          s.dr = nr;
-          s.di = ni;
-        }
-        s.g[j] = pair<T>(s.dr, s.di);
-      } else if constexpr (jj == 1) {
-        s.p[j] = s.g[j];
-        s.g[j] = mul2(cc, s.g[j]);
+      const P2<T> tt = mul2(cc, kpairs<T>().one[l][m]);
+      const P2<T> n = fma2(tt, s.g[j], s.p[j]);
+      s.p[j] = s.g[j];
+      s.g[j] = n;
+    }
+    constexpr int a = (acc_slot(L, M0, M1, l, m, 0) - Regs<T, L, M0, M1>::N0) / 2;
+    s.accp[a] = fma2(qq, s.g[j], s.accp[a]);
+  }
+}
+
+// A pair of complex columns (ma, mb = ma + 1) at degree l.  Registers: g[ja] = (Re_a, Re_b),
+// g[jb] = (Im_a, Im_b), and the same for the previous level in p.  From l = mb + 1 on one packed
+// multiply (k_a c, k_b c) and two packed FMAs advance both columns; column b's first step
+// (jj = 1, G = c G) is the general step with k = 1 and a zero previous value.
+template <typename T, int L, int M0, int M1, int l, int ma>
+__device__ __forceinline__ void pair_step(Regs<T, L, M0, M1>& s, T ux, T uy, P2<T> cc, P2<T> qq) {
+  if constexpr (ma <= l) {
+    constexpr int ja = ma - M0, jb = ja + 1, mb = ma + 1;
+    using R = Regs<T, L, M0, M1>;
+    if constexpr (l == ma) {  // seed column a
+      if constexpr (ma > M0) next_power(s, ux, uy);
+      s.g[ja].x = s.dr;
+      s.g[jb].x = s.di;
+      constexpr int a = (acc_slot(L, M0, M1, l, ma, 0) - R::N0) / 2;
+      s.accp[a].x = fmaT(qq.x, s.dr, s.accp[a].x);
+      s.accp[a].y = fmaT(qq.x, s.di, s.accp[a].y);
+    } else {
+      if constexpr (l == mb) {  // column a: G = c G; column b: seed
+        s.p[ja].x = s.g[ja].x;
+        s.p[jb].x = s.g[jb].x;
+        s.g[ja].x = cc.x * s.g[ja].x;
+        s.g[jb].x = cc.x * s.g[jb].x;
+        next_power(s, ux, uy);
+        s.g[ja].y = s.dr;
+        s.g[jb].y = s.di;
+        s.p[ja].y = (T)0;
+        s.p[jb].y = (T)0;
       } else {
-        constexpr T k = (T)(((jj - 1) & 1) ? -kcoef(l - 1, m) : kcoef(l - 1, m));
-        const P2<T> tt = mul2(cc, pair<T>(k, k));
-        const P2<T> n = fma2(tt, s.g[j], s.p[j]);
-        s.p[j] = s.g[j];
-        s.g[j] = n;
+        const P2<T> tt = mul2(cc, kpairs<T>().two[l][ma]);
+        const P2<T> nr = fma2(tt, s.g[ja], s.p[ja]);
+        const P2<T> ni = fma2(tt, s.g[jb], s.p[jb]);
+        s.p[ja] = s.g[ja];
+        s.p[jb] = s.g[jb];
+        s.g[ja] = nr;
+        s.g[jb] = ni;
       }
-      constexpr int a = (chunk_off(L, M0, m) - Regs<T, L, M0, M1>::N0) / 2 + jj;
-      s.accp[a] = fma2(qq, s.g[j], s.accp[a]);
+      constexpr int ar = (acc_slot(L, M0, M1, l, ma, 0) - R::N0) / 2;  // (Re_a, Re_b)
+      constexpr int ai = (acc_slot(L, M0, M1, l, ma, 1) - R::N0) / 2;  // (Im_a, Im_b)
+      s.accp[ar] = fma2(qq, s.g[ja], s.accp[ar]);
+      s.accp[ai] = fma2(qq, s.g[jb], s.accp[ai]);
     }
   }
 }
@@ -164,8 +252,16 @@ __device__ __forceinline__ void col_step(Regs<T, L, M0, M1>& s, T ux, T uy, P2<T
 template <typename T, int L, int M0, int M1, int l, int m>
 __device__ __forceinline__ void level_cols(Regs<T, L, M0, M1>& s, T ux, T uy, P2<T> cc, P2<T> qq) {
   if constexpr (m < M1) {
-    col_step<T, L, M0, M1, l, m>(s, ux, uy, cc, qq);
-    level_cols<T, L, M0, M1, l, m + 1>(s, ux, uy, cc, qq);
+    if constexpr (m == 0) {
+      col0_step<T, L, M0, M1, l>(s, cc, qq);
+      level_cols<T, L, M0, M1, l, 1>(s, ux, uy, cc, qq);
+    } else if constexpr (acc_pair_a(M0, M1, m)) {
+      pair_step<T, L, M0, M1, l, m>(s, ux, uy, cc, qq);
+      level_cols<T, L, M0, M1, l, m + 2>(s, ux, uy, cc, qq);
+    } else {
+      single_step<T, L, M0, M1, l, m>(s, ux, uy, cc, qq);
+      level_cols<T, L, M0, M1, l, m + 1>(s, ux, uy, cc, qq);
+    }
   }
 }
 

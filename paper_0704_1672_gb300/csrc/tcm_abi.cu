@@ -386,12 +386,11 @@ int build_tables(tcm_ctx* c) {
         const int m0 = plan_m0(L, kmax, nch, ch), m1 = plan_m0(L, kmax, nch, ch + 1);
         for (int m = m0; m < m1; ++m)
           for (int l = m; l <= L; ++l) {
-            const int slot = chunk_off(L, m0, m) + (m == 0 ? l : 2 * (l - m));
             if (m == 0) {
-              cmap[pi][off[L] + l * l] = make_int2(ch, slot);
+              cmap[pi][off[L] + l * l] = make_int2(ch, acc_slot(L, m0, m1, l, 0, 0));
             } else {
-              cmap[pi][off[L] + l * l + 2 * m - 1] = make_int2(ch, slot);
-              cmap[pi][off[L] + l * l + 2 * m] = make_int2(ch, slot + 1);
+              cmap[pi][off[L] + l * l + 2 * m - 1] = make_int2(ch, acc_slot(L, m0, m1, l, m, 0));
+              cmap[pi][off[L] + l * l + 2 * m] = make_int2(ch, acc_slot(L, m0, m1, l, m, 1));
             }
           }
       }

@@ -79,6 +79,35 @@ __host__ __device__ constexpr int chunk_off(int L, int m0, int m) {
   return o;
 }
 
+// Accumulator layout of a chunk [m0, m1) at degree L.  Column 0 (real) takes slots 0..L.
+// The complex columns from c0 = max(m0, 1) are grouped in pairs (c0, c0+1), (c0+2, c0+3), ...
+// (a last column left over stays single).  A pair (a, b = a+1) keeps Re and Im of its two
+// columns side by side, so one packed instruction advances both columns:
+//   slots o, o+1                       Re, Im of column a at l = a
+//   slots o+2+4(l-b) + {0, 1, 2, 3}    Re_a, Re_b, Im_a, Im_b at l >= b
+// and a single column m keeps (Re, Im) at o + 2(l-m) + {0, 1}; o = chunk_off(L, m0, first column).
+__host__ __device__ constexpr int acc_first_complex(int m0) { return m0 == 0 ? 1 : m0; }
+__host__ __device__ constexpr bool acc_pair_a(int m0, int m1, int m) {
+  return m >= acc_first_complex(m0) && ((m - acc_first_complex(m0)) % 2 == 0) && m + 1 < m1;
+}
+__host__ __device__ constexpr bool acc_pair_b(int m0, int m1, int m) {
+  return m > acc_first_complex(m0) && acc_pair_a(m0, m1, m - 1);
+}
+// Slot of component (l, m), part 0 = Re, 1 = Im (part ignored in column 0).
+__host__ __device__ constexpr int acc_slot(int L, int m0, int m1, int l, int m, int part) {
+  if (m == 0) return l;
+  if (acc_pair_a(m0, m1, m)) {
+    const int o = chunk_off(L, m0, m);
+    if (l == m) return o + part;
+    return o + 2 + 4 * (l - m - 1) + 2 * part;
+  }
+  if (acc_pair_b(m0, m1, m)) {
+    const int o = chunk_off(L, m0, m - 1);
+    return o + 2 + 4 * (l - m) + 2 * part + 1;
+  }
+  return chunk_off(L, m0, m) + 2 * (l - m) + part;
+}
+
 // Recurrence coefficient k_lm (l >= m+1), from the ratio r_l = s_l / s_l-1 of the
 // normalisations s_lm with F_lm = P_l^m e^{i m phi} = s_lm G_lm:
 //   s_mm = (2m-1)!!, s_m+1,m = (2m+1) s_mm, s_l+1 = (l+m) s_l-1 / (l-m+1).
