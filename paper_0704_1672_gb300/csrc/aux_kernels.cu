@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(256) k_finalize(const MomJob* __restrict__ job
 //   U = sum_{l1,l2} (-1)^l2 (l1+l2)! / R^{l1+l2+1}
 //         [Qhat'^A_l1,0 Qhat'^B_l2,0 + 2 sum_{m>=1} (-1)^m Re(Qhat'^A_l1m conj(Qhat'^B_l2m))]
 // (real charges: Q_l,-m = (-1)^m conj(Q_lm)).  Moments enter in the rotated frame: those of B
-// either come from the moment kernels with W folded into the atom transform (item flag
-// b_in_frame) or, like those of A, are rotated here:
+// either come from the moment kernels with W folded into the atom transform (mode kBInFrame),
+// or, like those of A, are rotated here (kBLab by W; kBRotate by W rotB from a moment cache):
 //   Q'_lm = sum_m' e^{-i m' alpha} d^l_{m'm}(beta) Q_lm'
 // with the Wigner d^l_{ab}, a >= |b|, from the three-term recursion in l started at
 //   d^a_{ab} = (-1)^{a-b} sqrt(C(2a, a+b)) cos^{a+b}(beta/2) sin^{a-b}(beta/2),
