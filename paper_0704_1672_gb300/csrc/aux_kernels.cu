@@ -86,13 +86,22 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom_centroid(const GeomJob* _
   const GeomJob j = gj[tile.gjob];
   const long long i0 = (long long)tile.t * kGeomTileAtoms;
   const long long i1 = min(j.n, i0 + (long long)kGeomTileAtoms);
+  // all of this thread's loads are issued before the sums (the data arrive from DRAM)
+  constexpr int kPer = kGeomTileAtoms / kGeomThreads;
+  double x[kPer], y[kPer], z[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const long long i = i0 + threadIdx.x + (long long)k * kGeomThreads;
+    double q;
+    x[k] = y[k] = z[k] = 0.0;
+    if (i < i1) load_xyz(j.xyzq, j.dtype, i, x[k], y[k], z[k], q);
+  }
   double sx = 0.0, sy = 0.0, sz = 0.0;
-  for (long long i = i0 + threadIdx.x; i < i1; i += kGeomThreads) {
-    double x, y, z, q;
-    load_xyz(j.xyzq, j.dtype, i, x, y, z, q);
-    sx += x;
-    sy += y;
-    sz += z;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    sx += x[k];
+    sy += y[k];
+    sz += z[k];
   }
   sx = block_sum(sx, sh);
   sy = block_sum(sy, sh);
@@ -107,16 +116,26 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom_centroid(const GeomJob* _
   }
   __syncthreads();
   if (!s_last) return;
+  // the last CTA adds the tile sums: every thread a strided subset in tile order (loads in
+  // parallel, through L2), then the fixed-order block sum
+  __threadfence();
+  const double* p = gpart + 4LL * j.tile_base;
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+  for (int t = threadIdx.x; t < j.n_tiles; t += kGeomThreads) {
+    t0 += __ldcg(p + 4 * t);
+    t1 += __ldcg(p + 4 * t + 1);
+    t2 += __ldcg(p + 4 * t + 2);
+  }
+  t0 = block_sum(t0, sh);
+  t1 = block_sum(t1, sh);
+  t2 = block_sum(t2, sh);
   if (threadIdx.x == 0) {
-    __threadfence();
     tickets[tile.gjob] = 0;
     if (j.need_center) {
-      double s[3] = {0.0, 0.0, 0.0};
-      const volatile double* p = gpart + 4LL * j.tile_base;
-      for (int t = 0; t < j.n_tiles; ++t)
-        for (int d = 0; d < 3; ++d) s[d] += p[4 * t + d];
       const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
-      for (int d = 0; d < 3; ++d) geoms[j.geom].c[d] = s[d] * inv;
+      geoms[j.geom].c[0] = t0 * inv;
+      geoms[j.geom].c[1] = t1 * inv;
+      geoms[j.geom].c[2] = t2 * inv;
     }
   }
 }
@@ -133,12 +152,22 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom_radius(const GeomJob* __r
   const double cx = geoms[j.geom].c[0], cy = geoms[j.geom].c[1], cz = geoms[j.geom].c[2];
   const long long i0 = (long long)tile.t * kGeomTileAtoms;
   const long long i1 = min(j.n, i0 + (long long)kGeomTileAtoms);
+  constexpr int kPer = kGeomTileAtoms / kGeomThreads;
+  double x[kPer], y[kPer], z[kPer];
+  bool ok[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const long long i = i0 + threadIdx.x + (long long)k * kGeomThreads;
+    double q;
+    ok[k] = i < i1;
+    x[k] = y[k] = z[k] = 0.0;
+    if (ok[k]) load_xyz(j.xyzq, j.dtype, i, x[k], y[k], z[k], q);
+  }
   double mx = 0.0;
-  for (long long i = i0 + threadIdx.x; i < i1; i += kGeomThreads) {
-    double x, y, z, q;
-    load_xyz(j.xyzq, j.dtype, i, x, y, z, q);
-    const double dx = x - cx, dy = y - cy, dz = z - cz;
-    mx = fmax(mx, dx * dx + dy * dy + dz * dz);
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const double dx = x[k] - cx, dy = y[k] - cy, dz = z[k] - cz;
+    if (ok[k]) mx = fmax(mx, dx * dx + dy * dy + dz * dz);
   }
   mx = block_max(mx, sh);
   if (threadIdx.x == 0) {
@@ -148,24 +177,23 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom_radius(const GeomJob* __r
   }
   __syncthreads();
   if (!s_last) return;
+  __threadfence();
+  const double* p = gpart + 4LL * j.tile_base;
+  double m = 0.0;
+  for (int t = threadIdx.x; t < j.n_tiles; t += kGeomThreads) m = fmax(m, __ldcg(p + 4 * t + 3));
+  m = block_max(m, sh);
   if (threadIdx.x == 0) {
-    __threadfence();
     tickets[tile.gjob] = 0;
-    if (j.need_radius) {
-      const volatile double* p = gpart + 4LL * j.tile_base;
-      double m = 0.0;
-      for (int t = 0; t < j.n_tiles; ++t) m = fmax(m, p[4 * t + 3]);
-      geoms[j.geom].a = sqrt(m);
-    }
+    if (j.need_radius) geoms[j.geom].a = sqrt(m);
   }
 }
 
-// a3: one CTA per moment job.  Sums the job's tile partials of each component in
-// tile order (double) and applies F_lm a^l.  cmap[cmap_off[L] + p] = (chunk, slot)
-// of packed component p.
+// a3: one CTA per moment job.  Threads walk the (chunk, slot) entries of the job's partial
+// rows in memory order (coalesced), sum each over the job's tiles in tile order (double) and
+// write F_lm a'^l times the sum to the packed component the slot holds.
 __global__ void __launch_bounds__(256) k_finalize(const MomJob* __restrict__ jobs, const double* __restrict__ partials,
-                                                  const SysGeom* __restrict__ geoms, const int2* __restrict__ cmap,
-                                                  const int* __restrict__ cmap_off, const double* __restrict__ ftab,
+                                                  const SysGeom* __restrict__ geoms, const int* __restrict__ imap,
+                                                  const int* __restrict__ imap_off, const double* __restrict__ ftab,
                                                   int kmax) {
   __shared__ double apow[kLmaxMax + 1];
   const MomJob& job = jobs[blockIdx.x];
@@ -178,18 +206,20 @@ __global__ void __launch_bounds__(256) k_finalize(const MomJob* __restrict__ job
     apow[threadIdx.x] = p;
   }
   __syncthreads();
-  const int ncomp = (L + 1) * (L + 1);
-  const int2* map = cmap + cmap_off[L];
-  for (int p = threadIdx.x; p < ncomp; p += blockDim.x) {
-    const int2 cs = map[p];
-    const double* base = partials + (long long)(job.tile_base + cs.x * tpc) * kmax + cs.y;
+  const int* map = imap + imap_off[L];
+  const int nq = imap_off[L + 1] - imap_off[L];  // nch x kmax
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    const int p = map[q];
+    if (p < 0) continue;
+    const int ch = q / kmax, slot = q - ch * kmax;
+    const double* base = partials + (long long)(job.tile_base + ch * tpc) * kmax + slot;
     double s = 0.0;
-    for (int t = 0; t < tpc; ++t) s += base[(long long)t * kmax];
+#pragma unroll 8
+    for (int t = 0; t < tpc; ++t) s += __ldcg(base + (long long)t * kmax);  // loads issued ahead of the adds
     int l = (int)sqrt((double)p);
     while (l * l > p) --l;
     while ((l + 1) * (l + 1) <= p) ++l;
-    const int r = p - l * l;
-    const int m = (r + 1) >> 1;
+    const int m = (p - l * l + 1) >> 1;
     job.out[p] = ftab[l * (kLmaxMax + 1) + m] * apow[l] * s;
   }
 }
@@ -291,15 +321,30 @@ __device__ void wigner_half_table(double* D, const double* cp, const double* sp,
     double d1 = flip(ztab[kZ_SQC + a * 2 * kZN + a + b] * cp[a + b] * sp[a - b], a - b);
     double d2 = 0.0;
     D[a * (a + 1) * (2 * a + 1) / 6 + a * a + a + b] = d1;
+    // the coefficients of step l + 1 are loaded while step l is computed
+    int e = (a + 1) * (a + 2) * (2 * a + 3) / 6 + a * a + a + b;
+    double2 c01 = make_double2(0.0, 0.0);
+    double c2 = 0.0;
+    if (a < L) {
+      c01 = __ldg(reinterpret_cast<const double2*>(rtab) + 2 * e);
+      c2 = __ldg(rtab + 4 * e + 2);
+    }
     for (int l = a + 1; l <= L; ++l) {
-      const int e = l * (l + 1) * (2 * l + 1) / 6 + a * a + a + b;
-      const double2 c01 = __ldg(reinterpret_cast<const double2*>(rtab) + 2 * e);
-      const double c2 = __ldg(rtab + 4 * e + 2);
+      const int en = e + (l + 1) * (l + 1);  // index of (l + 1, a, b)
+      double2 n01 = c01;
+      double n2 = c2;
+      if (l < L) {
+        n01 = __ldg(reinterpret_cast<const double2*>(rtab) + 2 * en);
+        n2 = __ldg(rtab + 4 * en + 2);
+      }
       const double At = fma(c01.x, cb, -c01.y);
       const double v = fma(At, d1, -(c2 * d2));
       D[e] = v;
       d2 = d1;
       d1 = v;
+      e = en;
+      c01 = n01;
+      c2 = n2;
     }
   }
 }
@@ -518,9 +563,19 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     const double2* a = ra + l1 * (l1 + 1) / 2;
     const double2* b = rb + l2 * (l2 + 1) / 2;
     const int mm = l1 < l2 ? l1 : l2;
-    double s = 0.0;
-    for (int m = 1; m <= mm; ++m) s += flip(fma(a[m].x, b[m].x, a[m].y * b[m].y), m);
-    s = fma(2.0, s, a[0].x * b[0].x);
+    double se = 0.0, so = 0.0;  // even and odd m: sum_m (-1)^m Re(a_m conj b_m) = se - so
+    int m = 1;
+    for (; m + 1 <= mm; m += 2) {
+      so = fma(a[m].x, b[m].x, so);
+      so = fma(a[m].y, b[m].y, so);
+      se = fma(a[m + 1].x, b[m + 1].x, se);
+      se = fma(a[m + 1].y, b[m + 1].y, se);
+    }
+    if (m <= mm) {
+      so = fma(a[m].x, b[m].x, so);
+      so = fma(a[m].y, b[m].y, so);
+    }
+    double s = fma(2.0, se - so, a[0].x * b[0].x);
     const double c = flip(ztab[kZ_FACT + l1 + l2] * rp[l1 + l2], l2);
     acc = fma(c, s, acc);
     if (kGrad) {
@@ -738,10 +793,15 @@ int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms, const int2* cmap,
-                    const int* cmap_off, const double* ftab, int kmax, cudaStream_t s) {
+int geom_launches(int n_gjobs, int n_gtiles) {
+  if (n_gjobs <= 0) return 0;
+  return n_gtiles > 0 ? 2 : 0;
+}
+
+int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms, const int* imap,
+                    const int* imap_off, const double* ftab, int kmax, cudaStream_t s) {
   if (n_jobs <= 0) return 0;
-  k_finalize<<<n_jobs, 256, 0, s>>>(jobs, partials, geoms, cmap, cmap_off, ftab, kmax);
+  k_finalize<<<n_jobs, 256, 0, s>>>(jobs, partials, geoms, imap, imap_off, ftab, kmax);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

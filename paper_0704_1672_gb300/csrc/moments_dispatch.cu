@@ -2,7 +2,9 @@
 #include <cuda_runtime.h>
 
 #include <array>
+#include <cmath>
 #include <utility>
+#include <vector>
 
 #include "tcm_internal.h"
 
@@ -43,6 +45,57 @@ int moments_smem_bytes(int precision, int L) {
     mx = n > mx ? n : mx;
   }
   return (kThreads / 32) * mx * stride_of(precision) * size_of(precision);
+}
+
+void finalize_tables(std::vector<double>& ftab, std::vector<int>& imap_off, std::vector<int>& imap) {
+  const int N = kLmaxMax + 1;
+  std::vector<long double> fact(2 * N + 2);
+  fact[0] = 1.0L;
+  for (size_t k = 1; k < fact.size(); ++k) fact[k] = fact[k - 1] * (long double)k;
+  ftab.assign(N * N, 0.0);
+  for (int m = 0; m < N; ++m) {
+    // s_lm: normalisation of the kernels' G_lm (tcm_internal.h): s_mm = (2m-1)!!,
+    // s_m+1,m = (2m+1) s_mm, s_l+1,m = (l+m) s_l-1,m / (l-m+1)
+    long double s_prev = 0.0L, s = 1.0L;
+    for (int k = 1; k < 2 * m; k += 2) s *= (long double)k;
+    for (int l = m; l < N; ++l) {
+      if (l == m + 1) {
+        s_prev = s;
+        s = (long double)(2 * m + 1) * s;
+      } else if (l > m + 1) {
+        const long double sn = (long double)(l - 1 + m) * s_prev / (long double)(l - m);
+        s_prev = s;
+        s = sn;
+      }
+      // (-1)^m of the Condon-Shortley phase times sigma_{l-m} of the kernels' H variables
+      const long double sgn = ((m & 1) ? -1.0L : 1.0L) * (((l - m) & 2) ? -1.0L : 1.0L);
+      ftab[l * N + m] = (double)(sgn * std::sqrt(fact[l - m] / fact[l + m]) * s);
+    }
+  }
+  imap_off.assign(2 * (N + 1), 0);
+  imap.clear();
+  for (int pi = 0; pi < 2; ++pi) {
+    const int kmax = moments_kmax(pi == 0 ? TCM_FP64 : TCM_MIXED);
+    for (int L = 0; L < N; ++L) {
+      const int nch = plan_nch(L, kmax);
+      const size_t base = imap.size();
+      imap_off[pi * (N + 1) + L] = (int)base;
+      imap.resize(base + (size_t)nch * kmax, -1);
+      for (int ch = 0; ch < nch; ++ch) {
+        const int m0 = plan_m0(L, kmax, nch, ch), m1 = plan_m0(L, kmax, nch, ch + 1);
+        for (int m = m0; m < m1; ++m)
+          for (int l = m; l <= L; ++l) {
+            if (m == 0) {
+              imap[base + ch * kmax + acc_slot(L, m0, m1, l, 0, 0)] = l * l;
+            } else {
+              imap[base + ch * kmax + acc_slot(L, m0, m1, l, m, 0)] = l * l + 2 * m - 1;
+              imap[base + ch * kmax + acc_slot(L, m0, m1, l, m, 1)] = l * l + 2 * m;
+            }
+          }
+      }
+    }
+    imap_off[pi * (N + 1) + N] = (int)imap.size();
+  }
 }
 
 int launch_moments(int precision, int L, const MomJob* jobs, const MomTile* tiles, int n_tiles, int* counter,

@@ -390,6 +390,25 @@ __device__ __forceinline__ void warp_reduce_store(const Regs<T, L, M0, M1>& s, T
   __syncwarp();
 }
 
+// u^E by repeated squaring (E a compile-time constant >= 1).
+template <typename T, int E>
+__device__ __forceinline__ void upow(T ux, T uy, T& pr, T& pi) {
+  if constexpr (E == 1) {
+    pr = ux;
+    pi = uy;
+  } else if constexpr (E % 2 == 0) {
+    T hr, hi;
+    upow<T, E / 2>(ux, uy, hr, hi);
+    pr = fmaT(hr, hr, -(hi * hi));
+    pi = (T)2 * hr * hi;
+  } else {
+    T hr, hi;
+    upow<T, E - 1>(ux, uy, hr, hi);
+    pr = fmaT(hr, ux, -(hi * uy));
+    pi = fmaT(hr, uy, hi * ux);
+  }
+}
+
 // Walks this lane's atoms of the warp tile [i0, i1), the next record prefetched while the
 // current one is processed.
 template <typename T, int L, int M0, int M1, typename Rec>
@@ -411,15 +430,7 @@ __device__ __forceinline__ void atom_loop(Regs<T, L, M0, M1>& s, const Rec* __re
       s.dr = (T)1;
       s.di = (T)0;
     } else {
-      s.dr = ux;
-      s.di = uy;
-#pragma unroll
-      for (int k = 1; k < M0; ++k) {
-        const T nr = s.dr * ux - s.di * uy;
-        const T ni = s.dr * uy + s.di * ux;
-        s.dr = nr;
-        s.di = ni;
-      }
+      upow<T, M0>(ux, uy, s.dr, s.di);  // the chunk's first column starts at u^M0
     }
     levels<T, L, M0, M1, 0>(s, ux, uy, cc, rr, qq);
   }

@@ -87,8 +87,8 @@ struct tcm_ctx {
   // tables
   double* d_ftab = nullptr;  // F_lm, [kLmaxMax+1][kLmaxMax+1]
   double* d_ztab = nullptr;  // contraction tables (Wigner-d recursion, factorials, 1/sqrt((l+m)!(l-m)!))
-  int2* d_cmap[2] = {nullptr, nullptr};
-  int* d_cmap_off = nullptr;
+  int* d_imap = nullptr;      // (chunk, slot) -> packed component, both precisions
+  int* d_imap_off = nullptr;  // [precision][L] offsets into d_imap
   // scratch
   DevBuf desc, partials, gpart, counters, moms, escr, dpart;
   Stage stage[kStages];
@@ -303,8 +303,8 @@ int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, 
   }
   {
     PhaseScope ps(c, TCM_PHASE_FINALIZE, 1);
-    TRY_LAUNCH(launch_finalize(d_jobs, (int)P.jobs.size(), parts, d_geoms, c->d_cmap[precision == TCM_FP64 ? 0 : 1],
-                               c->d_cmap_off, c->d_ftab, kmax, st));
+    TRY_LAUNCH(launch_finalize(d_jobs, (int)P.jobs.size(), parts, d_geoms, c->d_imap,
+                               c->d_imap_off + (precision == TCM_FP64 ? 0 : kLmaxMax + 2), c->d_ftab, kmax, st));
   }
   return TCM_OK;
 }
@@ -350,67 +350,19 @@ void identity(double* r) {
 // Host tables --------------------------------------------------------------------
 
 int build_tables(tcm_ctx* c) {
-  const int N = kLmaxMax + 1;
-  std::vector<long double> fact(2 * N + 2);
-  fact[0] = 1.0L;
-  for (size_t k = 1; k < fact.size(); ++k) fact[k] = fact[k - 1] * (long double)k;
-  std::vector<double> ftab(N * N, 0.0);
-  for (int m = 0; m < N; ++m) {
-    // s_lm: normalisation of the kernel's G_lm (see tcm_internal.h)
-    long double s_prev = 0.0L, s = 1.0L;
-    for (int k = 1; k < 2 * m; k += 2) s *= (long double)k;  // (2m-1)!!
-    for (int l = m; l < N; ++l) {
-      if (l == m + 1) {
-        s_prev = s;
-        s = (long double)(2 * m + 1) * s;
-      } else if (l > m + 1) {
-        const long double sn = (long double)(l - 1 + m) * s_prev / (long double)(l - m);
-        s_prev = s;
-        s = sn;
-      }
-      // (-1)^m of the Condon-Shortley phase times sigma_{l-m} of the kernels' H variables
-      const long double sgn = ((m & 1) ? -1.0L : 1.0L) * (((l - m) & 2) ? -1.0L : 1.0L);
-      ftab[l * N + m] = (double)(sgn * std::sqrt(fact[l - m] / fact[l + m]) * s);
-    }
-  }
-  std::vector<int> off(N + 1, 0);
-  for (int L = 0; L < N; ++L) off[L + 1] = off[L] + (L + 1) * (L + 1);
-  std::vector<int2> cmap[2];
-  for (int pi = 0; pi < 2; ++pi) {
-    const int prec = pi == 0 ? TCM_FP64 : TCM_MIXED;
-    const int kmax = moments_kmax(prec);
-    cmap[pi].assign(off[N], make_int2(-1, -1));
-    for (int L = 0; L < N; ++L) {
-      const int nch = plan_nch(L, kmax);
-      for (int ch = 0; ch < nch; ++ch) {
-        const int m0 = plan_m0(L, kmax, nch, ch), m1 = plan_m0(L, kmax, nch, ch + 1);
-        for (int m = m0; m < m1; ++m)
-          for (int l = m; l <= L; ++l) {
-            if (m == 0) {
-              cmap[pi][off[L] + l * l] = make_int2(ch, acc_slot(L, m0, m1, l, 0, 0));
-            } else {
-              cmap[pi][off[L] + l * l + 2 * m - 1] = make_int2(ch, acc_slot(L, m0, m1, l, m, 0));
-              cmap[pi][off[L] + l * l + 2 * m] = make_int2(ch, acc_slot(L, m0, m1, l, m, 1));
-            }
-          }
-      }
-    }
-  }
-  for (int pi = 0; pi < 2; ++pi)
-    for (const int2& e : cmap[pi])
-      if (e.x < 0 || e.y < 0 || e.y >= moments_kmax(pi == 0 ? TCM_FP64 : TCM_MIXED))
-        return set_err(TCM_ECUDA, "internal error: incomplete moment component map");
+  std::vector<double> ftab;
+  std::vector<int> imap_off, imap;
+  finalize_tables(ftab, imap_off, imap);
   TRY_CUDA(cudaMalloc(&c->d_ftab, ftab.size() * sizeof(double)));
+  TRY_CUDA(cudaMalloc(&c->d_imap, imap.size() * sizeof(int)));
+  TRY_CUDA(cudaMalloc(&c->d_imap_off, imap_off.size() * sizeof(int)));
+  TRY_CUDA(cudaMemcpy(c->d_ftab, ftab.data(), ftab.size() * sizeof(double), cudaMemcpyHostToDevice));
+  TRY_CUDA(cudaMemcpy(c->d_imap, imap.data(), imap.size() * sizeof(int), cudaMemcpyHostToDevice));
+  TRY_CUDA(cudaMemcpy(c->d_imap_off, imap_off.data(), imap_off.size() * sizeof(int), cudaMemcpyHostToDevice));
   std::vector<double> zt(contract_table_size());
   contract_tables(zt.data());
   TRY_CUDA(cudaMalloc(&c->d_ztab, zt.size() * sizeof(double)));
-  TRY_CUDA(cudaMalloc(&c->d_cmap_off, off.size() * sizeof(int)));
-  for (int pi = 0; pi < 2; ++pi) TRY_CUDA(cudaMalloc(&c->d_cmap[pi], cmap[pi].size() * sizeof(int2)));
-  TRY_CUDA(cudaMemcpy(c->d_ftab, ftab.data(), ftab.size() * sizeof(double), cudaMemcpyHostToDevice));
   TRY_CUDA(cudaMemcpy(c->d_ztab, zt.data(), zt.size() * sizeof(double), cudaMemcpyHostToDevice));
-  TRY_CUDA(cudaMemcpy(c->d_cmap_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
-  for (int pi = 0; pi < 2; ++pi)
-    TRY_CUDA(cudaMemcpy(c->d_cmap[pi], cmap[pi].data(), cmap[pi].size() * sizeof(int2), cudaMemcpyHostToDevice));
   return TCM_OK;
 }
 
@@ -419,8 +371,8 @@ void free_ctx(tcm_ctx* c) {
   cudaStreamSynchronize(c->stream);
   cudaFree(c->d_ftab);
   cudaFree(c->d_ztab);
-  cudaFree(c->d_cmap_off);
-  for (auto* p : c->d_cmap) cudaFree(p);
+  cudaFree(c->d_imap);
+  cudaFree(c->d_imap_off);
   for (DevBuf* b : {&c->desc, &c->partials, &c->gpart, &c->counters, &c->moms, &c->escr, &c->dpart}) cudaFree(b->p);
   for (auto& st : c->stage) {
     if (st.host) cudaFreeHost(st.host);
@@ -591,7 +543,7 @@ int tcm_prepare(tcm_ctx_t c, tcm_system* s) {
   TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   {
-    PhaseScope ps(c, TCM_PHASE_GEOM, 2);
+    PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches((int)gjobs.size(), ngt));
     TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
                            static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
@@ -644,7 +596,7 @@ int tcm_moments(tcm_ctx_t c, const tcm_system* s, const double* rot, int lmax, i
   if (!gjobs.empty()) {
     TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
     TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
-    PhaseScope ps(c, TCM_PHASE_GEOM, 2);
+    PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches((int)gjobs.size(), ngt));
     TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
                            static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
@@ -896,7 +848,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   auto enqueue = [&](cudaStream_t st) -> int {
     if (!gjobs.empty()) {
       TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), st));
-      PhaseScope ps(c, TCM_PHASE_GEOM, 2);
+      PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches((int)gjobs.size(), ngt));
       TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
                              reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
                              static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, st));
@@ -950,7 +902,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   }
   TRY_CUDA(cudaGraphLaunch(c->gexec, c->stream));
   ++c->graph_launches;
-  c->launches[TCM_PHASE_GEOM] += gjobs.empty() ? 0 : 2;
+  c->launches[TCM_PHASE_GEOM] += geom_launches((int)gjobs.size(), ngt);
   c->launches[TCM_PHASE_MOMENTS] += ngroups;
   c->launches[TCM_PHASE_FINALIZE] += 1;
   c->launches[TCM_PHASE_CONTRACT] += 1;
@@ -990,7 +942,7 @@ int direct_items(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, int64_t 
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   if (!gjobs.empty()) {
     TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
-    PhaseScope ps(c, TCM_PHASE_GEOM, 2);
+    PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches((int)gjobs.size(), ngt));
     TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
                            static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));

@@ -20,6 +20,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <vector>
 
 #include "../../include/tcm.h"
 
@@ -182,12 +183,22 @@ int launch_moments(int precision, int L, const MomJob* jobs, const MomTile* tile
 int moments_smem_bytes(int precision, int L);
 int moments_kmax(int precision);
 int moments_nchunks(int precision, int L);
+// Host: F_lm table and the inverse component maps of both precisions (imap_off has
+// 2 (kLmaxMax + 2) entries, FP64 first, each block ending with its total).
+void finalize_tables(std::vector<double>& ftab, std::vector<int>& imap_off, std::vector<int>& imap);
 
-// a1 in two launches; tickets: one int per geometry job, zero on entry (left zero on exit).
+// a1 in two tiled launches (the coordinate sums, then the largest |x - c|^2), spread over many
+// SMs because the per-atom double arithmetic would saturate the FP64 pipe of a few; tickets: one
+// int per geometry job, zero on entry (left zero on exit).  geom_launches gives the number of
+// kernels launch_geom queues.
 int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n_gtiles, double* gpart, int* tickets,
                 SysGeom* geoms, cudaStream_t s);
+int geom_launches(int n_gjobs, int n_gtiles);
+// Step a3: one CTA per job.  imap + imap_off[L] lists, per (chunk, slot) of degree L, the packed
+// component it holds (-1 for none), nch(L) x kmax entries; ftab[l][m] = F_lm with the sign
+// of the kernels' H variables.
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms,
-                    const int2* cmap, const int* cmap_off, const double* ftab, int kmax, cudaStream_t s);
+                    const int* imap, const int* imap_off, const double* ftab, int kmax, cudaStream_t s);
 
 
 

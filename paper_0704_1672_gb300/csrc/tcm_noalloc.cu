@@ -47,9 +47,10 @@ constexpr size_t kOffGTiles = align256(kOffGJob + sizeof(GeomJob));
 constexpr size_t kOffGPart = align256(kOffGTiles + sizeof(GeomTile) * kNaGeomTiles);
 constexpr size_t kOffCounters = align256(kOffGPart + sizeof(double) * 4 * kNaGeomTiles);
 constexpr size_t kOffFtab = align256(kOffCounters + sizeof(int) * 64);
-constexpr size_t kOffCmapOff = align256(kOffFtab + sizeof(double) * (kLmaxMax + 1) * (kLmaxMax + 1));
-constexpr size_t kOffCmap = align256(kOffCmapOff + sizeof(int) * (kLmaxMax + 2));
-constexpr size_t kScratchBytes = align256(kOffCmap + sizeof(int2) * 2 * kNaCompTotal);
+constexpr int kNaImapInts = 4 * kNaCompTotal;  // room for both precisions' (chunk, slot) maps
+constexpr size_t kOffImapOff = align256(kOffFtab + sizeof(double) * (kLmaxMax + 1) * (kLmaxMax + 1));
+constexpr size_t kOffImap = align256(kOffImapOff + sizeof(int) * 2 * (kLmaxMax + 2));
+constexpr size_t kScratchBytes = align256(kOffImap + sizeof(int) * kNaImapInts);
 
 // The scratch.  In host code this name is only a stand-in for the symbol; kernels get
 // the device address obtained with cudaGetSymbolAddress.
@@ -60,54 +61,6 @@ std::mutex g_setup_mutex;
 char* g_scratch_ptr[kMaxDevices] = {};  // device address of the scratch, per device
 
 int na_err(int code, const char* msg) { return record_error(code, msg); }
-
-// Host tables for the finalisation (F_lm and the component -> (chunk, slot) maps); the
-// same values a context uploads at creation.
-void host_tables(std::vector<double>& ftab, std::vector<int>& off, std::vector<int2>& cmap) {
-  const int N = kLmaxMax + 1;
-  std::vector<long double> fact(2 * N + 2);
-  fact[0] = 1.0L;
-  for (size_t k = 1; k < fact.size(); ++k) fact[k] = fact[k - 1] * (long double)k;
-  ftab.assign(N * N, 0.0);
-  for (int m = 0; m < N; ++m) {
-    long double s_prev = 0.0L, s = 1.0L;
-    for (int k = 1; k < 2 * m; k += 2) s *= (long double)k;
-    for (int l = m; l < N; ++l) {
-      if (l == m + 1) {
-        s_prev = s;
-        s = (long double)(2 * m + 1) * s;
-      } else if (l > m + 1) {
-        const long double sn = (long double)(l - 1 + m) * s_prev / (long double)(l - m);
-        s_prev = s;
-        s = sn;
-      }
-      const long double sgn = ((m & 1) ? -1.0L : 1.0L) * (((l - m) & 2) ? -1.0L : 1.0L);
-      ftab[l * N + m] = (double)(sgn * std::sqrt(fact[l - m] / fact[l + m]) * s);
-    }
-  }
-  off.assign(N + 1, 0);
-  for (int L = 0; L < N; ++L) off[L + 1] = off[L] + (L + 1) * (L + 1);
-  cmap.assign(2 * off[N], make_int2(0, 0));
-  for (int pi = 0; pi < 2; ++pi) {
-    const int kmax = moments_kmax(pi == 0 ? TCM_FP64 : TCM_MIXED);
-    int2* cm = cmap.data() + pi * off[N];
-    for (int L = 0; L < N; ++L) {
-      const int nch = plan_nch(L, kmax);
-      for (int ch = 0; ch < nch; ++ch) {
-        const int m0 = plan_m0(L, kmax, nch, ch), m1 = plan_m0(L, kmax, nch, ch + 1);
-        for (int m = m0; m < m1; ++m)
-          for (int l = m; l <= L; ++l) {
-            if (m == 0) {
-              cm[off[L] + l * l] = make_int2(ch, acc_slot(L, m0, m1, l, 0, 0));
-            } else {
-              cm[off[L] + l * l + 2 * m - 1] = make_int2(ch, acc_slot(L, m0, m1, l, m, 0));
-              cm[off[L] + l * l + 2 * m] = make_int2(ch, acc_slot(L, m0, m1, l, m, 1));
-            }
-          }
-      }
-    }
-  }
-}
 
 // Once per device, with that device current: the scratch address and the tables.
 int setup_device(int dev, char** out) {
@@ -121,13 +74,12 @@ int setup_device(int dev, char** out) {
   if (e != cudaSuccess) return na_err(TCM_ECUDA, "tcm_moments_noalloc: cudaGetSymbolAddress of the scratch failed");
   char* base = static_cast<char*>(ptr);
   std::vector<double> ftab;
-  std::vector<int> off;
-  std::vector<int2> cmap;
-  host_tables(ftab, off, cmap);
-  if ((int)off.back() != kNaCompTotal) return na_err(TCM_ECUDA, "tcm_moments_noalloc: internal table size mismatch");
+  std::vector<int> imap_off, imap;
+  finalize_tables(ftab, imap_off, imap);
+  if ((int)imap.size() > kNaImapInts) return na_err(TCM_ECUDA, "tcm_moments_noalloc: internal table size mismatch");
   if (cudaMemcpy(base + kOffFtab, ftab.data(), ftab.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(base + kOffCmapOff, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(base + kOffCmap, cmap.data(), cmap.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+      cudaMemcpy(base + kOffImapOff, imap_off.data(), imap_off.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(base + kOffImap, imap.data(), imap.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: copying the tables into the scratch failed");
   g_scratch_ptr[dev] = base;
   *out = base;
@@ -219,8 +171,9 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
                      std::min((n_tiles + kThreads / 32 - 1) / (kThreads / 32), 2 * num_sms), st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: moment launch failed");
   if (launch_finalize(d_job, 1, reinterpret_cast<double*>(base + kOffPartials), d_geom,
-                      reinterpret_cast<int2*>(base + kOffCmap) + (precision == TCM_FP64 ? 0 : kNaCompTotal),
-                      reinterpret_cast<int*>(base + kOffCmapOff), reinterpret_cast<double*>(base + kOffFtab), kmax, st) != 0)
+                      reinterpret_cast<int*>(base + kOffImap),
+                      reinterpret_cast<int*>(base + kOffImapOff) + (precision == TCM_FP64 ? 0 : kLmaxMax + 2),
+                      reinterpret_cast<double*>(base + kOffFtab), kmax, st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: finalisation launch failed");
   if (geom_out && cudaMemcpyAsync(geom_out, d_geom, sizeof(SysGeom), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: copy of the centre and radius failed");
