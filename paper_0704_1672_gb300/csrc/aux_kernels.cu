@@ -190,37 +190,37 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom_radius(const GeomJob* __r
 
 // a3: one CTA per moment job.  Threads walk the (chunk, slot) entries of the job's partial
 // rows in memory order (coalesced), sum each over the job's tiles in tile order (double) and
-// write F_lm a'^l times the sum to the packed component the slot holds.
-__global__ void __launch_bounds__(256) k_finalize(const MomJob* __restrict__ jobs, const double* __restrict__ partials,
-                                                  const SysGeom* __restrict__ geoms, const int* __restrict__ imap,
-                                                  const int* __restrict__ imap_off, const double* __restrict__ ftab,
-                                                  int kmax) {
-  __shared__ double apow[kLmaxMax + 1];
+// write F_lm a'^l times the sum to the packed component the slot holds.  The map entry, its
+// factor F_lm and the partial rows do not depend on each other, so their loads overlap; a' is a
+// power of two, so a'^l is formed exactly from its exponent.
+constexpr int kFinalizeThreads = 512;
+__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const MomJob* __restrict__ jobs,
+                                                               const double* __restrict__ partials,
+                                                               const SysGeom* __restrict__ geoms,
+                                                               const int* __restrict__ imap,
+                                                               const double* __restrict__ fmap,
+                                                               const int* __restrict__ imap_off, int kmax) {
   const MomJob& job = jobs[blockIdx.x];
   const int L = job.L;
   const int tpc = job.tiles_per_chunk;
-  const double a = scale_radius(geoms[job.geom].a);  // the moment kernels scaled by 1/a
-  if (threadIdx.x <= L) {
-    double p = 1.0;
-    for (int k = 0; k < (int)threadIdx.x; ++k) p *= a;
-    apow[threadIdx.x] = p;
-  }
-  __syncthreads();
-  const int* map = imap + imap_off[L];
-  const int nq = imap_off[L + 1] - imap_off[L];  // nch x kmax
+  const int o = imap_off[L];
+  const int nq = imap_off[L + 1] - o;  // nch x kmax
+  const double a = geoms[job.geom].a;
+  int e = 0;  // a' = scale_radius(a) = 2^e
+  if (a > 0.0) frexp(a, &e);
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-    const int p = map[q];
-    if (p < 0) continue;
+    const int p = imap[o + q];
+    const double f = fmap[o + q];
     const int ch = q / kmax, slot = q - ch * kmax;
     const double* base = partials + (long long)(job.tile_base + ch * tpc) * kmax + slot;
     double s = 0.0;
 #pragma unroll 8
     for (int t = 0; t < tpc; ++t) s += __ldcg(base + (long long)t * kmax);  // loads issued ahead of the adds
-    int l = (int)sqrt((double)p);
+    if (p < 0) continue;
+    int l = (int)sqrtf((float)p);
     while (l * l > p) --l;
     while ((l + 1) * (l + 1) <= p) ++l;
-    const int m = (p - l * l + 1) >> 1;
-    job.out[p] = ftab[l * (kLmaxMax + 1) + m] * apow[l] * s;
+    job.out[p] = f * ldexp(1.0, e * l) * s;
   }
 }
 
@@ -799,9 +799,9 @@ int geom_launches(int n_gjobs, int n_gtiles) {
 }
 
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms, const int* imap,
-                    const int* imap_off, const double* ftab, int kmax, cudaStream_t s) {
+                    const double* fmap, const int* imap_off, int kmax, cudaStream_t s) {
   if (n_jobs <= 0) return 0;
-  k_finalize<<<n_jobs, 256, 0, s>>>(jobs, partials, geoms, imap, imap_off, ftab, kmax);
+  k_finalize<<<n_jobs, kFinalizeThreads, 0, s>>>(jobs, partials, geoms, imap, fmap, imap_off, kmax);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

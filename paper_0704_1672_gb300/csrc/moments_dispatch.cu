@@ -47,8 +47,9 @@ int moments_smem_bytes(int precision, int L) {
   return (kThreads / 32) * mx * stride_of(precision) * size_of(precision);
 }
 
-void finalize_tables(std::vector<double>& ftab, std::vector<int>& imap_off, std::vector<int>& imap) {
+void finalize_tables(std::vector<int>& imap_off, std::vector<int>& imap, std::vector<double>& fmap) {
   const int N = kLmaxMax + 1;
+  std::vector<double> ftab;
   std::vector<long double> fact(2 * N + 2);
   fact[0] = 1.0L;
   for (size_t k = 1; k < fact.size(); ++k) fact[k] = fact[k - 1] * (long double)k;
@@ -95,6 +96,14 @@ void finalize_tables(std::vector<double>& ftab, std::vector<int>& imap_off, std:
       }
     }
     imap_off[pi * (N + 1) + N] = (int)imap.size();
+  }
+  fmap.assign(imap.size(), 0.0);
+  for (size_t q = 0; q < imap.size(); ++q) {
+    const int p = imap[q];
+    if (p < 0) continue;
+    int l = 0;
+    while ((l + 1) * (l + 1) <= p) ++l;
+    fmap[q] = ftab[l * N + ((p - l * l + 1) >> 1)];
   }
 }
 

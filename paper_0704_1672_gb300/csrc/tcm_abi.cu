@@ -85,7 +85,7 @@ struct tcm_ctx {
   int lmax_cap = 0;
   cudaStream_t stream = nullptr;
   // tables
-  double* d_ftab = nullptr;  // F_lm, [kLmaxMax+1][kLmaxMax+1]
+  double* d_fmap = nullptr;  // F_lm of the component each (chunk, slot) holds
   double* d_ztab = nullptr;  // contraction tables (Wigner-d recursion, factorials, 1/sqrt((l+m)!(l-m)!))
   int* d_imap = nullptr;      // (chunk, slot) -> packed component, both precisions
   int* d_imap_off = nullptr;  // [precision][L] offsets into d_imap
@@ -303,8 +303,8 @@ int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, 
   }
   {
     PhaseScope ps(c, TCM_PHASE_FINALIZE, 1);
-    TRY_LAUNCH(launch_finalize(d_jobs, (int)P.jobs.size(), parts, d_geoms, c->d_imap,
-                               c->d_imap_off + (precision == TCM_FP64 ? 0 : kLmaxMax + 2), c->d_ftab, kmax, st));
+    TRY_LAUNCH(launch_finalize(d_jobs, (int)P.jobs.size(), parts, d_geoms, c->d_imap, c->d_fmap,
+                               c->d_imap_off + (precision == TCM_FP64 ? 0 : kLmaxMax + 2), kmax, st));
   }
   return TCM_OK;
 }
@@ -350,13 +350,13 @@ void identity(double* r) {
 // Host tables --------------------------------------------------------------------
 
 int build_tables(tcm_ctx* c) {
-  std::vector<double> ftab;
+  std::vector<double> fmap;
   std::vector<int> imap_off, imap;
-  finalize_tables(ftab, imap_off, imap);
-  TRY_CUDA(cudaMalloc(&c->d_ftab, ftab.size() * sizeof(double)));
+  finalize_tables(imap_off, imap, fmap);
+  TRY_CUDA(cudaMalloc(&c->d_fmap, fmap.size() * sizeof(double)));
   TRY_CUDA(cudaMalloc(&c->d_imap, imap.size() * sizeof(int)));
   TRY_CUDA(cudaMalloc(&c->d_imap_off, imap_off.size() * sizeof(int)));
-  TRY_CUDA(cudaMemcpy(c->d_ftab, ftab.data(), ftab.size() * sizeof(double), cudaMemcpyHostToDevice));
+  TRY_CUDA(cudaMemcpy(c->d_fmap, fmap.data(), fmap.size() * sizeof(double), cudaMemcpyHostToDevice));
   TRY_CUDA(cudaMemcpy(c->d_imap, imap.data(), imap.size() * sizeof(int), cudaMemcpyHostToDevice));
   TRY_CUDA(cudaMemcpy(c->d_imap_off, imap_off.data(), imap_off.size() * sizeof(int), cudaMemcpyHostToDevice));
   std::vector<double> zt(contract_table_size());
@@ -369,7 +369,7 @@ int build_tables(tcm_ctx* c) {
 void free_ctx(tcm_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
-  cudaFree(c->d_ftab);
+  cudaFree(c->d_fmap);
   cudaFree(c->d_ztab);
   cudaFree(c->d_imap);
   cudaFree(c->d_imap_off);

@@ -183,9 +183,9 @@ int launch_moments(int precision, int L, const MomJob* jobs, const MomTile* tile
 int moments_smem_bytes(int precision, int L);
 int moments_kmax(int precision);
 int moments_nchunks(int precision, int L);
-// Host: F_lm table and the inverse component maps of both precisions (imap_off has
+// Host: the inverse component maps of both precisions and their factors F_lm (imap_off has
 // 2 (kLmaxMax + 2) entries, FP64 first, each block ending with its total).
-void finalize_tables(std::vector<double>& ftab, std::vector<int>& imap_off, std::vector<int>& imap);
+void finalize_tables(std::vector<int>& imap_off, std::vector<int>& imap, std::vector<double>& fmap);
 
 // a1 in two tiled launches (the coordinate sums, then the largest |x - c|^2), spread over many
 // SMs because the per-atom double arithmetic would saturate the FP64 pipe of a few; tickets: one
@@ -195,10 +195,10 @@ int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n
                 SysGeom* geoms, cudaStream_t s);
 int geom_launches(int n_gjobs, int n_gtiles);
 // Step a3: one CTA per job.  imap + imap_off[L] lists, per (chunk, slot) of degree L, the packed
-// component it holds (-1 for none), nch(L) x kmax entries; ftab[l][m] = F_lm with the sign
-// of the kernels' H variables.
+// component it holds (-1 for none), nch(L) x kmax entries; fmap beside it holds that
+// component's F_lm with the sign of the kernels' H variables.
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms,
-                    const int* imap, const int* imap_off, const double* ftab, int kmax, cudaStream_t s);
+                    const int* imap, const double* fmap, const int* imap_off, int kmax, cudaStream_t s);
 
 
 

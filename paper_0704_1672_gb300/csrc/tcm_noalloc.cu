@@ -46,11 +46,11 @@ constexpr size_t kOffGJob = align256(kOffGeom + sizeof(SysGeom));
 constexpr size_t kOffGTiles = align256(kOffGJob + sizeof(GeomJob));
 constexpr size_t kOffGPart = align256(kOffGTiles + sizeof(GeomTile) * kNaGeomTiles);
 constexpr size_t kOffCounters = align256(kOffGPart + sizeof(double) * 4 * kNaGeomTiles);
-constexpr size_t kOffFtab = align256(kOffCounters + sizeof(int) * 64);
 constexpr int kNaImapInts = 4 * kNaCompTotal;  // room for both precisions' (chunk, slot) maps
-constexpr size_t kOffImapOff = align256(kOffFtab + sizeof(double) * (kLmaxMax + 1) * (kLmaxMax + 1));
+constexpr size_t kOffImapOff = align256(kOffCounters + sizeof(int) * 64);
 constexpr size_t kOffImap = align256(kOffImapOff + sizeof(int) * 2 * (kLmaxMax + 2));
-constexpr size_t kScratchBytes = align256(kOffImap + sizeof(int) * kNaImapInts);
+constexpr size_t kOffFmap = align256(kOffImap + sizeof(int) * kNaImapInts);
+constexpr size_t kScratchBytes = align256(kOffFmap + sizeof(double) * kNaImapInts);
 
 // The scratch.  In host code this name is only a stand-in for the symbol; kernels get
 // the device address obtained with cudaGetSymbolAddress.
@@ -73,11 +73,11 @@ int setup_device(int dev, char** out) {
   cudaError_t e = cudaGetSymbolAddress(&ptr, g_tcm_noalloc_scratch);
   if (e != cudaSuccess) return na_err(TCM_ECUDA, "tcm_moments_noalloc: cudaGetSymbolAddress of the scratch failed");
   char* base = static_cast<char*>(ptr);
-  std::vector<double> ftab;
+  std::vector<double> fmap;
   std::vector<int> imap_off, imap;
-  finalize_tables(ftab, imap_off, imap);
+  finalize_tables(imap_off, imap, fmap);
   if ((int)imap.size() > kNaImapInts) return na_err(TCM_ECUDA, "tcm_moments_noalloc: internal table size mismatch");
-  if (cudaMemcpy(base + kOffFtab, ftab.data(), ftab.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+  if (cudaMemcpy(base + kOffFmap, fmap.data(), fmap.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(base + kOffImapOff, imap_off.data(), imap_off.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(base + kOffImap, imap.data(), imap.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: copying the tables into the scratch failed");
@@ -171,9 +171,9 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
                      std::min((n_tiles + kThreads / 32 - 1) / (kThreads / 32), 2 * num_sms), st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: moment launch failed");
   if (launch_finalize(d_job, 1, reinterpret_cast<double*>(base + kOffPartials), d_geom,
-                      reinterpret_cast<int*>(base + kOffImap),
+                      reinterpret_cast<int*>(base + kOffImap), reinterpret_cast<double*>(base + kOffFmap),
                       reinterpret_cast<int*>(base + kOffImapOff) + (precision == TCM_FP64 ? 0 : kLmaxMax + 2),
-                      reinterpret_cast<double*>(base + kOffFtab), kmax, st) != 0)
+                      kmax, st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: finalisation launch failed");
   if (geom_out && cudaMemcpyAsync(geom_out, d_geom, sizeof(SysGeom), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: copy of the centre and radius failed");
