@@ -171,7 +171,7 @@ struct GeomTile {
   int t;
 };
 
-constexpr int kGeomTileAtoms = 1024;
+constexpr int kGeomTileAtoms = 256;  // small tiles: the per-atom double arithmetic spreads over many SMs
 
 // ---------------------------------------------------------------------------------
 // Launchers (defined in the .cu files).
