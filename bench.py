@@ -180,6 +180,34 @@ def oracle_step(s, n, threads, pool):
     return time.perf_counter() - t0
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), for the baseline line."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_direct_pairs_per_s(s, threads, pool, n_a=400):
+    """Eq. (Coulomb) by the oracle on a sample: the first n_a atoms of A against all of B, split
+    across host threads.  Returns pair interactions per second."""
+    import oracle
+    cA, _ = oracle.center_radius(s.A)
+    cB, _ = oracle.center_radius(s.B)
+    bounds = np.linspace(0, n_a, threads + 1).astype(int)
+    t0 = time.perf_counter()
+    futs = [pool.submit(oracle.direct, s.A[bounds[i]:bounds[i + 1]], cA, s.B, cB, s.R0[0], s.rotB[0])
+            for i in range(threads)]
+    for f in futs:
+        f.result()
+    return n_a * len(s.B) / (time.perf_counter() - t0)
+
+
 def oracle_sample_size(per_atom, seconds, threads, n_max):
     return int(min(n_max, max(threads * 8, seconds * threads / per_atom)))
 
@@ -387,12 +415,16 @@ def run_ours(args, rank, world, dist):
         n = len(s.B)
         with ThreadPoolExecutor(max_workers=threads) as pool:
             tm = min(oracle_step(s, n, threads, pool) for _ in range(2))
+            t1 = oracle_step(s, n // 8, 1, pool)  # one thread on an eighth of the atoms
+            dpairs = oracle_direct_pairs_per_s(s, threads, pool)
         tc = oracle_contraction_seconds(s)
-        cpu = {"value": n / tm, "unit": UNIT, "cores": threads, "kind": "oracle",
+        cpu = {"value": n / tm, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
                "sample": f"oracle Eq. (multipole) at L={L} over all {n} atoms of one rotated copy of B, split across "
                          f"{threads} host threads (best of 2); one Eq. (Formula) contraction took {tc:.3f} s "
                          f"single-threaded",
-               "energies_per_s_single_thread": 1.0 / tc}
+               "single_thread_value": (n // 8) / t1,
+               "energies_per_s_single_thread": 1.0 / tc,
+               "direct_pairs_per_s": dpairs}
 
     if rank == 0:
         p50 = float(np.percentile(step_ms, 50))
