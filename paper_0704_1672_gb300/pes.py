@@ -70,3 +70,45 @@ def scan(ctx, A, B, R0, lmax_values, precision=None, direct=True, cA=None, cB=No
     res.centers = (mA.center, mB.center)
     res.radii = (mA.radius, mB.radius)
     return res
+
+
+def main():
+    """Command line: the Section IV surface scan on synthetic proteins; prints one JSON line with
+    the timings, energies per second and the median and maximum of Eq. (error) per Lmax."""
+    import argparse
+    import json
+
+    import torch
+
+    from . import build, synth, tcm
+    p = argparse.ArgumentParser(description="TCM surface scan (R0, Theta) with Eq. (error) maps")
+    p.add_argument("--dr", type=float, default=1.0)
+    p.add_argument("--dtheta", type=float, default=1.0)
+    p.add_argument("--lmax", type=str, default="1,2,3,4,6,8,10")
+    p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--no-direct", action="store_true", help="skip the exact energies")
+    p.add_argument("--repeat", type=int, default=2, help="scans run; the last is reported")
+    args = p.parse_args()
+    build.build()
+    g = synth.pes_grid_pair(dr=args.dr, dtheta=args.dtheta, lmax=tuple(int(x) for x in args.lmax.split(",")))
+    A = torch.tensor(g.A, device="cuda")
+    B = torch.tensor(g.B, device="cuda")
+    ctx = tcm.Context(lmax_cap=max(g.lmax))
+    prec = tcm.TCM_MIXED if args.precision == "mixed" else tcm.TCM_FP64
+    try:
+        for _ in range(max(1, args.repeat)):
+            res = scan(ctx, A, B, g.R0(), g.lmax, precision=prec, direct=not args.no_direct)
+    finally:
+        ctx.close()
+    n = len(res.R0)
+    out = {"workload": g.name, "points": n, "lmax": list(g.lmax), "timings_ms": res.timings_ms,
+           "tcm_energies_per_s": n * len(g.lmax) / (res.timings_ms["tcm_energies"] * 1e-3)}
+    if res.U_coul is not None:
+        out["direct_pairs_per_s"] = n * len(g.A) * len(g.B) / (res.timings_ms["direct"] * 1e-3)
+        out["eq_error_percent_median"] = {str(L): float(np.median(res.eta(L))) for L in g.lmax}
+        out["eq_error_percent_max"] = {str(L): float(np.max(res.eta(L))) for L in g.lmax}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
