@@ -250,27 +250,31 @@ double chunk_cost(int precision, int L, int chunk) {
   return 1.25 * chunk_off(L, m0, m1) + 4.0 * m0 + 30.0;
 }
 
+// Tiles grouped by L; within a degree, the (job, chunk) groups in decreasing order of their
+// tiles' cost (largest first, so the persistent warps finish together), each group's tiles in
+// order.  Sorting groups rather than tiles keeps the host cost O(tiles + groups log groups).
 void build_tiles(int precision, Plan& P) {
-  std::vector<std::vector<std::pair<double, MomTile>>> byL(kLmaxMax + 1);
+  struct Group {
+    double cost;
+    int job, chunk;
+  };
+  std::vector<std::vector<Group>> byL(kLmaxMax + 1);
   for (int ji = 0; ji < (int)P.jobs.size(); ++ji) {
     const MomJob& j = P.jobs[ji];
     const int nch = moments_nchunks(precision, j.L);
-    for (int ch = 0; ch < nch; ++ch) {
-      const double cc = chunk_cost(precision, j.L, ch);
-      for (int t = 0; t < j.tiles_per_chunk; ++t) {
-        const long long i0 = (long long)t * j.atoms_per_tile;
-        const long long cnt = std::max(0LL, std::min((long long)j.atoms_per_tile, j.n - i0));
-        MomTile mt{ji, ch, t, j.tile_base + ch * j.tiles_per_chunk + t};
-        byL[j.L].push_back({cc * (double)cnt, mt});
-      }
-    }
+    for (int ch = 0; ch < nch; ++ch)
+      byL[j.L].push_back({chunk_cost(precision, j.L, ch) * (double)j.atoms_per_tile, ji, ch});
   }
   P.tiles.clear();
   for (int L = 0; L <= kLmaxMax; ++L) {
     P.tile_begin[L] = (int)P.tiles.size();
     auto& v = byL[L];
-    std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-    for (auto& e : v) P.tiles.push_back(e.second);
+    std::stable_sort(v.begin(), v.end(), [](const Group& a, const Group& b) { return a.cost > b.cost; });
+    for (const Group& g : v) {
+      const MomJob& j = P.jobs[g.job];
+      for (int t = 0; t < j.tiles_per_chunk; ++t)
+        P.tiles.push_back(MomTile{g.job, g.chunk, t, j.tile_base + g.chunk * j.tiles_per_chunk + t});
+    }
   }
   P.tile_begin[kLmaxMax + 1] = (int)P.tiles.size();
 }

@@ -29,7 +29,7 @@ import numpy as np
 
 # ----------------------------------------------------------------------------- requests
 
-@dataclass
+@dataclass(eq=False)  # identity comparison: requests are removed from lists by identity
 class Request:
     rid: int
     a: int
@@ -54,16 +54,17 @@ class Request:
 
 @dataclass
 class Batch:
-    """Work items of one iteration: (request, item index) pairs in slot order."""
-    owners: list = field(default_factory=list)
-    a: list = field(default_factory=list)
-    b: list = field(default_factory=list)
-    L: list = field(default_factory=list)
-    rot: list = field(default_factory=list)
-    R0: list = field(default_factory=list)
+    """Work items of one iteration, as per-request segments (request, first item, count) and the
+    items' arrays in slot order."""
+    segments: list = field(default_factory=list)
+    a: np.ndarray = None
+    b: np.ndarray = None
+    L: np.ndarray = None
+    rot: np.ndarray = None  # (k, 3, 3)
+    R0: np.ndarray = None   # (k, 3)
 
     def __len__(self):
-        return len(self.owners)
+        return 0 if self.a is None else len(self.a)
 
 
 # ----------------------------------------------------------------------------- engine
@@ -134,35 +135,43 @@ class Engine:
         share = max(1, min(self.quota, self.max_items // n))
         order = [self.active[(self._rr + i) % n] for i in range(n)]
         self._rr = (self._rr + 1) % max(1, n)
+        total = 0
         for req in order:
-            take = min(share, req.n - req.next_item, self.max_items - len(b))
-            for k in range(req.next_item, req.next_item + take):
-                b.owners.append((req, k))
-                b.a.append(req.a)
-                b.b.append(req.b)
-                b.L.append(req.L)
-                b.rot.append(req.rot[k])
-                b.R0.append(req.R0[k])
+            take = min(share, req.n - req.next_item, self.max_items - total)
+            if take <= 0:
+                continue
+            b.segments.append((req, req.next_item, take))
             req.next_item += take
-            if len(b) >= self.max_items:
+            total += take
+            if total >= self.max_items:
                 break
+        if not b.segments:
+            return b
+        counts = np.fromiter((t for _, _, t in b.segments), dtype=np.int64, count=len(b.segments))
+        per_req = np.array([(r.a, r.b, r.L) for r, _, _ in b.segments], dtype=np.int32)
+        b.a = np.repeat(per_req[:, 0], counts)
+        b.b = np.repeat(per_req[:, 1], counts)
+        b.L = np.repeat(per_req[:, 2], counts)
+        b.rot = np.concatenate([r.rot[k:k + t] for r, k, t in b.segments])
+        b.R0 = np.concatenate([r.R0[k:k + t] for r, k, t in b.segments])
         return b
 
     def _complete(self, handle, batch):
         E, st = self.ex.collect(handle)
         now = self.clock()
-        for (req, k), e, s in zip(batch.owners, E, st):
-            if req.state != "active":
-                continue  # cancelled meanwhile
-            req.E[k] = e
-            req.status[k] = s
-            req.done_items += 1
-            if req.done_items == req.n:
-                req.state = "done"
-                req.t_done = now
-                self.active.remove(req)
-                self.used -= req.footprint
-                self.done.append(req)
+        off = 0
+        for req, k, t in batch.segments:
+            if req.state == "active":  # else cancelled meanwhile: results discarded
+                req.E[k:k + t] = E[off:off + t]
+                req.status[k:k + t] = st[off:off + t]
+                req.done_items += t
+                if req.done_items == req.n:
+                    req.state = "done"
+                    req.t_done = now
+                    self.active.remove(req)
+                    self.used -= req.footprint
+                    self.done.append(req)
+            off += t
 
     def step(self):
         """One scheduling iteration; returns True if anything happened."""
