@@ -38,6 +38,9 @@
  *     (tcm_energy, tcm_direct, tcm_prepare, tcm_moments when it must compute a
  *     centre or radius) synchronise that stream; the others are asynchronous.
  *   - A context is used by one host thread at a time.
+ *   - The calls stage their descriptors through pinned host buffers and may wait on the
+ *     host for a staging slot, so they cannot be captured into a caller's CUDA graph; the
+ *     library captures and replays its own launch sequence instead (tcm_ctx_set_graphs).
  *
  * Errors
  *   Every call returns a tcm_status; nothing throws across the ABI.  On failure
