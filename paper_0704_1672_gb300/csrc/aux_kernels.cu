@@ -388,23 +388,38 @@ __device__ Euler euler_zyz(const double* M) {
   return e;
 }
 
-__device__ void phase_powers(double2* ph, double2 e, int L) {  // ph[m] = conj(e)^m, m <= L
-  double er = 1.0, ei = 0.0;
-  for (int m = 0; m <= L; ++m) {
-    ph[m] = make_double2(er, ei);
-    const double nr = er * e.x + ei * e.y;
-    ei = ei * e.x - er * e.y;
-    er = nr;
+__device__ __forceinline__ double2 cmul(double2 a, double2 b);
+
+// x^n and z^n by binary powering (n >= 0): O(log n) multiplications, so every entry of a
+// power table is computed by its own thread instead of along one serial chain.
+__device__ __forceinline__ double rpow(double x, int n) {
+  double r = 1.0;
+  while (n) {
+    if (n & 1) r *= x;
+    x *= x;
+    n >>= 1;
   }
+  return r;
+}
+__device__ __forceinline__ double2 cpow(double2 z, int n) {
+  double2 r = make_double2(1.0, 0.0);
+  while (n) {
+    if (n & 1) r = cmul(r, z);
+    z = cmul(z, z);
+    n >>= 1;
+  }
+  return r;
 }
 
-__device__ void half_angle_powers(double* cp, double* sp, double ch, double sh, int L) {  // k <= 2L
-  double c = 1.0, s = 1.0;
-  for (int k = 0; k <= 2 * L; ++k) {
-    cp[k] = c;
-    sp[k] = s;
-    c *= ch;
-    s *= sh;
+// ph[m] = conj(e)^m (m <= L), cp[k] = ch^k, sp[k] = sh^k (k <= 2L), all threads of the block.
+__device__ void phase_powers(double2* ph, double2 e, int L) {
+  const double2 c = make_double2(e.x, -e.y);
+  for (int m = threadIdx.x; m <= L; m += blockDim.x) ph[m] = cpow(c, m);
+}
+__device__ void half_angle_powers(double* cp, double* sp, double ch, double sh, int L) {
+  for (int k = threadIdx.x; k <= 2 * L; k += blockDim.x) {
+    cp[k] = rpow(ch, k);
+    sp[k] = rpow(sh, k);
   }
 }
 
@@ -446,6 +461,7 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
                                                                const MomJob* __restrict__ jobs,
                                                                const SysGeom* __restrict__ geoms,
                                                                const double* __restrict__ ztab,
+                                                               const double* __restrict__ rots,
                                                                double* __restrict__ E, int32_t* __restrict__ status,
                                                                double* __restrict__ G) {
   const double* rtab = ztab + ((kZ_TOTAL + 3) / 4 * 4);  // recursion coefficients, 4 doubles per (l, a, b)
@@ -496,8 +512,8 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     g_ch = sqrt(0.5 * opc);
     g_sh = sqrt(0.5 * omc);
     g_iR = 1.0 / R;
-  } else if (threadIdx.x == 128 && bmode == kBRotate) {
-    g_eb = euler_zyz(items[blockIdx.x].Mb);
+  } else if (threadIdx.x == 32 && bmode == kBRotate) {
+    g_eb = euler_zyz(rots + 9LL * d.rot);
   }
   for (int k = threadIdx.x; k < nq; k += blockDim.x) {
     const int l = tri_l(k);
@@ -506,22 +522,16 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     qb[k] = m == 0 ? make_double2(pb[l * l], 0.0) : make_double2(pb[l * l + 2 * m - 1], pb[l * l + 2 * m]);
   }
   __syncthreads();
-  if (threadIdx.x == 32) {  // e^{-i m alpha}
+  {  // e^{-i m alpha}, the half-angle powers and R^-(k+1), every thread a share
     const double rho = sqrt(x * x + y * y);
     const double ca = rho > 0.0 ? x / rho : 1.0, sa = rho > 0.0 ? y / rho : 0.0;
     phase_powers(ph, make_double2(ca, sa), L);
-  } else if (threadIdx.x == 64) {
     half_angle_powers(cp, sp, g_ch, g_sh, L);
-  } else if (threadIdx.x == 96) {
-    double r = g_iR;
-    for (int k = 0; k <= 2 * L + 1; ++k) {
-      rp[k] = r;
-      r *= g_iR;
+    for (int k = threadIdx.x; k <= 2 * L + 1; k += blockDim.x) rp[k] = rpow(g_iR, k + 1);
+    if (bmode == kBRotate) {
+      phase_powers(pha, g_eb.ea, L);
+      phase_powers(phg, g_eb.eg, L);
     }
-  } else if (threadIdx.x == 128 && bmode == kBRotate) {
-    phase_powers(pha, g_eb.ea, L);
-  } else if (threadIdx.x == 160 && bmode == kBRotate) {
-    phase_powers(phg, g_eb.eg, L);
   }
   __syncthreads();
   // P_lm = e^{-i m alpha} Q_lm, once per (l, m), for the sides that are rotated here
@@ -547,7 +557,7 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     }
   } else {  // B's cached lab-frame moments by its own rotation M_B = R_z(-gamma) R_y(-beta) R_z(-alpha)
     __syncthreads();  // every thread is done with the frame's table
-    if (threadIdx.x == 64) half_angle_powers(cp, sp, g_eb.ch, g_eb.sh, L);
+    half_angle_powers(cp, sp, g_eb.ch, g_eb.sh, L);
     __syncthreads();
     wigner_half_table(D, cp, sp, g_eb.cb, L, ztab, rtab);
     __syncthreads();
@@ -668,9 +678,9 @@ __global__ void __launch_bounds__(kContractThreads) k_rotate_moments(const RotDe
     q[k] = m == 0 ? make_double2(d.in[l * l], 0.0) : make_double2(d.in[l * l + 2 * m - 1], d.in[l * l + 2 * m]);
   }
   __syncthreads();
-  if (threadIdx.x == 0) phase_powers(pha, g_e.ea, L);
-  else if (threadIdx.x == 32) phase_powers(phg, g_e.eg, L);
-  else if (threadIdx.x == 64) half_angle_powers(cp, sp, g_e.ch, g_e.sh, L);
+  phase_powers(pha, g_e.ea, L);
+  phase_powers(phg, g_e.eg, L);
+  half_angle_powers(cp, sp, g_e.ch, g_e.sh, L);
   __syncthreads();
   for (int k = threadIdx.x; k < nq; k += blockDim.x) {
     const int l = tri_l(k);
@@ -762,6 +772,13 @@ __global__ void k_direct_final(const double* __restrict__ part, int nblk, double
 
 }  // namespace
 
+// Threads per contraction CTA: the largest per-degree loops have (L+1)^2 iterations, so small
+// degrees take smaller CTAs (more of them resident per SM); at least 64, at most 256.
+int contract_threads(int L) {
+  const int n = (L + 1) * (L + 1);
+  return n <= 64 ? 64 : (n <= 128 ? 128 : kContractThreads);
+}
+
 int contract_smem_bytes(int L) {
   const int nq = (L + 1) * (L + 2) / 2;
   const int nd = (L + 1) * (L + 2) * (2 * L + 3) / 6;
@@ -781,7 +798,7 @@ int launch_rotate_moments(const RotDesc* sets, int n_sets, int Lmax_sets, const 
     if (cudaFuncSetAttribute(k_rotate_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return -1;
   }
-  k_rotate_moments<<<n_sets, kContractThreads, smem, s>>>(sets, ztab);
+  k_rotate_moments<<<n_sets, contract_threads(Lmax_sets), smem, s>>>(sets, ztab);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -806,19 +823,20 @@ int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, cons
 }
 
 int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const MomJob* jobs, const SysGeom* geoms,
-                    const double* ztab, double* E, int32_t* status, double* G, cudaStream_t s) {
+                    const double* ztab, const double* rots, double* E, int32_t* status, double* G, cudaStream_t s) {
   if (n_items <= 0) return 0;
   const int smem = contract_smem_bytes(Lmax_items);
+  const int nt = contract_threads(Lmax_items);
   if (G) {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return -1;
-    k_contract<true><<<n_items, kContractThreads, smem, s>>>(items, jobs, geoms, ztab, E, status, G);
+    k_contract<true><<<n_items, nt, smem, s>>>(items, jobs, geoms, ztab, rots, E, status, G);
   } else {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return -1;
-    k_contract<false><<<n_items, kContractThreads, smem, s>>>(items, jobs, geoms, ztab, E, status, nullptr);
+    k_contract<false><<<n_items, nt, smem, s>>>(items, jobs, geoms, ztab, rots, E, status, nullptr);
   }
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }

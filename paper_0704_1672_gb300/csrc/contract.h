@@ -21,7 +21,8 @@ struct PairDesc {  // one energy: moments of jobA and jobB at lmax L, separation
   int L;
   int b_mode;      // kBLab, kBInFrame or kBRotate
   double R0[3];
-  double Mb[9];    // kBRotate: rotation taking B's lab-frame moments into the frame
+  long long rot;   // kBRotate: index of the 3x3 rotation (W rotB) taking B's lab-frame moments
+                   // into the frame, in the call's rotation array
 };
 
 struct RotDesc {  // one moment set rotated about its centre: out = moments of (M x) from in
@@ -32,9 +33,10 @@ struct RotDesc {  // one moment set rotated about its centre: out = moments of (
 };
 
 // G (optional, device, 9 doubles per item): force on B, torque on A, torque on B (lab frame).
+// rots: device, 9 doubles per kBRotate item (PairDesc.rot), or null when there is none.
 int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const MomJob* jobs,
-                    const SysGeom* geoms, const double* ztab, double* E, int32_t* status, double* G,
-                    cudaStream_t s);
+                    const SysGeom* geoms, const double* ztab, const double* rots, double* E, int32_t* status,
+                    double* G, cudaStream_t s);
 int contract_smem_bytes(int L);
 int rotate_smem_bytes(int L);
 int launch_rotate_moments(const RotDesc* sets, int n_sets, int Lmax_sets, const double* ztab, cudaStream_t s);

@@ -641,7 +641,7 @@ int tcm_energy(tcm_ctx_t c, const tcm_moments_t* A, const tcm_moments_t* B, cons
   geoms[0].a = A->radius;
   geoms[1].a = B->radius;
   std::vector<PairDesc> items(1);
-  items[0] = PairDesc{0, 1, 0, 1, lmax, kBLab, {R0[0], R0[1], R0[2]}, {}};
+  items[0] = PairDesc{0, 1, 0, 1, lmax, kBLab, {R0[0], R0[1], R0[2]}, 0};
   Packer pk;
   const size_t o_job = pk.add(jobs), o_geo = pk.add(geoms), o_it = pk.add(items);
   char* base = nullptr;
@@ -652,7 +652,7 @@ int tcm_energy(tcm_ctx_t c, const tcm_moments_t* A, const tcm_moments_t* B, cons
     PhaseScope ps(c, TCM_PHASE_CONTRACT, 1);
     TRY_LAUNCH(launch_contract(reinterpret_cast<PairDesc*>(base + o_it), 1, lmax,
                                reinterpret_cast<MomJob*>(base + o_job), reinterpret_cast<SysGeom*>(base + o_geo),
-                               c->d_ztab, dE, nullptr, nullptr, c->stream));
+                               c->d_ztab, nullptr, dE, nullptr, nullptr, c->stream));
   }
   TRY_CUDA(cudaMemcpyAsync(c->pinned_small, dE, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   TRY_CUDA(cudaStreamSynchronize(c->stream));
@@ -787,6 +787,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
     job_of[key] = id;
     return id;
   };
+  std::vector<double> rots;  // 3x3 per rotate-from-cache item
   for (int64_t k = 0; k < n_items; ++k) {
     const tcm_pair_item& it = items[k];
     const int ja = get_job(it.a, it.lmax, -1, nullptr);
@@ -796,10 +797,11 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
       double W[9];
       frame_rotation(it.R0, W);
       jb = get_job(it.b, it.lmax, -1, nullptr);
-      pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, kBRotate, {it.R0[0], it.R0[1], it.R0[2]}, {}};
+      pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, kBRotate, {it.R0[0], it.R0[1], it.R0[2]},
+                       (long long)(rots.size() / 9)};
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
-          pd[k].Mb[3 * i + j] = W[3 * i + 0] * it.rotB[0 + j] + W[3 * i + 1] * it.rotB[3 + j] + W[3 * i + 2] * it.rotB[6 + j];
+          rots.push_back(W[3 * i + 0] * it.rotB[0 + j] + W[3 * i + 1] * it.rotB[3 + j] + W[3 * i + 2] * it.rotB[6 + j]);
       continue;
     }
     if (it.has_rot) {
@@ -814,7 +816,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
     } else {
       jb = get_job(it.b, it.lmax, -1, nullptr);
     }
-    pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, it.has_rot ? kBInFrame : kBLab, {it.R0[0], it.R0[1], it.R0[2]}, {}};
+    pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, it.has_rot ? kBInFrame : kBLab, {it.R0[0], it.R0[1], it.R0[2]}, 0};
   }
   P.n_tile_ids = next_id;
   TRY(dev_ensure(c, c->moms, std::max<size_t>(moff, 1) * sizeof(double)));
@@ -837,7 +839,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   for (int s = 0; s < n_systems; ++s) geoms[s] = host_geom(systems[s]);
   Packer pk;
   const size_t o_geo = pk.add(geoms), o_job = pk.add(all_jobs), o_tile = pk.add(P.tiles), o_gj = pk.add(gjobs),
-               o_gt = pk.add(gtiles), o_it = pk.add(pd);
+               o_gt = pk.add(gtiles), o_it = pk.add(pd), o_rot = pk.add(rots);
   // every buffer the launches touch is sized before anything is queued (no reallocation
   // may happen while a graph is being captured)
   if (!gjobs.empty())
@@ -860,7 +862,8 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
     TRY(run_moments(c, precision, P, d_jobs, reinterpret_cast<MomTile*>(base + o_tile), d_geo, st));
     PhaseScope ps(c, TCM_PHASE_CONTRACT, 1);
     TRY_LAUNCH(launch_contract(reinterpret_cast<PairDesc*>(base + o_it), (int)n_items, Lmax_items, d_jobs, d_geo,
-                               c->d_ztab, E, status, G, st));
+                               c->d_ztab, rots.empty() ? nullptr : reinterpret_cast<double*>(base + o_rot), E,
+                               status, G, st));
     return TCM_OK;
   };
   if (!c->graphs || c->prof || !c->cap_stream) return enqueue(c->stream);
@@ -868,7 +871,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   // buffers as the captured one (only the uploaded descriptor contents differ).
   std::vector<long long> key = {precision, G != nullptr, (long long)(uintptr_t)G, ngt, (long long)gjobs.size(), (long long)P.jobs.size(), P.n_tile_ids,
                                 (long long)n_items, Lmax_items, (long long)o_geo, (long long)o_job, (long long)o_tile,
-                                (long long)o_gj, (long long)o_gt, (long long)o_it, (long long)(uintptr_t)base,
+                                (long long)o_gj, (long long)o_gt, (long long)o_it, (long long)o_rot, (long long)rots.empty(), (long long)(uintptr_t)base,
                                 (long long)(uintptr_t)c->gpart.p, (long long)(uintptr_t)c->partials.p,
                                 (long long)(uintptr_t)c->counters.p, (long long)(uintptr_t)E,
                                 (long long)(uintptr_t)status};
