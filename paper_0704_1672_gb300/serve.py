@@ -361,8 +361,8 @@ def main():
     p.add_argument("--seconds", type=float, default=10.0)
     p.add_argument("--rate", type=float, default=2000.0)
     p.add_argument("--pool", type=int, default=512)
-    p.add_argument("--max-items", type=int, default=2048)
-    p.add_argument("--quota", type=int, default=256)
+    p.add_argument("--max-items", type=int, default=8192)
+    p.add_argument("--quota", type=int, default=512)
     p.add_argument("--budget-gb", type=float, default=4.0)
     p.add_argument("--plain-fp64", type=int, default=100, help="requests timed through the plain FP64 path")
     p.add_argument("--rotate-cached", action="store_true",
