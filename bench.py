@@ -406,8 +406,12 @@ def run_ours(args, rank, world, dist):
 
     # reference points: the plain single-request FP64 GPU path, and the CPU oracle
     fp64_plain = None
+    fp64_batched = None
     if args.fp64_steps > 0 and rank == 0:
         fp64_plain = plain_fp64(ctx, tcm, torch, A, B, s, args.fp64_steps)
+        if prec == tcm.TCM_MIXED:
+            fp64_batched = batched_fp64(ctx, tcm, torch, pb, E, st, stream, flush, atoms_per_step, k,
+                                        n_sm, sm_max, L)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         from concurrent.futures import ThreadPoolExecutor
@@ -438,7 +442,7 @@ def run_ours(args, rank, world, dist):
                 "gpu_launches_per_step": {p: launches[p] / args.steps for p in launches},
                 "roofline": roofline, "clocks": ck, "e2e": e2e, "graph_replay": graph_replay,
                 "rotate_cached": rotate_cached, "pes_grid": pes_grid,
-                "fp64_plain_gpu": fp64_plain,
+                "fp64_plain_gpu": fp64_plain, "fp64_batched_gpu": fp64_batched,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -480,6 +484,39 @@ def run_pes_grid(torch, tcm, prec, n_sm, sm_mhz, stream):
                                 "peak_source": f"{n_sm} SMs x {FP64_PER_SM_CLK} FP64/clk x {sm_mhz:.0f} MHz"},
             "eq_error_percent_median": {str(L): float(np.median(res.eta(L))) for L in g.lmax},
             "eq_error_percent_max": {str(L): float(np.max(res.eta(L))) for L in g.lmax}}
+
+
+def batched_fp64(ctx, tcm, torch, pb, E, st, stream, flush, atoms_per_step, k, n_sm, sm_mhz, L, steps=5):
+    """The same batched step in double precision throughout (double moment kernels): the
+    accuracy the plain FP64 path has, at batched throughput.  Moment phase against the FP64
+    pipe (3 (L+1)^2 + 12 FP64 instructions per atom-moment)."""
+    ctx.tcm_ctx_set_profiling(True)
+    ctx.tcm_ctx_read_profile()
+    for _ in range(2):
+        flush.zero_()
+        ctx.tcm_energy_batch_packed(pb, tcm.TCM_FP64, E, st)
+    torch.cuda.synchronize()
+    ctx.tcm_ctx_read_profile()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0.record(stream)
+        ctx.tcm_energy_batch_packed(pb, tcm.TCM_FP64, E, st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms, launches = ctx.tcm_ctx_read_profile()
+    ctx.tcm_ctx_set_profiling(False)
+    step_ms = tot / steps
+    mom_ms = ms["moments"] / max(1, launches["moments"])
+    achieved = atoms_per_step * moment_instr_per_atom(L) / (mom_ms * 1e-3) / 1e9
+    peak = n_sm * FP64_PER_SM_CLK * sm_mhz * 1e6 / 1e9
+    return {"value": atoms_per_step / (step_ms * 1e-3), "unit": UNIT, "energies_per_s": k / (step_ms * 1e-3),
+            "ms_per_step": step_ms, "steps": steps, "moments_ms": mom_ms,
+            "moments_roofline": {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "G FP64 instr/s",
+                                 "frac": achieved / peak},
+            "how": "the benchmark batch through tcm_energy_batch at TCM_FP64 (double moment kernels)"}
 
 
 def plain_fp64(ctx, tcm, torch, A, B, s, steps):
