@@ -707,11 +707,15 @@ __global__ void __launch_bounds__(kContractThreads) k_rotate_moments(const RotDe
 // already rotated and translated: b' = R0 + rot (x_b - c_B).  Double precision.
 constexpr int kDirectThreads = 256;
 
+struct alignas(32) Atom4 {  // a staged atom of B: position after rotation and separation, charge
+  double x, y, z, w;
+};
+
 __global__ void __launch_bounds__(kDirectThreads) k_direct(const void* __restrict__ a, long long na, int dta,
                                                            const void* __restrict__ b, long long nb, int dtb,
                                                            const SysGeom* __restrict__ geo, const double* __restrict__ xf,
                                                            double* __restrict__ part) {
-  __shared__ double4 sb[kDirectThreads];
+  __shared__ Atom4 sb[kDirectThreads];
   __shared__ double sh[32];
   const double* cA = geo[0].c;
   const double* cB = geo[1].c;
@@ -729,7 +733,7 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const void* __restric
   double acc = 0.0;
   for (long long j0 = 0; j0 < nb; j0 += kDirectThreads) {
     const long long j = j0 + threadIdx.x;
-    double4 v = make_double4(1e300, 1e300, 1e300, 0.0);
+    Atom4 v{1e300, 1e300, 1e300, 0.0};
     if (j < nb) {
       double x, y, z, q;
       load_xyz(b, dtb, j, x, y, z, q);
@@ -747,7 +751,7 @@ __global__ void __launch_bounds__(kDirectThreads) k_direct(const void* __restric
     if (i < na) {
       const int cnt = (int)min((long long)kDirectThreads, nb - j0);
       for (int k = 0; k < cnt; ++k) {
-        const double4 w = sb[k];
+        const Atom4 w = sb[k];
         const double dx = w.x - ax, dy = w.y - ay, dz = w.z - az;
         acc += w.w * rsqrt(dx * dx + dy * dy + dz * dz);
       }
