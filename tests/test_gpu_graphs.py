@@ -117,3 +117,28 @@ def test_graph_replay_with_cached_moments(tcm):
     finally:
         ctx.close()
         ref.close()
+
+
+def test_graph_replay_of_gradients(tcm):
+    """The gradient variant of the batched call replays too, with the same forces and torques."""
+    T = [(s, None, None) for s in _systems()]
+    rad = [6.0, 10.0, 16.0]
+    k = 40
+    a, b, L, R0, rot = _items(11, k, rad)
+    E = torch.empty(k, dtype=torch.float64, device="cuda")
+    G = torch.empty((k, 9), dtype=torch.float64, device="cuda")
+    st = torch.empty(k, dtype=torch.int32, device="cuda")
+    direct = tcm.Context(lmax_cap=24)
+    direct.tcm_ctx_set_graphs(False)
+    graph = tcm.Context(lmax_cap=24)
+    try:
+        for rep in range(3):
+            R = R0 * (1.0 + 0.03 * rep)
+            Ed, Gd, _ = direct.tcm_gradients_batch(T, a, b, L, R, rotB=rot)
+            graph.tcm_gradients_batch(T, a, b, L, R, rotB=rot, E=E, G=G, status=st)
+            torch.cuda.synchronize()
+            assert torch.equal(Ed, E) and torch.equal(Gd, G), rep
+        assert graph.tcm_ctx_graph_stats()[1] >= 1
+    finally:
+        direct.close()
+        graph.close()

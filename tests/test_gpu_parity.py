@@ -217,3 +217,44 @@ def test_invalid_arguments(ctx, tcm):
     with pytest.raises(tcm.TcmError) as e:
         ctx.tcm_energy_batch([(S, None, None)], [0], [3], [4], [[0.0, 0.0, 100.0]])
     assert e.value.code == tcm.TCM_EINVAL
+
+
+@pytest.mark.parametrize("precision_name", ["TCM_FP64", "TCM_MIXED"])
+def test_degenerate_batch(ctx, tcm, precision_name):
+    """Empty systems, single charges at the centre, all-zero charges, Lmax = 0 and Lmax = 24
+    items side by side in one batch: each against the oracle (or its closed form)."""
+    precision = getattr(tcm, precision_name)
+    rng = np.random.default_rng(21)
+    empty = np.zeros((0, 4))
+    one = np.array([[1.0, -2.0, 0.5, 0.8]])
+    zeros = synth.pack(synth.uniform_ball(rng, 500, 4.0), np.zeros(500))
+    gen = sphere_system(22, 700, radius=5.0)
+    gen[:, 3] += 0.01
+    systems = [empty, one, zeros, gen]
+    dt = torch.float64 if precision == tcm.TCM_FP64 else torch.float32
+    T = [(dev(S, dt) if len(S) else torch.zeros((0, 4), dtype=dt, device="cuda"),
+          np.zeros(3) if len(S) == 0 else None, None) for S in systems]
+    items = [(0, 3, 6), (1, 3, 0), (1, 3, 24), (2, 3, 10), (3, 1, 12), (1, 1, 4), (3, 3, 24)]
+    a, b, L = zip(*items)
+    R0 = np.array([[0.0, 0.0, 40.0], [30.0, 1.0, -2.0], [0.0, 35.0, 0.0], [25.0, 25.0, 25.0],
+                   [-20.0, 10.0, 30.0], [5.0, 0.0, 0.0], [1e-9, 0.0, -30.0]])
+    E, st = ctx.tcm_energy_batch(T, a, b, L, R0, precision=precision)
+    torch.cuda.synchronize()
+    assert st.tolist() == [0] * len(items)
+    E = E.cpu().numpy()
+    mixed = precision == tcm.TCM_MIXED
+    for k, (ia, ib, Lk) in enumerate(items):
+        Sa = systems[ia].astype(np.float32).astype(np.float64) if mixed else systems[ia]
+        Sb = systems[ib].astype(np.float32).astype(np.float64) if mixed else systems[ib]
+        ca = np.zeros(3) if len(Sa) == 0 else oracle.center_radius(Sa)[0]
+        cb = np.zeros(3) if len(Sb) == 0 else oracle.center_radius(Sb)[0]
+        QA = oracle.moments(Sa, ca, Lk) if len(Sa) else np.zeros((Lk + 1) ** 2, dtype=complex)
+        QB = oracle.moments(Sb, cb, Lk) if len(Sb) else np.zeros((Lk + 1) ** 2, dtype=complex)
+        Eo = oracle.tcm_energy(Lk, QA, QB, R0[k])
+        blocks = oracle.tcm_blocks(Lk, QA, QB, R0[k])
+        if not np.any(blocks):
+            assert E[k] == 0.0, (k, E[k])
+        else:
+            assert energy_error(E[k], Eo, blocks, mixed=mixed) < (TOL_MIX_E if mixed else TOL_FP64), (k, E[k], Eo)
+    # a single charge at its own centroid against itself: q^2 / R exactly at every Lmax
+    assert abs(E[5] - 0.8 * 0.8 / 5.0) <= 1e-15 * 0.128 * (1 if not mixed else 1e8)
