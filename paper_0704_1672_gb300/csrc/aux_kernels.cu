@@ -5,6 +5,7 @@
 //   a4  irregular solid harmonics of the separation vector R0            (Eq. (Formula))
 //   a5  two-center contraction in double                                 (Eq. (Formula))
 //   a6  exact pairwise Coulomb sum in double                             (Eq. (Coulomb))
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "contract.h"
@@ -73,6 +74,118 @@ __device__ __forceinline__ void load_xyz(const void* p, int dtype, long long i, 
 }
 
 constexpr int kGeomThreads = 128;
+
+// a1 for a float32 system of at most kGeomClusterAtoms atoms, in one launch: a cluster of
+// kGeomClusterCTAs CTAs per system holds the atoms in registers (kGeomClusterPer per thread),
+// and the CTAs combine their partial sums through distributed shared memory, so the two passes
+// need neither a second launch nor global tickets.  The per-atom arithmetic is float:
+//   * centroid: each thread adds its coordinates with an error-free two-sum (value + error),
+//     the pairs go to double for the block and cluster sums (fixed order);
+//   * radius: |x - c|^2 in float from the split centre (c_hi + c_lo) picks the candidates
+//     within a relative 4e-6 of the largest (the float value is within 1e-6 of the exact one),
+//     and only those are recomputed in double; their maximum is the exact double radius^2.
+namespace cg = cooperative_groups;
+__device__ __forceinline__ void two_sum_add(float& s, float& e, float x) {
+  const float t = s + x;
+  const float bb = t - s;
+  e += (s - (t - bb)) + (x - bb);
+  s = t;
+}
+
+__global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeomClusterThreads)
+    k_geom_cluster(const GeomJob* __restrict__ gj, SysGeom* __restrict__ geoms) {
+  __shared__ double sh[32];
+  __shared__ double s_part[4];   // this CTA's sums (x, y, z) and, later, its max
+  __shared__ double s_c[3];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const GeomJob j = gj[blockIdx.x / kGeomClusterCTAs];
+  const float4* xyzq = reinterpret_cast<const float4*>(j.xyzq);
+  const long long stride = (long long)kGeomClusterCTAs * kGeomClusterThreads;
+  const long long i0 = (long long)rank * kGeomClusterThreads + threadIdx.x;
+  float x[kGeomClusterPer], y[kGeomClusterPer], z[kGeomClusterPer];
+#pragma unroll
+  for (int k = 0; k < kGeomClusterPer; ++k) {
+    const long long i = i0 + k * stride;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < j.n) v = __ldg(xyzq + i);
+    x[k] = v.x;
+    y[k] = v.y;
+    z[k] = v.z;
+  }
+  // pass 1: coordinate sums
+  float sx = 0.f, ex = 0.f, sy = 0.f, ey = 0.f, sz = 0.f, ez = 0.f;
+#pragma unroll
+  for (int k = 0; k < kGeomClusterPer; ++k) {  // padding atoms add exact zeros
+    two_sum_add(sx, ex, x[k]);
+    two_sum_add(sy, ey, y[k]);
+    two_sum_add(sz, ez, z[k]);
+  }
+  double tx = block_sum((double)sx + (double)ex, sh);
+  double ty = block_sum((double)sy + (double)ey, sh);
+  double tz = block_sum((double)sz + (double)ez, sh);
+  if (threadIdx.x == 0) {
+    s_part[0] = tx;
+    s_part[1] = ty;
+    s_part[2] = tz;
+  }
+  cluster.sync();
+  if (rank == 0 && threadIdx.x == 0) {
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int r = 0; r < kGeomClusterCTAs; ++r) {  // rank order
+      const double* p = cluster.map_shared_rank(s_part, r);
+      for (int d = 0; d < 3; ++d) c[d] += p[d];
+    }
+    const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
+    const SysGeom g = geoms[j.geom];
+    for (int d = 0; d < 3; ++d) s_c[d] = j.need_center ? c[d] * inv : g.c[d];
+  }
+  cluster.sync();
+  const double* c0 = cluster.map_shared_rank(s_c, 0);
+  const double cx = c0[0], cy = c0[1], cz = c0[2];
+  cluster.sync();  // every CTA has read the centre before CTA 0 reuses its buffers
+  // pass 2: largest |x - c|^2, float filter then exact double on the candidates
+  const float chx = (float)cx, chy = (float)cy, chz = (float)cz;
+  const float clx = (float)(cx - (double)chx), cly = (float)(cy - (double)chy), clz = (float)(cz - (double)chz);
+  float r2f[kGeomClusterPer];
+  float mf = 0.f;
+#pragma unroll
+  for (int k = 0; k < kGeomClusterPer; ++k) {
+    const float dx = (x[k] - chx) - clx, dy = (y[k] - chy) - cly, dz = (z[k] - chz) - clz;
+    r2f[k] = (i0 + k * stride < j.n) ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : -1.f;
+    mf = fmaxf(mf, r2f[k]);
+  }
+  mf = (float)block_max((double)mf, sh);
+  if (threadIdx.x == 0) s_part[3] = mf;
+  cluster.sync();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int r = 0; r < kGeomClusterCTAs; ++r) m = fmaxf(m, (float)cluster.map_shared_rank(s_part, r)[3]);
+    s_c[0] = m;  // reuse: the cluster's float maximum, per CTA
+  }
+  __syncthreads();
+  const float thr = (float)s_c[0] * (1.0f - 4e-6f);
+  double md = 0.0;
+#pragma unroll
+  for (int k = 0; k < kGeomClusterPer; ++k) {
+    if (r2f[k] >= thr) {
+      const double dx = (double)x[k] - cx, dy = (double)y[k] - cy, dz = (double)z[k] - cz;
+      md = fmax(md, dx * dx + dy * dy + dz * dz);
+    }
+  }
+  md = block_max(md, sh);
+  cluster.sync();  // all CTAs are done with s_part[3] and s_c before they are overwritten
+  if (threadIdx.x == 0) s_part[3] = md;
+  cluster.sync();
+  if (rank == 0 && threadIdx.x == 0) {
+    double m = 0.0;
+    for (int r = 0; r < kGeomClusterCTAs; ++r) m = fmax(m, cluster.map_shared_rank(s_part, r)[3]);
+    if (j.need_center)
+      for (int d = 0; d < 3; ++d) geoms[j.geom].c[d] = (d == 0 ? cx : (d == 1 ? cy : cz));
+    if (j.need_radius) geoms[j.geom].a = sqrt(m);
+  }
+  cluster.sync();  // no CTA exits while its shared memory may still be read
+}
 
 // a1, pass 1: per-tile sums of the coordinates (double); the last CTA of a system to
 // finish (ticket) adds the tile sums in tile order and writes the centroid.
@@ -806,17 +919,20 @@ int launch_rotate_moments(const RotDesc* sets, int n_sets, int Lmax_sets, const 
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n_gtiles, double* gpart, int* tickets,
-                SysGeom* geoms, cudaStream_t s) {
+int launch_geom(const GeomJob* gjobs, int n_gjobs, int n_cluster_jobs, const GeomTile* gtiles, int n_gtiles,
+                double* gpart, int* tickets, SysGeom* geoms, cudaStream_t s) {
   if (n_gjobs <= 0) return 0;
-  k_geom_centroid<<<n_gtiles, kGeomThreads, 0, s>>>(gjobs, gtiles, gpart, tickets, geoms);
-  k_geom_radius<<<n_gtiles, kGeomThreads, 0, s>>>(gjobs, gtiles, gpart, tickets, geoms);
+  if (n_cluster_jobs > 0)
+    k_geom_cluster<<<n_cluster_jobs * kGeomClusterCTAs, kGeomClusterThreads, 0, s>>>(gjobs, geoms);
+  if (n_gtiles > 0) {
+    k_geom_centroid<<<n_gtiles, kGeomThreads, 0, s>>>(gjobs, gtiles, gpart, tickets, geoms);
+    k_geom_radius<<<n_gtiles, kGeomThreads, 0, s>>>(gjobs, gtiles, gpart, tickets, geoms);
+  }
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-int geom_launches(int n_gjobs, int n_gtiles) {
-  if (n_gjobs <= 0) return 0;
-  return n_gtiles > 0 ? 2 : 0;
+int geom_launches(int n_cluster_jobs, int n_gtiles) {
+  return (n_cluster_jobs > 0 ? 1 : 0) + (n_gtiles > 0 ? 2 : 0);
 }
 
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms, const int* imap,

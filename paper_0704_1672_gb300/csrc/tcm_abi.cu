@@ -319,25 +319,38 @@ int* geom_tickets(tcm_ctx* c, int ngt, int) {
 }
 
 // Step a1 for the systems that need it (device only, no host round trip).
+// Step a1 jobs for the systems that need it (device only, no host round trip).  Float32
+// systems of at most kGeomClusterAtoms atoms come first and have no tiles (one cluster each);
+// the others are cut into kGeomTileAtoms tiles.  Returns the number of tiles.
 int add_geom_jobs(const tcm_system* systems, int n_systems, const std::vector<char>& used,
                   std::vector<GeomJob>& gjobs, std::vector<GeomTile>& gtiles) {
   int base = 0;
-  for (int s = 0; s < n_systems; ++s) {
-    if (!used[s] || geom_known(systems[s])) continue;
-    GeomJob g{};
-    g.xyzq = systems[s].xyzq;
-    g.n = systems[s].n;
-    g.dtype = systems[s].dtype;
-    g.geom = s;
-    g.need_center = systems[s].has_center ? 0 : 1;
-    g.need_radius = 1;
-    g.n_tiles = (int)std::max<long long>(1, (g.n + kGeomTileAtoms - 1) / kGeomTileAtoms);
-    g.tile_base = base;
-    base += g.n_tiles;
-    for (int t = 0; t < g.n_tiles; ++t) gtiles.push_back(GeomTile{(int)gjobs.size(), t});
-    gjobs.push_back(g);
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int s = 0; s < n_systems; ++s) {
+      if (!used[s] || geom_known(systems[s])) continue;
+      const bool cluster = systems[s].dtype == TCM_F32 && systems[s].n <= kGeomClusterAtoms;
+      if (cluster != (pass == 0)) continue;
+      GeomJob g{};
+      g.xyzq = systems[s].xyzq;
+      g.n = systems[s].n;
+      g.dtype = systems[s].dtype;
+      g.geom = s;
+      g.need_center = systems[s].has_center ? 0 : 1;
+      g.need_radius = 1;
+      g.n_tiles = cluster ? 0 : (int)std::max<long long>(1, (g.n + kGeomTileAtoms - 1) / kGeomTileAtoms);
+      g.tile_base = base;
+      base += g.n_tiles;
+      for (int t = 0; t < g.n_tiles; ++t) gtiles.push_back(GeomTile{(int)gjobs.size(), t});
+      gjobs.push_back(g);
+    }
   }
   return base;
+}
+
+int cluster_jobs(const std::vector<GeomJob>& gjobs) {
+  int n = 0;
+  for (const GeomJob& g : gjobs) n += g.n_tiles == 0;
+  return n;
 }
 
 SysGeom host_geom(const tcm_system& s) {
@@ -547,8 +560,8 @@ int tcm_prepare(tcm_ctx_t c, tcm_system* s) {
   TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   {
-    PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches((int)gjobs.size(), ngt));
-    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
+    PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches(cluster_jobs(gjobs), ngt));
+    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(), cluster_jobs(gjobs),
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
                            static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
   }
@@ -600,8 +613,8 @@ int tcm_moments(tcm_ctx_t c, const tcm_system* s, const double* rot, int lmax, i
   if (!gjobs.empty()) {
     TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
     TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
-    PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches((int)gjobs.size(), ngt));
-    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
+    PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches(cluster_jobs(gjobs), ngt));
+    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(), cluster_jobs(gjobs),
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
                            static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
   }
@@ -854,8 +867,8 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   auto enqueue = [&](cudaStream_t st) -> int {
     if (!gjobs.empty()) {
       TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), st));
-      PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches((int)gjobs.size(), ngt));
-      TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
+      PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches(cluster_jobs(gjobs), ngt));
+      TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(), cluster_jobs(gjobs),
                              reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
                              static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, st));
     }
@@ -870,7 +883,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   // Replay a captured graph of the launch sequence when this call has the same shape and
   // buffers as the captured one (only the uploaded descriptor contents differ).
   std::vector<long long> key = {precision, G != nullptr, (long long)(uintptr_t)G, ngt, (long long)gjobs.size(), (long long)P.jobs.size(), P.n_tile_ids,
-                                (long long)n_items, Lmax_items, (long long)o_geo, (long long)o_job, (long long)o_tile,
+                                (long long)n_items, Lmax_items, (long long)cluster_jobs(gjobs), (long long)o_geo, (long long)o_job, (long long)o_tile,
                                 (long long)o_gj, (long long)o_gt, (long long)o_it, (long long)o_rot, (long long)rots.empty(), (long long)(uintptr_t)base,
                                 (long long)(uintptr_t)c->gpart.p, (long long)(uintptr_t)c->partials.p,
                                 (long long)(uintptr_t)c->counters.p, (long long)(uintptr_t)E,
@@ -909,7 +922,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   }
   TRY_CUDA(cudaGraphLaunch(c->gexec, c->stream));
   ++c->graph_launches;
-  c->launches[TCM_PHASE_GEOM] += geom_launches((int)gjobs.size(), ngt);
+  c->launches[TCM_PHASE_GEOM] += geom_launches(cluster_jobs(gjobs), ngt);
   c->launches[TCM_PHASE_MOMENTS] += ngroups;
   c->launches[TCM_PHASE_FINALIZE] += 1;
   c->launches[TCM_PHASE_CONTRACT] += 1;
@@ -949,8 +962,8 @@ int direct_items(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, int64_t 
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   if (!gjobs.empty()) {
     TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
-    PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches((int)gjobs.size(), ngt));
-    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(),
+    PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches(cluster_jobs(gjobs), ngt));
+    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(), cluster_jobs(gjobs),
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
                            static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
   }

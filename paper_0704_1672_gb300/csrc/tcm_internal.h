@@ -172,6 +172,10 @@ struct GeomTile {
 };
 
 constexpr int kGeomTileAtoms = 256;  // small tiles: the per-atom double arithmetic spreads over many SMs
+constexpr int kGeomClusterCTAs = 8;     // CTAs per cluster (portable cluster size)
+constexpr int kGeomClusterThreads = 512;
+constexpr int kGeomClusterPer = 8;      // atoms per thread, held in registers
+constexpr long long kGeomClusterAtoms = (long long)kGeomClusterCTAs * kGeomClusterThreads * kGeomClusterPer;
 
 // ---------------------------------------------------------------------------------
 // Launchers (defined in the .cu files).
@@ -187,13 +191,15 @@ int moments_nchunks(int precision, int L);
 // 2 (kLmaxMax + 2) entries, FP64 first, each block ending with its total).
 void finalize_tables(std::vector<int>& imap_off, std::vector<int>& imap, std::vector<double>& fmap);
 
-// a1 in two tiled launches (the coordinate sums, then the largest |x - c|^2), spread over many
-// SMs because the per-atom double arithmetic would saturate the FP64 pipe of a few; tickets: one
-// int per geometry job, zero on entry (left zero on exit).  geom_launches gives the number of
-// kernels launch_geom queues.
-int launch_geom(const GeomJob* gjobs, int n_gjobs, const GeomTile* gtiles, int n_gtiles, double* gpart, int* tickets,
-                SysGeom* geoms, cudaStream_t s);
-int geom_launches(int n_gjobs, int n_gtiles);
+// a1.  The first n_cluster_jobs geometry jobs (float32 systems of at most kGeomClusterAtoms atoms,
+// no tiles) take one launch of one thread-block cluster each; the others go through two tiled
+// launches (the coordinate sums, then the largest |x - c|^2) spread over many SMs, because their
+// per-atom double arithmetic would saturate the FP64 pipe of a few.  tickets: one int per
+// geometry job, zero on entry (left zero on exit).  geom_launches gives the number of kernels
+// launch_geom queues.
+int launch_geom(const GeomJob* gjobs, int n_gjobs, int n_cluster_jobs, const GeomTile* gtiles, int n_gtiles,
+                double* gpart, int* tickets, SysGeom* geoms, cudaStream_t s);
+int geom_launches(int n_cluster_jobs, int n_gtiles);
 // Step a3: one CTA per job.  imap + imap_off[L] lists, per (chunk, slot) of degree L, the packed
 // component it holds (-1 for none), nch(L) x kmax entries; fmap beside it holds that
 // component's F_lm with the sign of the kernels' H variables.

@@ -152,13 +152,16 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   gj.need_center = s->has_center ? 0 : 1;
   gj.need_radius = 1;
   gj.tile_base = 0;
-  gj.n_tiles = (int)std::max<long long>(1, (s->n + kGeomTileAtoms - 1) / kGeomTileAtoms);
+  gj.n_tiles = (s->dtype == TCM_F32 && s->n <= kGeomClusterAtoms)
+                   ? 0
+                   : (int)std::max<long long>(1, (s->n + kGeomTileAtoms - 1) / kGeomTileAtoms);
 
   MomJob* d_job = reinterpret_cast<MomJob*>(base + kOffJob);
   SysGeom* d_geom = reinterpret_cast<SysGeom*>(base + kOffGeom);
   k_noalloc_prepare<<<1, 256, 0, st>>>(base, job, geom, gj, known ? 0 : gj.n_tiles, nch, tpc);
   if (cudaPeekAtLastError() != cudaSuccess) return na_err(TCM_ECUDA, "tcm_moments_noalloc: launch failed");
-  if (!known && launch_geom(reinterpret_cast<GeomJob*>(base + kOffGJob), 1, reinterpret_cast<GeomTile*>(base + kOffGTiles),
+  if (!known && launch_geom(reinterpret_cast<GeomJob*>(base + kOffGJob), 1, gj.n_tiles == 0 ? 1 : 0,
+                            reinterpret_cast<GeomTile*>(base + kOffGTiles),
                             gj.n_tiles, reinterpret_cast<double*>(base + kOffGPart),
                             reinterpret_cast<int*>(base + kOffCounters) + 32, d_geom, st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: centre/radius launch failed");

@@ -258,3 +258,21 @@ def test_degenerate_batch(ctx, tcm, precision_name):
             assert energy_error(E[k], Eo, blocks, mixed=mixed) < (TOL_MIX_E if mixed else TOL_FP64), (k, E[k], Eo)
     # a single charge at its own centroid against itself: q^2 / R exactly at every Lmax
     assert abs(E[5] - 0.8 * 0.8 / 5.0) <= 1e-15 * 0.128 * (1 if not mixed else 1e8)
+
+
+@pytest.mark.parametrize("n", [0, 1, 100, 5000, 32768, 32769, 70000])
+def test_prepare_float32_centre_and_radius(ctx, tcm, n):
+    """Step a1 for float32 systems: one cluster per system up to 32,768 atoms (float arithmetic
+    with an error-free centroid sum and an exact double radius over the float-filtered
+    candidates), the tiled kernels above: both against the oracle on the same float values."""
+    rng = np.random.default_rng(300 + n)
+    S = synth.pack(synth.uniform_ball(rng, n, 25.0) + [1000.0, -500.0, 250.0], rng.normal(size=n))
+    S32 = S.astype(np.float32).astype(np.float64)
+    t = torch.tensor(S32, dtype=torch.float32, device="cuda") if n else torch.zeros((0, 4), device="cuda")
+    c, a = ctx.tcm_prepare(t)
+    if n == 0:
+        assert a == 0.0
+        return
+    c_ref, a_ref = oracle.center_radius(S32)
+    assert np.allclose(c, c_ref, rtol=0, atol=1e-12 * 1000.0), (c, c_ref)
+    assert abs(a - a_ref) <= 1e-12 * a_ref, (a, a_ref)
