@@ -97,6 +97,7 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
   __shared__ double sh[32];
   __shared__ double s_part[4];   // this CTA's sums (x, y, z) and, later, its max
   __shared__ double s_c[3];
+  __shared__ double s_all[kGeomClusterCTAs][3];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const GeomJob j = gj[blockIdx.x / kGeomClusterCTAs];
@@ -130,15 +131,23 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
     s_part[2] = tz;
   }
   cluster.sync();
-  if (rank == 0 && threadIdx.x == 0) {
-    double c[3] = {0.0, 0.0, 0.0};
-    for (int r = 0; r < kGeomClusterCTAs; ++r) {  // rank order
+  if (rank == 0 && threadIdx.x < 32) {  // lanes fetch the ranks' partials in parallel
+    const int r = threadIdx.x;
+    if (r < kGeomClusterCTAs) {
       const double* p = cluster.map_shared_rank(s_part, r);
-      for (int d = 0; d < 3; ++d) c[d] += p[d];
+      s_all[r][0] = p[0];
+      s_all[r][1] = p[1];
+      s_all[r][2] = p[2];
     }
-    const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
-    const SysGeom g = geoms[j.geom];
-    for (int d = 0; d < 3; ++d) s_c[d] = j.need_center ? c[d] * inv : g.c[d];
+    __syncwarp();
+    if (threadIdx.x == 0) {
+      double c[3] = {0.0, 0.0, 0.0};
+      for (int q = 0; q < kGeomClusterCTAs; ++q)  // rank order
+        for (int d = 0; d < 3; ++d) c[d] += s_all[q][d];
+      const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
+      const SysGeom g = geoms[j.geom];
+      for (int d = 0; d < 3; ++d) s_c[d] = j.need_center ? c[d] * inv : g.c[d];
+    }
   }
   cluster.sync();
   const double* c0 = cluster.map_shared_rank(s_c, 0);
@@ -158,10 +167,11 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
   mf = (float)block_max((double)mf, sh);
   if (threadIdx.x == 0) s_part[3] = mf;
   cluster.sync();
-  if (threadIdx.x == 0) {
-    float m = 0.f;
-    for (int r = 0; r < kGeomClusterCTAs; ++r) m = fmaxf(m, (float)cluster.map_shared_rank(s_part, r)[3]);
-    s_c[0] = m;  // reuse: the cluster's float maximum, per CTA
+  if (threadIdx.x < 32) {
+    const int r = threadIdx.x;
+    double m = r < kGeomClusterCTAs ? cluster.map_shared_rank(s_part, r)[3] : 0.0;
+    m = warp_max(m);
+    if (threadIdx.x == 0) s_c[0] = m;  // reuse: the cluster's float maximum, per CTA
   }
   __syncthreads();
   const float thr = (float)s_c[0] * (1.0f - 4e-6f);
@@ -177,12 +187,18 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
   cluster.sync();  // all CTAs are done with s_part[3] and s_c before they are overwritten
   if (threadIdx.x == 0) s_part[3] = md;
   cluster.sync();
-  if (rank == 0 && threadIdx.x == 0) {
-    double m = 0.0;
-    for (int r = 0; r < kGeomClusterCTAs; ++r) m = fmax(m, cluster.map_shared_rank(s_part, r)[3]);
-    if (j.need_center)
-      for (int d = 0; d < 3; ++d) geoms[j.geom].c[d] = (d == 0 ? cx : (d == 1 ? cy : cz));
-    if (j.need_radius) geoms[j.geom].a = sqrt(m);
+  if (rank == 0 && threadIdx.x < 32) {
+    const int r = threadIdx.x;
+    double m = r < kGeomClusterCTAs ? cluster.map_shared_rank(s_part, r)[3] : 0.0;
+    m = warp_max(m);
+    if (threadIdx.x == 0) {
+      if (j.need_center) {
+        geoms[j.geom].c[0] = cx;
+        geoms[j.geom].c[1] = cy;
+        geoms[j.geom].c[2] = cz;
+      }
+      if (j.need_radius) geoms[j.geom].a = sqrt(m);
+    }
   }
   cluster.sync();  // no CTA exits while its shared memory may still be read
 }

@@ -557,7 +557,8 @@ int tcm_prepare(tcm_ctx_t c, tcm_system* s) {
   char* base = nullptr;
   TRY(upload(c, pk, &base));
   TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
-  TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
+  if (ngt > 0)  // the tiled kernels take tickets
+    TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   {
     PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches(cluster_jobs(gjobs), ngt));
@@ -612,7 +613,8 @@ int tcm_moments(tcm_ctx_t c, const tcm_system* s, const double* rot, int lmax, i
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   if (!gjobs.empty()) {
     TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
-    TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
+    if (ngt > 0)  // the tiled kernels take tickets
+      TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
     PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches(cluster_jobs(gjobs), ngt));
     TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(), cluster_jobs(gjobs),
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
@@ -866,7 +868,8 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   for (int L = 0; L <= kLmaxMax; ++L) ngroups += P.tile_begin[L + 1] > P.tile_begin[L];
   auto enqueue = [&](cudaStream_t st) -> int {
     if (!gjobs.empty()) {
-      TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), st));
+      if (ngt > 0)  // the tiled kernels take tickets
+        TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), st));
       PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches(cluster_jobs(gjobs), ngt));
       TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(), cluster_jobs(gjobs),
                              reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
@@ -961,7 +964,8 @@ int direct_items(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, int64_t 
   TRY(upload(c, pk, &base));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   if (!gjobs.empty()) {
-    TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
+    if (ngt > 0)  // the tiled kernels take tickets
+      TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
     PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches(cluster_jobs(gjobs), ngt));
     TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(), cluster_jobs(gjobs),
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
