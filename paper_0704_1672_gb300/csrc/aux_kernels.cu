@@ -92,14 +92,38 @@ __device__ __forceinline__ void two_sum_add(float& s, float& e, float x) {
   s = t;
 }
 
+// Warp sum of float-float values (s + e): each level adds the partner's pair with a two-sum,
+// so the warp total keeps about 48 bits; float instructions only (the FP64 pipe is 1/64 of
+// the FP32 one, so double reductions over 16 warps would dominate this kernel).
+__device__ __forceinline__ void warp_sum_ff(float& s, float& e) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const float e2 = __shfl_xor_sync(0xffffffffu, e, o);
+    two_sum_add(s, e, s2);
+    e += e2;
+  }
+}
+
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeomClusterThreads)
     k_geom_cluster(const GeomJob* __restrict__ gj, SysGeom* __restrict__ geoms) {
-  __shared__ double sh[32];
-  __shared__ double s_part[4];   // this CTA's sums (x, y, z) and, later, its max
+  constexpr int kWarps = kGeomClusterThreads / 32;
+  __shared__ double s_wsum[kWarps][3];
+  __shared__ float s_wmax[kWarps];
+  __shared__ double s_part[3];               // this CTA's coordinate sums
+  __shared__ float s_fmax;                   // this CTA's float maximum of |x - c|^2
+  __shared__ unsigned long long s_dmax;      // its exact double maximum over the candidates (bits)
   __shared__ double s_c[3];
-  __shared__ double s_all[kGeomClusterCTAs][3];
+  __shared__ float s_thr;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const GeomJob j = gj[blockIdx.x / kGeomClusterCTAs];
   const float4* xyzq = reinterpret_cast<const float4*>(j.xyzq);
   const long long stride = (long long)kGeomClusterCTAs * kGeomClusterThreads;
@@ -114,7 +138,8 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
     y[k] = v.y;
     z[k] = v.z;
   }
-  // pass 1: coordinate sums
+  if (threadIdx.x == 0) s_dmax = 0ull;
+  // pass 1: coordinate sums, float-float within warps, double across warps and CTAs
   float sx = 0.f, ex = 0.f, sy = 0.f, ey = 0.f, sz = 0.f, ez = 0.f;
 #pragma unroll
   for (int k = 0; k < kGeomClusterPer; ++k) {  // padding atoms add exact zeros
@@ -122,37 +147,30 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
     two_sum_add(sy, ey, y[k]);
     two_sum_add(sz, ez, z[k]);
   }
-  double tx = block_sum((double)sx + (double)ex, sh);
-  double ty = block_sum((double)sy + (double)ey, sh);
-  double tz = block_sum((double)sz + (double)ez, sh);
-  if (threadIdx.x == 0) {
-    s_part[0] = tx;
-    s_part[1] = ty;
-    s_part[2] = tz;
+  warp_sum_ff(sx, ex);
+  warp_sum_ff(sy, ey);
+  warp_sum_ff(sz, ez);
+  if (lane == 0) {
+    s_wsum[warp][0] = (double)sx + (double)ex;
+    s_wsum[warp][1] = (double)sy + (double)ey;
+    s_wsum[warp][2] = (double)sz + (double)ez;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {  // warp order
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += s_wsum[w][threadIdx.x];
+    s_part[threadIdx.x] = t;
   }
   cluster.sync();
-  if (rank == 0 && threadIdx.x < 32) {  // lanes fetch the ranks' partials in parallel
-    const int r = threadIdx.x;
-    if (r < kGeomClusterCTAs) {
-      const double* p = cluster.map_shared_rank(s_part, r);
-      s_all[r][0] = p[0];
-      s_all[r][1] = p[1];
-      s_all[r][2] = p[2];
-    }
-    __syncwarp();
-    if (threadIdx.x == 0) {
-      double c[3] = {0.0, 0.0, 0.0};
-      for (int q = 0; q < kGeomClusterCTAs; ++q)  // rank order
-        for (int d = 0; d < 3; ++d) c[d] += s_all[q][d];
-      const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
-      const SysGeom g = geoms[j.geom];
-      for (int d = 0; d < 3; ++d) s_c[d] = j.need_center ? c[d] * inv : g.c[d];
-    }
+  if (rank == 0 && threadIdx.x < 3) {  // rank order
+    double t = 0.0;
+    for (int r = 0; r < kGeomClusterCTAs; ++r) t += cluster.map_shared_rank(s_part, r)[threadIdx.x];
+    const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
+    s_c[threadIdx.x] = j.need_center ? t * inv : geoms[j.geom].c[threadIdx.x];
   }
   cluster.sync();
   const double* c0 = cluster.map_shared_rank(s_c, 0);
   const double cx = c0[0], cy = c0[1], cz = c0[2];
-  cluster.sync();  // every CTA has read the centre before CTA 0 reuses its buffers
   // pass 2: largest |x - c|^2, float filter then exact double on the candidates
   const float chx = (float)cx, chy = (float)cy, chz = (float)cz;
   const float clx = (float)(cx - (double)chx), cly = (float)(cy - (double)chy), clz = (float)(cz - (double)chz);
@@ -164,41 +182,42 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
     r2f[k] = (i0 + k * stride < j.n) ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : -1.f;
     mf = fmaxf(mf, r2f[k]);
   }
-  mf = (float)block_max((double)mf, sh);
-  if (threadIdx.x == 0) s_part[3] = mf;
-  cluster.sync();
-  if (threadIdx.x < 32) {
-    const int r = threadIdx.x;
-    double m = r < kGeomClusterCTAs ? cluster.map_shared_rank(s_part, r)[3] : 0.0;
-    m = warp_max(m);
-    if (threadIdx.x == 0) s_c[0] = m;  // reuse: the cluster's float maximum, per CTA
+  mf = warp_max_f(mf);
+  if (lane == 0) s_wmax[warp] = mf;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int w = 0; w < kWarps; ++w) m = fmaxf(m, s_wmax[w]);
+    s_fmax = m;
+  }
+  cluster.sync();  // every CTA's float maximum is in place; rank 0's centre has been read
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int r = 0; r < kGeomClusterCTAs; ++r) m = fmaxf(m, *cluster.map_shared_rank(&s_fmax, r));
+    s_thr = m * (1.0f - 4e-6f);
   }
   __syncthreads();
-  const float thr = (float)s_c[0] * (1.0f - 4e-6f);
-  double md = 0.0;
+  const float thr = s_thr;
 #pragma unroll
   for (int k = 0; k < kGeomClusterPer; ++k) {
-    if (r2f[k] >= thr) {
+    if (r2f[k] >= thr) {  // a handful of atoms: their exact squared distance, max through the bits
       const double dx = (double)x[k] - cx, dy = (double)y[k] - cy, dz = (double)z[k] - cz;
-      md = fmax(md, dx * dx + dy * dy + dz * dz);
+      atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(dx * dx + dy * dy + dz * dz));
     }
   }
-  md = block_max(md, sh);
-  cluster.sync();  // all CTAs are done with s_part[3] and s_c before they are overwritten
-  if (threadIdx.x == 0) s_part[3] = md;
-  cluster.sync();
-  if (rank == 0 && threadIdx.x < 32) {
-    const int r = threadIdx.x;
-    double m = r < kGeomClusterCTAs ? cluster.map_shared_rank(s_part, r)[3] : 0.0;
-    m = warp_max(m);
-    if (threadIdx.x == 0) {
-      if (j.need_center) {
-        geoms[j.geom].c[0] = cx;
-        geoms[j.geom].c[1] = cy;
-        geoms[j.geom].c[2] = cz;
-      }
-      if (j.need_radius) geoms[j.geom].a = sqrt(m);
+  cluster.sync();  // every CTA's candidates are in
+  if (rank == 0 && threadIdx.x == 0) {
+    unsigned long long m = 0ull;
+    for (int r = 0; r < kGeomClusterCTAs; ++r) {
+      const unsigned long long v = *cluster.map_shared_rank(&s_dmax, r);
+      m = v > m ? v : m;  // non-negative doubles order like their bit patterns
     }
+    if (j.need_center) {
+      geoms[j.geom].c[0] = cx;
+      geoms[j.geom].c[1] = cy;
+      geoms[j.geom].c[2] = cz;
+    }
+    if (j.need_radius) geoms[j.geom].a = sqrt(__longlong_as_double((long long)m));
   }
   cluster.sync();  // no CTA exits while its shared memory may still be read
 }
