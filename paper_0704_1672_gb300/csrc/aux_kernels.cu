@@ -348,6 +348,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const MomJob* __r
                                                                const int* __restrict__ imap,
                                                                const double* __restrict__ fmap,
                                                                const int* __restrict__ imap_off, int kmax) {
+  pdl_wait();  // the moment kernels' partial rows are complete
   const MomJob& job = jobs[blockIdx.x];
   const int L = job.L;
   const int tpc = job.tiles_per_chunk;
@@ -617,6 +618,7 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
   __shared__ double sh[(kGrad ? 9 : 1) * 32];
   __shared__ double g_cb, g_ch, g_sh, g_iR;
   __shared__ Euler g_eb;
+  pdl_wait();  // the moments (and centres and radii) of the launches before are complete
   const PairDesc d = items[blockIdx.x];
   const int L = d.L;
   const double x = d.R0[0], y = d.R0[1], z = d.R0[2];
@@ -973,8 +975,10 @@ int geom_launches(int n_cluster_jobs, int n_gtiles) {
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms, const int* imap,
                     const double* fmap, const int* imap_off, int kmax, cudaStream_t s) {
   if (n_jobs <= 0) return 0;
-  k_finalize<<<n_jobs, kFinalizeThreads, 0, s>>>(jobs, partials, geoms, imap, fmap, imap_off, kmax);
-  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+  return launch_pdl(k_finalize, dim3(n_jobs), dim3(kFinalizeThreads), 0, s, jobs, partials, geoms, imap, fmap,
+                    imap_off, kmax) == cudaSuccess
+             ? 0
+             : -1;
 }
 
 int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const MomJob* jobs, const SysGeom* geoms,
@@ -986,12 +990,16 @@ int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const Mo
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return -1;
-    k_contract<true><<<n_items, nt, smem, s>>>(items, jobs, geoms, ztab, rots, E, status, G);
+    if (launch_pdl(k_contract<true>, dim3(n_items), dim3(nt), smem, s, items, jobs, geoms, ztab, rots, E, status, G) !=
+        cudaSuccess)
+      return -1;
   } else {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return -1;
-    k_contract<false><<<n_items, nt, smem, s>>>(items, jobs, geoms, ztab, rots, E, status, nullptr);
+    if (launch_pdl(k_contract<false>, dim3(n_items), dim3(nt), smem, s, items, jobs, geoms, ztab, rots, E, status,
+                   (double*)nullptr) != cudaSuccess)
+      return -1;
   }
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }

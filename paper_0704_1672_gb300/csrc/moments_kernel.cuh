@@ -478,7 +478,8 @@ __device__ __forceinline__ void run_tile(const MomTile& tile, const MomJob* __re
 }
 
 // Persistent kernel: every warp pulls warp tiles from the shared counter until none are
-// left, so warps never wait for each other.
+// left, so warps never wait for each other.  counter[0] is the work counter and counter[32]
+// the exit ticket, both zero on entry and left zero on exit.
 template <typename T, int L>
 __global__ void __launch_bounds__(kThreads, TCM_MOMENT_CTAS_PER_SM)
     k_moments(const MomJob* __restrict__ jobs, const MomTile* __restrict__ tiles, int n_tiles,
@@ -487,13 +488,19 @@ __global__ void __launch_bounds__(kThreads, TCM_MOMENT_CTAS_PER_SM)
   __shared__ Xform<T> s_xf[kThreads / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* wb = reinterpret_cast<T*>(smem) + warp * (Plan<T, L>::max_nacc() * MomTraits<T>::stride);
+  pdl_wait();  // the centres and radii of the launch before are complete
   for (;;) {
     int ti = 0;
     if (lane == 0) ti = atomicAdd(counter, 1);
     ti = __shfl_sync(0xffffffffu, ti, 0);
-    if (ti >= n_tiles) return;
+    if (ti >= n_tiles) break;
     const MomTile tile = tiles[ti];
     run_tile<T, L, 0>(tile, jobs, geoms, partials, wb, &s_xf[warp]);
+  }
+  // the last warp out leaves the work counter and its own ticket at zero for the next launch
+  if (lane == 0 && atomicAdd(counter + 32, 1) == (int)(gridDim.x * (kThreads / 32)) - 1) {
+    atomicExch(counter, 0);
+    atomicExch(counter + 32, 0);
   }
 }
 
@@ -505,8 +512,10 @@ int launch_moments_t(const MomJob* jobs, const MomTile* tiles, int n_tiles, int*
     if (cudaFuncSetAttribute(k_moments<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return -1;
   }
-  k_moments<T, L><<<grid, kThreads, smem, s>>>(jobs, tiles, n_tiles, counter, geoms, partials);
-  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+  return launch_pdl(k_moments<T, L>, dim3(grid), dim3(kThreads), smem, s, jobs, tiles, n_tiles, counter, geoms,
+                    partials) == cudaSuccess
+             ? 0
+             : -1;
 }
 
 }  // namespace tcm

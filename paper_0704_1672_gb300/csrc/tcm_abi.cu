@@ -280,9 +280,15 @@ void build_tiles(int precision, Plan& P) {
 }
 
 // Queue the moment pass (step a2/a3) for every job of the plan.
+// The moment kernels' work counters and exit tickets (counters[L], counters[32 + L]) are zero
+// on entry and left zero by every launch, so they are cleared once, when allocated.
 int ensure_moment_buffers(tcm_ctx* c, int precision, const Plan& P) {
   TRY(dev_ensure(c, c->partials, (size_t)std::max(P.n_tile_ids, 1) * moments_kmax(precision) * sizeof(double)));
+  void* before = c->counters.p;
   TRY(dev_ensure(c, c->counters, 64 * sizeof(int)));
+  if (c->counters.p != before) {
+    TRY_CUDA(cudaMemsetAsync(c->counters.p, 0, 64 * sizeof(int), c->stream));
+  }
   return TCM_OK;
 }
 
@@ -290,7 +296,6 @@ int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, 
                 const SysGeom* d_geoms, cudaStream_t st) {
   const int kmax = moments_kmax(precision);
   TRY(ensure_moment_buffers(c, precision, P));
-  TRY_CUDA(cudaMemsetAsync(c->counters.p, 0, 64 * sizeof(int), st));
   int* counters = static_cast<int*>(c->counters.p);
   double* parts = static_cast<double*>(c->partials.p);
   int ngroups = 0;

@@ -177,11 +177,38 @@ constexpr int kGeomClusterThreads = 512;
 constexpr int kGeomClusterPer = 8;      // atoms per thread, held in registers
 constexpr long long kGeomClusterAtoms = (long long)kGeomClusterCTAs * kGeomClusterThreads * kGeomClusterPer;
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization
+// is set up while its predecessor drains; pdl_wait() blocks until the predecessor grid has
+// completed and its memory is visible (a no-op for an ordinary launch).  pdl_trigger() would
+// let the next kernel be scheduled before this one ends; the kernels do not call it, because
+// dependent CTAs resident early slowed the replayed step down (0.372 ms against 0.325 ms).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// Launch with programmatic stream serialization (programmatic dependent launch): the kernel
+// may be scheduled while the previous kernel on the stream drains, and must call
+// griddepcontrol.wait before it reads that kernel's results.
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 // ---------------------------------------------------------------------------------
 // Launchers (defined in the .cu files).
 
 // Moment kernels: one persistent launch over `n_tiles` tiles of Lmax L.
-// precision: TCM_MIXED (float kernels) or TCM_FP64 (double kernels).
+// precision: TCM_MIXED (float kernels) or TCM_FP64 (double kernels).  counter[0] and
+// counter[32] must be zero on entry; the launch leaves them zero.
 int launch_moments(int precision, int L, const MomJob* jobs, const MomTile* tiles, int n_tiles,
                    int* counter, const SysGeom* geoms, double* partials, int grid, cudaStream_t s);
 int moments_smem_bytes(int precision, int L);

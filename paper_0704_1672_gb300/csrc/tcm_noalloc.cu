@@ -163,7 +163,7 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   if (!known && launch_geom(reinterpret_cast<GeomJob*>(base + kOffGJob), 1, gj.n_tiles == 0 ? 1 : 0,
                             reinterpret_cast<GeomTile*>(base + kOffGTiles),
                             gj.n_tiles, reinterpret_cast<double*>(base + kOffGPart),
-                            reinterpret_cast<int*>(base + kOffCounters) + 32, d_geom, st) != 0)
+                            reinterpret_cast<int*>(base + kOffCounters) + 40, d_geom, st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: centre/radius launch failed");
   int num_sms = 0;
   if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
