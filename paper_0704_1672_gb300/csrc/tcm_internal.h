@@ -179,11 +179,10 @@ constexpr long long kGeomClusterAtoms = (long long)kGeomClusterCTAs * kGeomClust
 
 // Programmatic dependent launch: a kernel launched with programmatic stream serialization
 // is set up while its predecessor drains; pdl_wait() blocks until the predecessor grid has
-// completed and its memory is visible (a no-op for an ordinary launch).  pdl_trigger() would
-// let the next kernel be scheduled before this one ends; the kernels do not call it, because
-// dependent CTAs resident early slowed the replayed step down (0.372 ms against 0.325 ms).
+// completed and its memory is visible (a no-op for an ordinary launch).  No kernel issues
+// griddepcontrol.launch_dependents: dependent CTAs made resident before the moment kernel's
+// tail had drained slowed the replayed step down (0.372 ms against 0.325 ms).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
 // Launch with programmatic stream serialization (programmatic dependent launch): the kernel
 // may be scheduled while the previous kernel on the stream drains, and must call
