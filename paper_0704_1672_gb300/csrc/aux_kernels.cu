@@ -114,12 +114,13 @@ __device__ __forceinline__ float warp_max_f(float v) {
 __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeomClusterThreads)
     k_geom_cluster(const GeomJob* __restrict__ gj, SysGeom* __restrict__ geoms) {
   constexpr int kWarps = kGeomClusterThreads / 32;
-  __shared__ double s_wsum[kWarps][3];
+  __shared__ float2 s_wsum[3][kWarps];       // warp sums as float-float pairs (value, error)
   __shared__ float s_wmax[kWarps];
   __shared__ double s_part[3];               // this CTA's coordinate sums
   __shared__ float s_fmax;                   // this CTA's float maximum of |x - c|^2
   __shared__ unsigned long long s_dmax;      // its exact double maximum over the candidates (bits)
-  __shared__ double s_c[3];
+  __shared__ double s_c[3];                  // the centre (rank 0)
+  __shared__ float2 s_cf[3];                 // and its split c = hi + lo into floats
   __shared__ float s_thr;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -139,7 +140,7 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
     z[k] = v.z;
   }
   if (threadIdx.x == 0) s_dmax = 0ull;
-  // pass 1: coordinate sums, float-float within warps, double across warps and CTAs
+  // pass 1: coordinate sums, float-float within the CTA, double across the CTAs
   float sx = 0.f, ex = 0.f, sy = 0.f, ey = 0.f, sz = 0.f, ez = 0.f;
 #pragma unroll
   for (int k = 0; k < kGeomClusterPer; ++k) {  // padding atoms add exact zeros
@@ -151,29 +152,35 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
   warp_sum_ff(sy, ey);
   warp_sum_ff(sz, ez);
   if (lane == 0) {
-    s_wsum[warp][0] = (double)sx + (double)ex;
-    s_wsum[warp][1] = (double)sy + (double)ey;
-    s_wsum[warp][2] = (double)sz + (double)ez;
+    s_wsum[0][warp] = make_float2(sx, ex);
+    s_wsum[1][warp] = make_float2(sy, ey);
+    s_wsum[2][warp] = make_float2(sz, ez);
   }
   __syncthreads();
-  if (threadIdx.x < 3) {  // warp order
-    double t = 0.0;
-    for (int w = 0; w < kWarps; ++w) t += s_wsum[w][threadIdx.x];
-    s_part[threadIdx.x] = t;
+  if (threadIdx.x < 3) {  // warp order, float-float; one conversion to double per CTA
+    float t = 0.f, te = 0.f;
+    for (int w = 0; w < kWarps; ++w) {
+      const float2 v = s_wsum[threadIdx.x][w];
+      two_sum_add(t, te, v.x);
+      te += v.y;
+    }
+    s_part[threadIdx.x] = (double)t + (double)te;
   }
   cluster.sync();
   if (rank == 0 && threadIdx.x < 3) {  // rank order
     double t = 0.0;
     for (int r = 0; r < kGeomClusterCTAs; ++r) t += cluster.map_shared_rank(s_part, r)[threadIdx.x];
     const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
-    s_c[threadIdx.x] = j.need_center ? t * inv : geoms[j.geom].c[threadIdx.x];
+    const double c = j.need_center ? t * inv : geoms[j.geom].c[threadIdx.x];
+    const float hi = (float)c;
+    s_c[threadIdx.x] = c;
+    s_cf[threadIdx.x] = make_float2(hi, (float)(c - (double)hi));
   }
   cluster.sync();
-  const double* c0 = cluster.map_shared_rank(s_c, 0);
-  const double cx = c0[0], cy = c0[1], cz = c0[2];
   // pass 2: largest |x - c|^2, float filter then exact double on the candidates
-  const float chx = (float)cx, chy = (float)cy, chz = (float)cz;
-  const float clx = (float)(cx - (double)chx), cly = (float)(cy - (double)chy), clz = (float)(cz - (double)chz);
+  const float2* cf0 = cluster.map_shared_rank(s_cf, 0);
+  const float2 fx = cf0[0], fy = cf0[1], fz = cf0[2];
+  const float chx = fx.x, chy = fy.x, chz = fz.x, clx = fx.y, cly = fy.y, clz = fz.y;
   float r2f[kGeomClusterPer];
   float mf = 0.f;
 #pragma unroll
@@ -198,6 +205,8 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
   }
   __syncthreads();
   const float thr = s_thr;
+  const double* c0 = cluster.map_shared_rank(s_c, 0);
+  const double cx = c0[0], cy = c0[1], cz = c0[2];
 #pragma unroll
   for (int k = 0; k < kGeomClusterPer; ++k) {
     if (r2f[k] >= thr) {  // a handful of atoms: their exact squared distance, max through the bits
@@ -616,22 +625,12 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
   const double* rtab = ztab + ((kZ_TOTAL + 3) / 4 * 4);  // recursion coefficients, 4 doubles per (l, a, b)
   extern __shared__ double2 sm2[];
   __shared__ double sh[(kGrad ? 9 : 1) * 32];
-  __shared__ double g_cb, g_ch, g_sh, g_iR;
+  __shared__ double g_cb, g_ch, g_sh, g_iR, g_ca, g_sa;
+  __shared__ int g_conv;
   __shared__ Euler g_eb;
   pdl_wait();  // the moments (and centres and radii) of the launches before are complete
   const PairDesc d = items[blockIdx.x];
   const int L = d.L;
-  const double x = d.R0[0], y = d.R0[1], z = d.R0[2];
-  const double R = sqrt(x * x + y * y + z * z);
-  const double aA = geoms[d.geomA].a, aB = geoms[d.geomB].a;
-  if (!(R > aA + aB)) {  // Eq. (mainCond) violated: the expansion does not converge
-    if (threadIdx.x == 0) {
-      E[blockIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
-      if (status) status[blockIdx.x] = TCM_ENOTCONV;
-    }
-    if (kGrad && threadIdx.x < 9) G[9LL * blockIdx.x + threadIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
-    return;
-  }
   const int nq = (L + 1) * (L + 2) / 2;
   double2* qa = sm2;           // lab frame, then reused
   double2* qb = qa + nq;
@@ -647,9 +646,14 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
   const double* pa = jobs[d.jobA].out;
   const double* pb = jobs[d.jobB].out;
   const int bmode = d.b_mode;
-  // geometry of the frame; half angles without cancellation
+  // Geometry of the frame, once per CTA (every FP64 instruction costs the whole warp's slot on
+  // the FP64 pipe): the convergence test, 1/R, cos b and the half angles without cancellation,
+  // and e^{i alpha} of R0's azimuth.
   if (threadIdx.x == 0) {
+    const double x = d.R0[0], y = d.R0[1], z = d.R0[2];
     const double rho2 = x * x + y * y;
+    const double R = sqrt(rho2 + z * z);
+    g_conv = R > geoms[d.geomA].a + geoms[d.geomB].a;  // Eq. (mainCond)
     double opc, omc;  // 1 + cos b, 1 - cos b
     if (z >= 0.0) {
       opc = (R + z) / R;
@@ -662,6 +666,9 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     g_ch = sqrt(0.5 * opc);
     g_sh = sqrt(0.5 * omc);
     g_iR = 1.0 / R;
+    const double rho = sqrt(rho2);
+    g_ca = rho > 0.0 ? x / rho : 1.0;
+    g_sa = rho > 0.0 ? y / rho : 0.0;
   } else if (threadIdx.x == 32 && bmode == kBRotate) {
     g_eb = euler_zyz(rots + 9LL * d.rot);
   }
@@ -672,10 +679,16 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     qb[k] = m == 0 ? make_double2(pb[l * l], 0.0) : make_double2(pb[l * l + 2 * m - 1], pb[l * l + 2 * m]);
   }
   __syncthreads();
+  if (!g_conv) {  // the expansion does not converge: NaN and a status instead of an energy
+    if (threadIdx.x == 0) {
+      E[blockIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
+      if (status) status[blockIdx.x] = TCM_ENOTCONV;
+    }
+    if (kGrad && threadIdx.x < 9) G[9LL * blockIdx.x + threadIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
+    return;
+  }
   {  // e^{-i m alpha}, the half-angle powers and R^-(k+1), every thread a share
-    const double rho = sqrt(x * x + y * y);
-    const double ca = rho > 0.0 ? x / rho : 1.0, sa = rho > 0.0 ? y / rho : 0.0;
-    phase_powers(ph, make_double2(ca, sa), L);
+    phase_powers(ph, make_double2(g_ca, g_sa), L);
     half_angle_powers(cp, sp, g_ch, g_sh, L);
     for (int k = threadIdx.x; k <= 2 * L + 1; k += blockDim.x) rp[k] = rpow(g_iR, k + 1);
     if (bmode == kBRotate) {
@@ -714,12 +727,19 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     rotate_d(qb, rb, D, L, ztab, phg, true);
   }
   __syncthreads();
-  // z-axis contraction: one thread per (l1, l2)
+  // z-axis contraction: one thread per (l1, l2).  The pairs are taken in shells of equal
+  // s = min(l1, l2), s = L first: the (L - s)^2 pairs before shell s are those of the larger
+  // shells, and shell s lists (s, s), (s, s+1), (s+1, s), (s, s+2), ...  Neighbouring lanes then
+  // run the m loops (s terms) to nearly the same length.
   double acc = 0.0;
   double gx = 0.0, gy = 0.0, gz = 0.0, tbx = 0.0, tby = 0.0, tbz = 0.0, tax = 0.0, tay = 0.0;
   for (int p = threadIdx.x; p < (L + 1) * (L + 1); p += blockDim.x) {
-    const int l1 = p / (L + 1);
-    const int l2 = p - l1 * (L + 1);
+    int u = (int)sqrtf((float)p);  // u = L - s = floor(sqrt(p))
+    while (u * u > p) --u;
+    while ((u + 1) * (u + 1) <= p) ++u;
+    const int sh_s = L - u, j = p - u * u;
+    const int l1 = (j & 1) ? sh_s : sh_s + (j >> 1);
+    const int l2 = (j & 1) ? sh_s + ((j + 1) >> 1) : sh_s;
     const double2* a = ra + l1 * (l1 + 1) / 2;
     const double2* b = rb + l2 * (l2 + 1) / 2;
     const int mm = l1 < l2 ? l1 : l2;
