@@ -394,26 +394,39 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const MomJob* __r
 // (real charges: Q_l,-m = (-1)^m conj(Q_lm)).  Moments enter in the rotated frame: those of B
 // either come from the moment kernels with W folded into the atom transform (mode kBInFrame),
 // or, like those of A, are rotated here (kBLab by W; kBRotate by W rotB from a moment cache):
-//   Q'_lm = sum_m' e^{-i m' alpha} d^l_{m'm}(beta) Q_lm'
-// with the Wigner d^l_{ab}, a >= |b|, from the three-term recursion in l started at
-//   d^a_{ab} = (-1)^{a-b} sqrt(C(2a, a+b)) cos^{a+b}(beta/2) sin^{a-b}(beta/2),
-// the other entries by d_{m'm} = (-1)^{m-m'} d_{mm'} = d_{-m,-m'}.  O(L^3) work per energy.
+//   Q'_lm = sum_m' d^l_{m'm}(beta) P_lm',  P_lm' = e^{-i m' alpha} Q_lm'.
+// The Wigner matrix d^l(beta) is never formed.  A rotation about y is a rotation about z
+// between two rotations by pi/2 about x, which for the constant matrices D^l = d^l(pi/2) gives
+//   d^l_{m'm}(beta) = i^(m-m') sum_k D^l_{km'} D^l_{km} e^{i k beta},
+// so Q' follows from two products with D^l around a diagonal phase:
+//   p_k = sum_m' D^l_{km'} v_m',  v_m' = (-i)^m' P_lm';   Q'_lm = i^m sum_k D^l_{km} e^{i k beta} p_k.
+// For real charges v_-m' = (-1)^m' conj(v_m') and p_-k = (-1)^k conj(p_k); with
+// D^l_{k,-m'} = (-1)^(l+k) D^l_{km'} and D^l_{km} = (-1)^(k-m) D^l_{mk} the terms of m' and -m'
+// (and of k and -k) combine into one real product, which leaves, for k, m >= 0,
+//   Re p_k = sum_{m' = l+k (mod 2)} D^l_{km'} Re v~_m',   Im p_k = sum_{other m'} D^l_{km'} Im v~_m',
+//   S_m = (-1)^l [sum_{k = l+m (mod 2)} D^l_{mk} Re p~_k - i sum_{other k} D^l_{mk} Im p~_k],  Q'_lm = i^m S_m,
+// with v~_m' = v_m' and p~_k = e^{i k beta} p_k, both doubled for indices >= 1: (l+1)^2 real
+// multiply-adds per product and degree, no table of d^l(beta) per energy.
 constexpr int kContractThreads = 256;
 
-// Offsets of the per-(l, a) tables in ztab (doubles), each [kLmaxMax+1][kLmaxMax+1].
+// Layout of ztab (doubles): k! for k < 2 kZN, 1/sqrt((l+m)!(l-m)!) at [l][m], and the rows of
+// D^l = d^l(pi/2): D^l_{km}, 0 <= k, m <= l, at kZ_DPI2 + dpi2_off(l) + k (l + 1) + m.
 constexpr int kZN = kLmaxMax + 1;
-constexpr int kZ_K1 = 0;                 // l(2l-1) / sqrt(l^2 - a^2)        (a < l)
-constexpr int kZ_IRS = kZ_K1 + kZN * kZN;  // 1 / sqrt(l^2 - b^2)              (b < l)
-constexpr int kZ_K2 = kZ_IRS + kZN * kZN;  // sqrt((l-1)^2 - a^2) / ((l-1)(2l-1)) (l >= 2)
-constexpr int kZ_RS1 = kZ_K2 + kZN * kZN;  // sqrt((l-1)^2 - b^2)              (l >= 1)
-constexpr int kZ_ILL = kZ_RS1 + kZN * kZN; // 1 / (l (l-1))                    (l >= 2)
-constexpr int kZ_SQC = kZ_ILL + kZN;       // sqrt(C(2a, a+b)), [kZN][2 kZN]
-constexpr int kZ_FACT = kZ_SQC + kZN * 2 * kZN;  // k!, k <= 2 kLmaxMax
-constexpr int kZ_ISF = kZ_FACT + 2 * kZN;  // 1 / sqrt((l+m)! (l-m)!)
-constexpr int kZ_TOTAL = kZ_ISF + kZN * kZN;
+constexpr int kZ_FACT = 0;
+constexpr int kZ_ISF = kZ_FACT + 2 * kZN;
+constexpr int kZ_DPI2 = kZ_ISF + kZN * kZN;
+__host__ __device__ constexpr int dpi2_off(int l) { return l * (l + 1) * (2 * l + 1) / 6; }
+constexpr int kZ_TOTAL = kZ_DPI2 + dpi2_off(kZN);
 
 __device__ __forceinline__ double flip(double x, int odd) {  // (-1)^odd x without an FP64 op
   return __longlong_as_double(__double_as_longlong(x) ^ ((long long)(odd & 1) << 63));
+}
+
+// i^n z for any integer n, by exchanging and negating the parts (no FP64 operation).
+__device__ __forceinline__ double2 mul_ipow(double2 z, int n) {
+  const int r = n & 3;
+  const double2 s = (r & 1) ? make_double2(z.y, z.x) : z;
+  return make_double2(flip(s.x, r == 1 || r == 2), flip(s.y, r >= 2));
 }
 
 __device__ __forceinline__ int tri_l(int k) {  // l with l(l+1)/2 <= k < (l+1)(l+2)/2
@@ -423,88 +436,26 @@ __device__ __forceinline__ int tri_l(int k) {  // l with l(l+1)/2 <= k < (l+1)(l
   return l;
 }
 
-// d^l_{m'm} for m >= 0 from the half table D (entries a >= |b|, D[off(l) + a*a + a + b]).
-__device__ __forceinline__ double dget(const double* D, int offl, int mp, int m) {
-  if (mp <= m && -mp <= m) return flip(D[offl + m * m + m + mp], m - mp);
-  if (mp > m) return D[offl + mp * mp + mp + m];
-  return flip(D[offl + mp * mp - mp - m], m - mp);  // a = -mp, b = -m
+// Row product with a parity split: (sum over j = par (mod 2) of row[j] Re x_j, sum over the other
+// j of row[j] Im x_j), j = 0..l.  One multiply-add per entry.
+__device__ __forceinline__ double2 row_split(const double* row, const double2* x, int l, int par) {
+  const double* xs = reinterpret_cast<const double*>(x);
+  double a = 0.0, b = 0.0;  // even j, odd j
+  int j = 0;
+  for (; j + 1 <= l; j += 2) {
+    a = fma(row[j], xs[2 * j + par], a);
+    b = fma(row[j + 1], xs[2 * j + 3 - par], b);
+  }
+  if (j == l) a = fma(row[j], xs[2 * j + par], a);
+  return par ? make_double2(b, a) : make_double2(a, b);
 }
 
-// Rotate moments already multiplied by e^{-i m alpha} (m >= 0, complex in qin) by R_y(-beta)
-// with the half table D of beta; optionally multiply the result by phg[m] = e^{-i m gamma}
-// (the last factor of R_z(-gamma) R_y(-beta) R_z(-alpha)) and normalise to Qhat.  Threads
-// stride over (l, m).
-__device__ void rotate_d(const double2* qin, double2* qout, const double* D, int L, const double* ztab,
-                         const double2* phg, bool hat) {
-  const int nq = (L + 1) * (L + 2) / 2;
-  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
-    const int l = tri_l(k);
-    const int m = k - l * (l + 1) / 2;
-    const int offl = l * (l + 1) * (2 * l + 1) / 6;
-    const double2* q = qin + l * (l + 1) / 2;
-    double re = dget(D, offl, 0, m) * q[0].x;
-    double im = 0.0;
-    for (int mp = 1; mp <= l; ++mp) {
-      const double d1 = dget(D, offl, mp, m);
-      const double d2 = flip(dget(D, offl, -mp, m), mp);
-      re = fma(d1 + d2, q[mp].x, re);
-      im = fma(d1 - d2, q[mp].y, im);
-    }
-    if (hat) {
-      const double f = ztab[kZ_ISF + l * kZN + m];
-      re *= f;
-      im *= f;
-    }
-    if (phg && m > 0) {
-      const double2 e = phg[m];
-      const double r2 = e.x * re - e.y * im;
-      im = e.x * im + e.y * re;
-      re = r2;
-    }
-    qout[k] = make_double2(re, im);
-  }
-}
-
-// Wigner d^l_{ab}(beta), a >= |b|, l <= L: one thread per (a, b) walks l upward from the seed
-//   d^a_{ab} = (-1)^(a-b) sqrt(C(2a, a+b)) cos^(a+b)(beta/2) sin^(a-b)(beta/2);
-// the step d_l = A (t d_l-1 - B d_l-2), t = cos(beta) - ab / (l (l-1)), uses per-(l, a, b)
-// coefficients (A, A ab / (l (l-1)), A B) from rtab.  cp/sp hold the powers of cos/sin(beta/2).
-__device__ void wigner_half_table(double* D, const double* cp, const double* sp, double cb, int L,
-                                  const double* ztab, const double* rtab) {
-  for (int p = threadIdx.x; p < (L + 1) * (L + 1); p += blockDim.x) {
-    int a = (int)sqrtf((float)p);
-    while (a * a > p) --a;
-    while ((a + 1) * (a + 1) <= p) ++a;
-    const int b = p - a * a - a;
-    double d1 = flip(ztab[kZ_SQC + a * 2 * kZN + a + b] * cp[a + b] * sp[a - b], a - b);
-    double d2 = 0.0;
-    D[a * (a + 1) * (2 * a + 1) / 6 + a * a + a + b] = d1;
-    // the coefficients of step l + 1 are loaded while step l is computed
-    int e = (a + 1) * (a + 2) * (2 * a + 3) / 6 + a * a + a + b;
-    double2 c01 = make_double2(0.0, 0.0);
-    double c2 = 0.0;
-    if (a < L) {
-      c01 = __ldg(reinterpret_cast<const double2*>(rtab) + 2 * e);
-      c2 = __ldg(rtab + 4 * e + 2);
-    }
-    for (int l = a + 1; l <= L; ++l) {
-      const int en = e + (l + 1) * (l + 1);  // index of (l + 1, a, b)
-      double2 n01 = c01;
-      double n2 = c2;
-      if (l < L) {
-        n01 = __ldg(reinterpret_cast<const double2*>(rtab) + 2 * en);
-        n2 = __ldg(rtab + 4 * en + 2);
-      }
-      const double At = fma(c01.x, cb, -c01.y);
-      const double v = fma(At, d1, -(c2 * d2));
-      D[e] = v;
-      d2 = d1;
-      d1 = v;
-      e = en;
-      c01 = n01;
-      c2 = n2;
-    }
-  }
+// Copies the rows of D^l for l <= L into shared memory (a constant table: no dependence on the
+// kernels before, so it is read ahead of griddepcontrol.wait).
+__device__ void load_dpi2(double* Ds, const double* __restrict__ ztab, int L) {
+  const double* src = ztab + kZ_DPI2;
+  const int n = dpi2_off(L + 1);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) Ds[i] = __ldg(src + i);
 }
 
 // Euler angles of a rotation M = R_z(-gamma) R_y(-beta) R_z(-alpha), beta in [0, pi], through
@@ -546,7 +497,9 @@ __device__ Euler euler_zyz(const double* M) {
   return e;
 }
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b);
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
 
 // x^n and z^n by binary powering (n >= 0): O(log n) multiplications, so every entry of a
 // power table is computed by its own thread instead of along one serial chain.
@@ -569,20 +522,44 @@ __device__ __forceinline__ double2 cpow(double2 z, int n) {
   return r;
 }
 
-// ph[m] = conj(e)^m (m <= L), cp[k] = ch^k, sp[k] = sh^k (k <= 2L), all threads of the block.
-__device__ void phase_powers(double2* ph, double2 e, int L) {
-  const double2 c = make_double2(e.x, -e.y);
-  for (int m = threadIdx.x; m <= L; m += blockDim.x) ph[m] = cpow(c, m);
+// The phase factors of one rotation R_z(-gamma) R_y(-beta) R_z(-alpha):
+//   in:   (-i)^m e^{-i m alpha}, doubled for m >= 1       (from e^{i alpha})
+//   beta: e^{i k beta}, doubled for k >= 1                (from cos beta, sin beta)
+//   out:  i^m e^{-i m gamma}                              (from e^{i gamma})
+__device__ __forceinline__ double2 in_phase(double2 e, int m) {
+  const double2 z = mul_ipow(cpow(make_double2(e.x, -e.y), m), -m);
+  return m > 0 ? make_double2(2.0 * z.x, 2.0 * z.y) : z;
 }
-__device__ void half_angle_powers(double* cp, double* sp, double ch, double sh, int L) {
-  for (int k = threadIdx.x; k <= 2 * L; k += blockDim.x) {
-    cp[k] = rpow(ch, k);
-    sp[k] = rpow(sh, k);
-  }
+__device__ __forceinline__ double2 beta_phase(double cb, double sb, int k) {
+  const double2 z = cpow(make_double2(cb, sb), k);
+  return k > 0 ? make_double2(2.0 * z.x, 2.0 * z.y) : z;
+}
+__device__ __forceinline__ double2 out_phase(double2 e, int m) {
+  return mul_ipow(cpow(make_double2(e.x, -e.y), m), m);
 }
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+// First product of a rotation, item k = (l, kk) of the triangle: p~_kk from v~ (the moments
+// times the input phases) of degree l.
+__device__ __forceinline__ double2 rot_first(const double* Ds, const double2* v, const double2* eb, int k) {
+  const int l = tri_l(k);
+  const int kk = k - l * (l + 1) / 2;
+  const double2 p = row_split(Ds + dpi2_off(l) + kk * (l + 1), v + l * (l + 1) / 2, l, (l + kk) & 1);
+  return cmul(eb[kk], p);
+}
+// Second product, item k = (l, m): S_m, times the output phase (i^m when there is no gamma) and,
+// with hat, 1/sqrt((l+m)!(l-m)!).
+__device__ __forceinline__ double2 rot_second(const double* Ds, const double2* p, const double2* phout,
+                                              const double* ztab, bool hat, int k) {
+  const int l = tri_l(k);
+  const int m = k - l * (l + 1) / 2;
+  const double2 a = row_split(Ds + dpi2_off(l) + m * (l + 1), p + l * (l + 1) / 2, l, (l + m) & 1);
+  const double2 S = make_double2(flip(a.x, l), flip(a.y, l + 1));
+  double2 q = phout ? cmul(phout[m], S) : mul_ipow(S, m);
+  if (hat) {
+    const double f = ztab[kZ_ISF + l * kZN + m];
+    q = make_double2(q.x * f, q.y * f);
+  }
+  return q;
 }
 
 // Sum of N values over the block; thread 0 gets the totals in v.  sh holds N * 32 doubles.
@@ -622,33 +599,34 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
                                                                const double* __restrict__ rots,
                                                                double* __restrict__ E, int32_t* __restrict__ status,
                                                                double* __restrict__ G) {
-  const double* rtab = ztab + ((kZ_TOTAL + 3) / 4 * 4);  // recursion coefficients, 4 doubles per (l, a, b)
   extern __shared__ double2 sm2[];
   __shared__ double sh[(kGrad ? 9 : 1) * 32];
-  __shared__ double g_cb, g_ch, g_sh, g_iR, g_ca, g_sa;
+  __shared__ double g_cb, g_sb, g_iR, g_ca, g_sa;
   __shared__ int g_conv;
   __shared__ Euler g_eb;
-  pdl_wait();  // the moments (and centres and radii) of the launches before are complete
-  const PairDesc d = items[blockIdx.x];
+  const PairDesc d = items[blockIdx.x];  // descriptors and tables precede the kernels before
   const int L = d.L;
   const int nq = (L + 1) * (L + 2) / 2;
-  double2* qa = sm2;           // lab frame, then reused
-  double2* qb = qa + nq;
-  double2* ra = qb + nq;       // Qhat' of A
-  double2* rb = ra + nq;       // Qhat' of B
-  double2* ph = rb + nq;       // e^{-i m alpha}, m <= L
-  double2* pha = ph + (L + 1); // B's own rotation (mode TCM_B_ROTATE): e^{-i m alpha_B}
-  double2* phg = pha + (L + 1);//                                      e^{-i m gamma_B}
-  double* cp = reinterpret_cast<double*>(phg + (L + 1));  // cos^k(beta/2), k <= 2L
-  double* sp = cp + 2 * L + 1;                             // sin^k(beta/2)
-  double* rp = sp + 2 * L + 1;                             // R^-(k+1), k <= 2L + 1
-  double* D = rp + 2 * L + 2;                              // half Wigner table, sum (l+1)^2 entries
+  const int n1 = L + 1;
+  double2* qa = sm2;            // A: lab frame, v~, then Qhat' in the frame
+  double2* qb = qa + nq;        // B: the same (or its frame moments, mode kBInFrame)
+  double2* ta = qb + nq;        // p~ of A
+  double2* tb = ta + nq;        // p~ of B
+  double2* ph = tb + nq;        // input phases of W (alpha of R0)
+  double2* eb = ph + n1;        // beta phases of W
+  double2* pha = eb + n1;       // mode kBRotate: input, beta and output phases of W rotB
+  double2* ebB = pha + n1;
+  double2* phg = ebB + n1;
+  double* rp = reinterpret_cast<double*>(phg + n1);  // R^-(k+1), k <= 2L + 1
+  double* Ds = rp + 2 * L + 2;                        // rows of D^l, l <= L
+  load_dpi2(Ds, ztab, L);
+  pdl_wait();  // the moments (and centres and radii) of the launches before are complete
   const double* pa = jobs[d.jobA].out;
   const double* pb = jobs[d.jobB].out;
   const int bmode = d.b_mode;
   // Geometry of the frame, once per CTA (every FP64 instruction costs the whole warp's slot on
-  // the FP64 pipe): the convergence test, 1/R, cos b and the half angles without cancellation,
-  // and e^{i alpha} of R0's azimuth.
+  // the FP64 pipe): the convergence test, 1/R, cos b and sin b from the half angles without
+  // cancellation, and e^{i alpha} of R0's azimuth.
   if (threadIdx.x == 0) {
     const double x = d.R0[0], y = d.R0[1], z = d.R0[2];
     const double rho2 = x * x + y * y;
@@ -663,8 +641,7 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
       opc = rho2 / (R * (R - z));
     }
     g_cb = z / R;
-    g_ch = sqrt(0.5 * opc);
-    g_sh = sqrt(0.5 * omc);
+    g_sb = 2.0 * sqrt(0.5 * opc) * sqrt(0.5 * omc);  // 2 cos(b/2) sin(b/2)
     g_iR = 1.0 / R;
     const double rho = sqrt(rho2);
     g_ca = rho > 0.0 ? x / rho : 1.0;
@@ -687,46 +664,56 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     if (kGrad && threadIdx.x < 9) G[9LL * blockIdx.x + threadIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
     return;
   }
-  {  // e^{-i m alpha}, the half-angle powers and R^-(k+1), every thread a share
-    phase_powers(ph, make_double2(g_ca, g_sa), L);
-    half_angle_powers(cp, sp, g_ch, g_sh, L);
-    for (int k = threadIdx.x; k <= 2 * L + 1; k += blockDim.x) rp[k] = rpow(g_iR, k + 1);
-    if (bmode == kBRotate) {
-      phase_powers(pha, g_eb.ea, L);
-      phase_powers(phg, g_eb.eg, L);
+  {  // the phase tables and R^-(k+1), one entry per thread
+    const int nt = 2 * n1 + (2 * L + 2) + (bmode == kBRotate ? 3 * n1 : 0);
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+      if (t < n1) {
+        ph[t] = in_phase(make_double2(g_ca, g_sa), t);
+      } else if (t < 2 * n1) {
+        eb[t - n1] = beta_phase(g_cb, g_sb, t - n1);
+      } else if (t < 2 * n1 + 2 * L + 2) {
+        rp[t - 2 * n1] = rpow(g_iR, t - 2 * n1 + 1);
+      } else {
+        const int u = t - 2 * n1 - (2 * L + 2);
+        if (u < n1) pha[u] = in_phase(g_eb.ea, u);
+        else if (u < 2 * n1) ebB[u - n1] = beta_phase(g_eb.cb, 2.0 * g_eb.ch * g_eb.sh, u - n1);
+        else phg[u - 2 * n1] = out_phase(g_eb.eg, u - 2 * n1);
+      }
     }
   }
   __syncthreads();
-  // P_lm = e^{-i m alpha} Q_lm, once per (l, m), for the sides that are rotated here
+  // v~ = input phases times the moments of the sides rotated here; mode kBInFrame scales B to Qhat
   for (int k = threadIdx.x; k < nq; k += blockDim.x) {
     const int l = tri_l(k);
     const int m = k - l * (l + 1) / 2;
-    if (m == 0) continue;
     qa[k] = cmul(ph[m], qa[k]);
-    if (bmode == kBLab) qb[k] = cmul(ph[m], qb[k]);
-    else if (bmode == kBRotate) qb[k] = cmul(pha[m], qb[k]);
-  }
-  wigner_half_table(D, cp, sp, g_cb, L, ztab, rtab);
-  __syncthreads();
-  rotate_d(qa, ra, D, L, ztab, nullptr, true);
-  if (bmode == kBLab) {
-    rotate_d(qb, rb, D, L, ztab, nullptr, true);
-  } else if (bmode == kBInFrame) {
-    for (int k = threadIdx.x; k < nq; k += blockDim.x) {
-      const int l = tri_l(k);
-      const int m = k - l * (l + 1) / 2;
+    if (bmode == kBLab) {
+      qb[k] = cmul(ph[m], qb[k]);
+    } else if (bmode == kBRotate) {
+      qb[k] = cmul(pha[m], qb[k]);
+    } else {
       const double f = ztab[kZ_ISF + l * kZN + m];
-      rb[k] = make_double2(qb[k].x * f, qb[k].y * f);
+      qb[k] = make_double2(qb[k].x * f, qb[k].y * f);
     }
-  } else {  // B's cached lab-frame moments by its own rotation M_B = R_z(-gamma) R_y(-beta) R_z(-alpha)
-    __syncthreads();  // every thread is done with the frame's table
-    half_angle_powers(cp, sp, g_eb.ch, g_eb.sh, L);
-    __syncthreads();
-    wigner_half_table(D, cp, sp, g_eb.cb, L, ztab, rtab);
-    __syncthreads();
-    rotate_d(qb, rb, D, L, ztab, phg, true);
   }
   __syncthreads();
+  const int nrot = bmode == kBInFrame ? 1 : 2;
+  for (int it = threadIdx.x; it < nrot * nq; it += blockDim.x) {
+    const int side = it >= nq;
+    const int k = it - side * nq;
+    if (side) tb[k] = rot_first(Ds, qb, bmode == kBRotate ? ebB : eb, k);
+    else ta[k] = rot_first(Ds, qa, eb, k);
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < nrot * nq; it += blockDim.x) {
+    const int side = it >= nq;
+    const int k = it - side * nq;
+    if (side) qb[k] = rot_second(Ds, tb, bmode == kBRotate ? phg : nullptr, ztab, true, k);
+    else qa[k] = rot_second(Ds, ta, nullptr, ztab, true, k);
+  }
+  __syncthreads();
+  const double2* ra = qa;  // Qhat' of A and B in the frame
+  const double2* rb = qb;
   // z-axis contraction: one thread per (l1, l2).  The pairs are taken in shells of equal
   // s = min(l1, l2), s = L first: the (L - s)^2 pairs before shell s are those of the larger
   // shells, and shell s lists (s, s), (s, s+1), (s+1, s), (s, s+2), ...  Neighbouring lanes then
@@ -825,22 +812,23 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
 }
 
 // Moments of a system rotated by M about its centre, from its lab-frame moments: the Wigner
-// rotation R_z(-gamma) R_y(-beta) R_z(-alpha) = M applied degree by degree (one CTA per set).
+// rotation R_z(-gamma) R_y(-beta) R_z(-alpha) = M applied degree by degree (one CTA per set),
+// by the two products with d^l(pi/2) above.
 __global__ void __launch_bounds__(kContractThreads) k_rotate_moments(const RotDesc* __restrict__ sets,
                                                                      const double* __restrict__ ztab) {
-  const double* rtab = ztab + ((kZ_TOTAL + 3) / 4 * 4);
   extern __shared__ double2 sm2[];
   __shared__ Euler g_e;
   const RotDesc d = sets[blockIdx.x];
   const int L = d.L;
   const int nq = (L + 1) * (L + 2) / 2;
+  const int n1 = L + 1;
   double2* q = sm2;
-  double2* r = q + nq;
-  double2* pha = r + nq;
-  double2* phg = pha + (L + 1);
-  double* cp = reinterpret_cast<double*>(phg + (L + 1));
-  double* sp = cp + 2 * L + 1;
-  double* D = sp + 2 * L + 1;
+  double2* t = q + nq;
+  double2* pha = t + nq;
+  double2* ebB = pha + n1;
+  double2* phg = ebB + n1;
+  double* Ds = reinterpret_cast<double*>(phg + n1);
+  load_dpi2(Ds, ztab, L);
   if (threadIdx.x == 0) g_e = euler_zyz(sets[blockIdx.x].M);
   for (int k = threadIdx.x; k < nq; k += blockDim.x) {
     const int l = tri_l(k);
@@ -848,27 +836,28 @@ __global__ void __launch_bounds__(kContractThreads) k_rotate_moments(const RotDe
     q[k] = m == 0 ? make_double2(d.in[l * l], 0.0) : make_double2(d.in[l * l + 2 * m - 1], d.in[l * l + 2 * m]);
   }
   __syncthreads();
-  phase_powers(pha, g_e.ea, L);
-  phase_powers(phg, g_e.eg, L);
-  half_angle_powers(cp, sp, g_e.ch, g_e.sh, L);
-  __syncthreads();
-  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
-    const int l = tri_l(k);
-    const int m = k - l * (l + 1) / 2;
-    if (m > 0) q[k] = cmul(pha[m], q[k]);
+  for (int u = threadIdx.x; u < 3 * n1; u += blockDim.x) {
+    if (u < n1) pha[u] = in_phase(g_e.ea, u);
+    else if (u < 2 * n1) ebB[u - n1] = beta_phase(g_e.cb, 2.0 * g_e.ch * g_e.sh, u - n1);
+    else phg[u - 2 * n1] = out_phase(g_e.eg, u - 2 * n1);
   }
-  wigner_half_table(D, cp, sp, g_e.cb, L, ztab, rtab);
   __syncthreads();
-  rotate_d(q, r, D, L, ztab, phg, false);
+  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+    const int l = tri_l(k);
+    q[k] = cmul(pha[k - l * (l + 1) / 2], q[k]);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nq; k += blockDim.x) t[k] = rot_first(Ds, q, ebB, k);
   __syncthreads();
   for (int k = threadIdx.x; k < nq; k += blockDim.x) {
     const int l = tri_l(k);
     const int m = k - l * (l + 1) / 2;
+    const double2 r = rot_second(Ds, t, phg, ztab, false, k);
     if (m == 0) {
-      d.out[l * l] = r[k].x;
+      d.out[l * l] = r.x;
     } else {
-      d.out[l * l + 2 * m - 1] = r[k].x;
-      d.out[l * l + 2 * m] = r[k].y;
+      d.out[l * l + 2 * m - 1] = r.x;
+      d.out[l * l + 2 * m] = r.y;
     }
   }
 }
@@ -955,14 +944,12 @@ int contract_threads(int L) {
 
 int contract_smem_bytes(int L) {
   const int nq = (L + 1) * (L + 2) / 2;
-  const int nd = (L + 1) * (L + 2) * (2 * L + 3) / 6;
-  return (4 * nq + 3 * (L + 1)) * (int)sizeof(double2) + (3 * (2 * L + 1) + 1 + nd) * (int)sizeof(double);
+  return (4 * nq + 5 * (L + 1)) * (int)sizeof(double2) + (2 * L + 2 + dpi2_off(L + 1)) * (int)sizeof(double);
 }
 
 int rotate_smem_bytes(int L) {
   const int nq = (L + 1) * (L + 2) / 2;
-  const int nd = (L + 1) * (L + 2) * (2 * L + 3) / 6;
-  return (2 * nq + 2 * (L + 1)) * (int)sizeof(double2) + (2 * (2 * L + 1) + nd) * (int)sizeof(double);
+  return (2 * nq + 3 * (L + 1)) * (int)sizeof(double2) + dpi2_off(L + 1) * (int)sizeof(double);
 }
 
 int launch_rotate_moments(const RotDesc* sets, int n_sets, int Lmax_sets, const double* ztab, cudaStream_t s) {
@@ -1024,54 +1011,37 @@ int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const Mo
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-// Scalar tables (kZ_TOTAL doubles, rounded up to a 4-double boundary) followed by the
-// recursion coefficients (A, A ab / (l (l-1)), A B, 0) of every (l, a, b), a >= |b|, at
-// index l(l+1)(2l+1)/6 + a^2 + a + b.
-constexpr int kZ_RTAB_OFF = (kZ_TOTAL + 3) / 4 * 4;
-constexpr int kZ_RTAB_N = kZN * (kZN + 1) * (2 * kZN + 1) / 6;
-int contract_table_size() { return kZ_RTAB_OFF + 4 * kZ_RTAB_N; }
+int contract_table_size() { return kZ_TOTAL; }
+
+// d^l_{km}(pi/2) for 0 <= k, m <= l: at beta = pi/2 both half-angle factors are 2^(-1/2), so
+//   d^l_{km}(pi/2) = 2^-l sqrt((l+k)!(l-k)! / ((l+m)!(l-m)!)) sum_s (-1)^(k-m+s) C(l+m, s) C(l-m, l-k-s),
+// an exact integer sum (at most C(2l, l-k) in magnitude) times one square root.
+static double dpi2_entry(int l, int k, int m, const long long (*C)[2 * kZN + 1], const long double* fact) {
+  long long S = 0;
+  for (int s = (m > k ? m - k : 0); s <= l + m && s <= l - k; ++s) {
+    const long long t = C[l + m][s] * C[l - m][l - k - s];
+    S += ((k - m + s) & 1) ? -t : t;
+  }
+  const long double r = sqrtl(fact[l + k] * fact[l - k] / (fact[l + m] * fact[l - m]));
+  return (double)ldexpl((long double)S * r, -l);
+}
 
 void contract_tables(double* t) {
   for (int k = 0; k < kZ_TOTAL; ++k) t[k] = 0.0;
   long double fact[2 * kZN + 2];
   fact[0] = 1.0L;
   for (int k = 1; k < 2 * kZN + 2; ++k) fact[k] = fact[k - 1] * (long double)k;
-  for (int l = 0; l < kZN; ++l) {
-    for (int a = 0; a <= l; ++a) {
-      if (a < l) {
-        const long double r = sqrtl((long double)(l * l - a * a));
-        t[kZ_K1 + l * kZN + a] = (double)((long double)(l * (2 * l - 1)) / r);
-        t[kZ_IRS + l * kZN + a] = (double)(1.0L / r);
-      }
-      if (l >= 1 && a <= l - 1) t[kZ_RS1 + l * kZN + a] = (double)sqrtl((long double)((l - 1) * (l - 1) - a * a));
-      if (l >= 2 && a <= l - 1)
-        t[kZ_K2 + l * kZN + a] = (double)(sqrtl((long double)((l - 1) * (l - 1) - a * a)) /
-                                          (long double)((l - 1) * (2 * l - 1)));
-      t[kZ_ISF + l * kZN + a] = (double)(1.0L / sqrtl(fact[l + a] * fact[l - a]));
-    }
-    if (l >= 2) t[kZ_ILL + l] = (double)(1.0L / (long double)(l * (l - 1)));
-    for (int b = -l; b <= l; ++b)
-      t[kZ_SQC + l * 2 * kZN + l + b] = (double)sqrtl(fact[2 * l] / (fact[l + b] * fact[l - b]));
-  }
   for (int k = 0; k < 2 * kZN; ++k) t[kZ_FACT + k] = (double)fact[k];
   for (int l = 0; l < kZN; ++l)
-    for (int a = 0; a <= l; ++a)
-      for (int b = -a; b <= a; ++b) {
-        double* c = t + kZ_RTAB_OFF + 4 * (l * (l + 1) * (2 * l + 1) / 6 + a * a + a + b);
-        if (l <= a) continue;  // seeds, no step
-        const int ab = b < 0 ? -b : b;
-        const long double A = (long double)(l * (2 * l - 1)) /
-                              (sqrtl((long double)(l * l - a * a)) * sqrtl((long double)(l * l - ab * ab)));
-        const long double ill = l >= 2 ? 1.0L / (long double)(l * (l - 1)) : 0.0L;
-        long double B = 0.0L;
-        if (l - 2 >= a)
-          B = sqrtl((long double)((l - 1) * (l - 1) - a * a)) * sqrtl((long double)((l - 1) * (l - 1) - ab * ab)) /
-              (long double)((l - 1) * (2 * l - 1));
-        c[0] = (double)A;
-        c[1] = (double)(A * (long double)(a * b) * ill);
-        c[2] = (double)(A * B);
-        c[3] = 0.0;
-      }
+    for (int m = 0; m <= l; ++m) t[kZ_ISF + l * kZN + m] = (double)(1.0L / sqrtl(fact[l + m] * fact[l - m]));
+  static long long C[2 * kZN + 1][2 * kZN + 1];  // binomials up to C(2 kLmaxMax, .), exact
+  for (int n = 0; n <= 2 * kZN; ++n) {
+    C[n][0] = 1;
+    for (int k = 1; k <= 2 * kZN; ++k) C[n][k] = n == 0 ? 0 : C[n - 1][k - 1] + C[n - 1][k];
+  }
+  for (int l = 0; l < kZN; ++l)
+    for (int k = 0; k <= l; ++k)
+      for (int m = 0; m <= l; ++m) t[kZ_DPI2 + dpi2_off(l) + k * (l + 1) + m] = dpi2_entry(l, k, m, C, fact);
 }
 
 int direct_blocks(long long na) { return (int)((na + kDirectThreads - 1) / kDirectThreads); }
