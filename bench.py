@@ -465,7 +465,9 @@ def run_pes_grid(torch, tcm, prec, n_sm, sm_mhz, stream):
     R0 = g.R0()
     ctx = tcm.Context(lmax_cap=max(g.lmax), stream=stream)
     try:
-        pes.scan(ctx, A, B, R0[:64], g.lmax, precision=prec)  # warm-up (kernel attributes, buffers)
+        pes.scan(ctx, A, B, R0[:64], g.lmax, precision=prec)  # warm-up (kernel attributes)
+        for _ in range(4):  # descriptor staging buffers and scratch at the full grid's size
+            pes.scan(ctx, A, B, R0, g.lmax, precision=prec, direct=False)
         res = pes.scan(ctx, A, B, R0, g.lmax, precision=prec)
     finally:
         ctx.close()

@@ -410,12 +410,18 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const MomJob* __r
 constexpr int kContractThreads = 256;
 
 // Layout of ztab (doubles): k! for k < 2 kZN, 1/sqrt((l+m)!(l-m)!) at [l][m], and the rows of
-// D^l = d^l(pi/2): D^l_{km}, 0 <= k, m <= l, at kZ_DPI2 + dpi2_off(l) + k (l + 1) + m.
+// D^l = d^l(pi/2): D^l_{km}, 0 <= k, m <= l, at kZ_DPI2 + dpi2_off(l) + k dpi2_stride(l) + m.  The
+// row stride is odd (rows of even length get one zero), so that the lanes of a warp reading
+// one entry of consecutive rows hit distinct shared-memory banks; shared memory holds the
+// same layout.
 constexpr int kZN = kLmaxMax + 1;
 constexpr int kZ_FACT = 0;
 constexpr int kZ_ISF = kZ_FACT + 2 * kZN;
 constexpr int kZ_DPI2 = kZ_ISF + kZN * kZN;
-__host__ __device__ constexpr int dpi2_off(int l) { return l * (l + 1) * (2 * l + 1) / 6; }
+__host__ __device__ constexpr int dpi2_stride(int l) { return (l + 1) | 1; }
+__host__ __device__ constexpr int dpi2_off(int l) {  // sum over l' < l of (l'+1) dpi2_stride(l')
+  return l * (l + 1) * (2 * l + 1) / 6 + (l / 2) * (l / 2 + 1);
+}
 constexpr int kZ_TOTAL = kZ_DPI2 + dpi2_off(kZN);
 
 __device__ __forceinline__ double flip(double x, int odd) {  // (-1)^odd x without an FP64 op
@@ -458,45 +464,6 @@ __device__ void load_dpi2(double* Ds, const double* __restrict__ ztab, int L) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) Ds[i] = __ldg(src + i);
 }
 
-// Euler angles of a rotation M = R_z(-gamma) R_y(-beta) R_z(-alpha), beta in [0, pi], through
-// its unit quaternion (largest-component extraction): with q = (w, x, y, z),
-//   cos(beta/2) = |(w, z)|,  sin(beta/2) = |(x, y)|,
-//   e^{i(alpha+gamma)/2} = (w - i z) / cos(beta/2),  e^{i(alpha-gamma)/2} = (-y + i x) / sin(beta/2),
-// which stays accurate near beta = 0 and pi (where only alpha+gamma, resp. alpha-gamma, matters).
-struct Euler {
-  double cb, ch, sh;  // cos(beta), cos(beta/2), sin(beta/2)
-  double2 ea, eg;     // e^{i alpha}, e^{i gamma}
-};
-
-__device__ Euler euler_zyz(const double* M) {
-  const double t = M[0] + M[4] + M[8];
-  double w, x, y, z;
-  if (t > 0.0) {
-    const double s = 2.0 * sqrt(t + 1.0);
-    w = 0.25 * s; x = (M[7] - M[5]) / s; y = (M[2] - M[6]) / s; z = (M[3] - M[1]) / s;
-  } else if (M[0] > M[4] && M[0] > M[8]) {
-    const double s = 2.0 * sqrt(1.0 + M[0] - M[4] - M[8]);
-    w = (M[7] - M[5]) / s; x = 0.25 * s; y = (M[1] + M[3]) / s; z = (M[2] + M[6]) / s;
-  } else if (M[4] > M[8]) {
-    const double s = 2.0 * sqrt(1.0 + M[4] - M[0] - M[8]);
-    w = (M[2] - M[6]) / s; x = (M[1] + M[3]) / s; y = 0.25 * s; z = (M[5] + M[7]) / s;
-  } else {
-    const double s = 2.0 * sqrt(1.0 + M[8] - M[0] - M[4]);
-    w = (M[3] - M[1]) / s; x = (M[2] + M[6]) / s; y = (M[5] + M[7]) / s; z = 0.25 * s;
-  }
-  const double n = 1.0 / sqrt(w * w + x * x + y * y + z * z);
-  w *= n; x *= n; y *= n; z *= n;
-  Euler e;
-  e.ch = sqrt(w * w + z * z);
-  e.sh = sqrt(x * x + y * y);
-  e.cb = (e.ch - e.sh) * (e.ch + e.sh);
-  const double2 p = e.ch > 0.0 ? make_double2(w / e.ch, -z / e.ch) : make_double2(1.0, 0.0);
-  const double2 q = e.sh > 0.0 ? make_double2(-y / e.sh, x / e.sh) : make_double2(1.0, 0.0);
-  e.ea = make_double2(p.x * q.x - p.y * q.y, p.x * q.y + p.y * q.x);  // p q
-  e.eg = make_double2(p.x * q.x + p.y * q.y, p.y * q.x - p.x * q.y);  // p conj(q)
-  return e;
-}
-
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -522,20 +489,44 @@ __device__ __forceinline__ double2 cpow(double2 z, int n) {
   return r;
 }
 
-// The phase factors of one rotation R_z(-gamma) R_y(-beta) R_z(-alpha):
+// z^lane in every lane of the calling warp (lane <= 31): an inclusive product scan of
+// (1, z, z, ...), five steps of one complex multiplication each.
+__device__ __forceinline__ double2 warp_pow_scan(double2 z, int lane) {
+  double2 r = lane == 0 ? make_double2(1.0, 0.0) : z;
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const double2 u = make_double2(__shfl_up_sync(0xffffffffu, r.x, s), __shfl_up_sync(0xffffffffu, r.y, s));
+    if (lane >= s) r = cmul(r, u);
+  }
+  return r;
+}
+// x^(lane + 1) in every lane of the calling warp.
+__device__ __forceinline__ double warp_rpow_scan(double x, int lane) {
+  double r = x;
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const double u = __shfl_up_sync(0xffffffffu, r, s);
+    if (lane >= s) r *= u;
+  }
+  return r;
+}
+
+// The phase factors of one rotation R_z(-gamma) R_y(-beta) R_z(-alpha), one warp per table,
+// entry m = lane <= L:
 //   in:   (-i)^m e^{-i m alpha}, doubled for m >= 1       (from e^{i alpha})
 //   beta: e^{i k beta}, doubled for k >= 1                (from cos beta, sin beta)
 //   out:  i^m e^{-i m gamma}                              (from e^{i gamma})
-__device__ __forceinline__ double2 in_phase(double2 e, int m) {
-  const double2 z = mul_ipow(cpow(make_double2(e.x, -e.y), m), -m);
-  return m > 0 ? make_double2(2.0 * z.x, 2.0 * z.y) : z;
+__device__ __forceinline__ void in_phases(double2* t, double2 e, int L, int lane) {
+  const double2 z = mul_ipow(warp_pow_scan(make_double2(e.x, -e.y), lane), -lane);
+  if (lane <= L) t[lane] = lane > 0 ? make_double2(2.0 * z.x, 2.0 * z.y) : z;
 }
-__device__ __forceinline__ double2 beta_phase(double cb, double sb, int k) {
-  const double2 z = cpow(make_double2(cb, sb), k);
-  return k > 0 ? make_double2(2.0 * z.x, 2.0 * z.y) : z;
+__device__ __forceinline__ void beta_phases(double2* t, double cb, double sb, int L, int lane) {
+  const double2 z = warp_pow_scan(make_double2(cb, sb), lane);
+  if (lane <= L) t[lane] = lane > 0 ? make_double2(2.0 * z.x, 2.0 * z.y) : z;
 }
-__device__ __forceinline__ double2 out_phase(double2 e, int m) {
-  return mul_ipow(cpow(make_double2(e.x, -e.y), m), m);
+__device__ __forceinline__ void out_phases(double2* t, double2 e, int L, int lane) {
+  const double2 z = mul_ipow(warp_pow_scan(make_double2(e.x, -e.y), lane), lane);
+  if (lane <= L) t[lane] = z;
 }
 
 // First product of a rotation, item k = (l, kk) of the triangle: p~_kk from v~ (the moments
@@ -543,7 +534,7 @@ __device__ __forceinline__ double2 out_phase(double2 e, int m) {
 __device__ __forceinline__ double2 rot_first(const double* Ds, const double2* v, const double2* eb, int k) {
   const int l = tri_l(k);
   const int kk = k - l * (l + 1) / 2;
-  const double2 p = row_split(Ds + dpi2_off(l) + kk * (l + 1), v + l * (l + 1) / 2, l, (l + kk) & 1);
+  const double2 p = row_split(Ds + dpi2_off(l) + kk * dpi2_stride(l), v + l * (l + 1) / 2, l, (l + kk) & 1);
   return cmul(eb[kk], p);
 }
 // Second product, item k = (l, m): S_m, times the output phase (i^m when there is no gamma) and,
@@ -552,7 +543,7 @@ __device__ __forceinline__ double2 rot_second(const double* Ds, const double2* p
                                               const double* ztab, bool hat, int k) {
   const int l = tri_l(k);
   const int m = k - l * (l + 1) / 2;
-  const double2 a = row_split(Ds + dpi2_off(l) + m * (l + 1), p + l * (l + 1) / 2, l, (l + m) & 1);
+  const double2 a = row_split(Ds + dpi2_off(l) + m * dpi2_stride(l), p + l * (l + 1) / 2, l, (l + m) & 1);
   const double2 S = make_double2(flip(a.x, l), flip(a.y, l + 1));
   double2 q = phout ? cmul(phout[m], S) : mul_ipow(S, m);
   if (hat) {
@@ -601,9 +592,7 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
                                                                double* __restrict__ G) {
   extern __shared__ double2 sm2[];
   __shared__ double sh[(kGrad ? 9 : 1) * 32];
-  __shared__ double g_cb, g_sb, g_iR, g_ca, g_sa;
   __shared__ int g_conv;
-  __shared__ Euler g_eb;
   const PairDesc d = items[blockIdx.x];  // descriptors and tables precede the kernels before
   const int L = d.L;
   const int nq = (L + 1) * (L + 2) / 2;
@@ -624,31 +613,8 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
   const double* pa = jobs[d.jobA].out;
   const double* pb = jobs[d.jobB].out;
   const int bmode = d.b_mode;
-  // Geometry of the frame, once per CTA (every FP64 instruction costs the whole warp's slot on
-  // the FP64 pipe): the convergence test, 1/R, cos b and sin b from the half angles without
-  // cancellation, and e^{i alpha} of R0's azimuth.
-  if (threadIdx.x == 0) {
-    const double x = d.R0[0], y = d.R0[1], z = d.R0[2];
-    const double rho2 = x * x + y * y;
-    const double R = sqrt(rho2 + z * z);
-    g_conv = R > geoms[d.geomA].a + geoms[d.geomB].a;  // Eq. (mainCond)
-    double opc, omc;  // 1 + cos b, 1 - cos b
-    if (z >= 0.0) {
-      opc = (R + z) / R;
-      omc = rho2 / (R * (R + z));
-    } else {
-      omc = (R - z) / R;
-      opc = rho2 / (R * (R - z));
-    }
-    g_cb = z / R;
-    g_sb = 2.0 * sqrt(0.5 * opc) * sqrt(0.5 * omc);  // 2 cos(b/2) sin(b/2)
-    g_iR = 1.0 / R;
-    const double rho = sqrt(rho2);
-    g_ca = rho > 0.0 ? x / rho : 1.0;
-    g_sa = rho > 0.0 ? y / rho : 0.0;
-  } else if (threadIdx.x == 32 && bmode == kBRotate) {
-    g_eb = euler_zyz(rots + 9LL * d.rot);
-  }
+  // the frame's angles and R come with the descriptor; the radii from the kernels before
+  if (threadIdx.x == 0) g_conv = d.fr[1] > geoms[d.geomA].a + geoms[d.geomB].a;  // Eq. (mainCond)
   for (int k = threadIdx.x; k < nq; k += blockDim.x) {
     const int l = tri_l(k);
     const int m = k - l * (l + 1) / 2;
@@ -664,20 +630,28 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     if (kGrad && threadIdx.x < 9) G[9LL * blockIdx.x + threadIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
     return;
   }
-  {  // the phase tables and R^-(k+1), one entry per thread
-    const int nt = 2 * n1 + (2 * L + 2) + (bmode == kBRotate ? 3 * n1 : 0);
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-      if (t < n1) {
-        ph[t] = in_phase(make_double2(g_ca, g_sa), t);
-      } else if (t < 2 * n1) {
-        eb[t - n1] = beta_phase(g_cb, g_sb, t - n1);
-      } else if (t < 2 * n1 + 2 * L + 2) {
-        rp[t - 2 * n1] = rpow(g_iR, t - 2 * n1 + 1);
-      } else {
-        const int u = t - 2 * n1 - (2 * L + 2);
-        if (u < n1) pha[u] = in_phase(g_eb.ea, u);
-        else if (u < 2 * n1) ebB[u - n1] = beta_phase(g_eb.cb, 2.0 * g_eb.ch * g_eb.sh, u - n1);
-        else phg[u - 2 * n1] = out_phase(g_eb.eg, u - 2 * n1);
+  {  // the phase tables and R^-(k+1) (k <= 2L + 1 <= 49), one warp per table (warp-uniform tasks)
+    const int lane = threadIdx.x & 31;
+    const int ntask = bmode == kBRotate ? 7 : 4;
+    for (int tt = threadIdx.x >> 5; tt < ntask; tt += blockDim.x >> 5) {
+      const EulerZYZ* e = reinterpret_cast<const EulerZYZ*>(rots) + d.rot;
+      switch (tt) {
+        case 0: in_phases(ph, make_double2(d.fr[4], d.fr[5]), L, lane); break;
+        case 1: beta_phases(eb, d.fr[2], d.fr[3], L, lane); break;
+        case 2: {
+          const double r = warp_rpow_scan(d.fr[0], lane);
+          if (lane < 2 * L + 2) rp[lane] = r;
+          break;
+        }
+        case 3:
+          if (2 * L + 2 > 32) {
+            const double r = warp_rpow_scan(d.fr[0], lane) * rpow(d.fr[0], 32);
+            if (32 + lane < 2 * L + 2) rp[32 + lane] = r;
+          }
+          break;
+        case 4: in_phases(pha, make_double2(e->ea[0], e->ea[1]), L, lane); break;
+        case 5: beta_phases(ebB, e->cb, e->sb, L, lane); break;
+        default: out_phases(phg, make_double2(e->eg[0], e->eg[1]), L, lane); break;
       }
     }
   }
@@ -795,8 +769,8 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     if (threadIdx.x == 0) {
       E[blockIdx.x] = v[0];
       if (status) status[blockIdx.x] = TCM_OK;
-      double W[9];
-      frame_rotation(d.R0, W);
+      const double cb = d.fr[2], sb = d.fr[3], ca = d.fr[4], sa = d.fr[5];
+      const double W[9] = {cb * ca, cb * sa, -sb, -sa, ca, 0.0, sb * ca, sb * sa, cb};  // R_y(-b) R_z(-a)
       // frame -> lab: v_lab = W^T v_frame; force = -grad; tau_A,z = -tau_B,z
       const double f[3] = {-v[1], -v[2], -v[3]};
       const double ta[3] = {v[7], v[8], -v[6]};
@@ -817,7 +791,7 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
 __global__ void __launch_bounds__(kContractThreads) k_rotate_moments(const RotDesc* __restrict__ sets,
                                                                      const double* __restrict__ ztab) {
   extern __shared__ double2 sm2[];
-  __shared__ Euler g_e;
+  __shared__ EulerZYZ g_e;
   const RotDesc d = sets[blockIdx.x];
   const int L = d.L;
   const int nq = (L + 1) * (L + 2) / 2;
@@ -836,10 +810,11 @@ __global__ void __launch_bounds__(kContractThreads) k_rotate_moments(const RotDe
     q[k] = m == 0 ? make_double2(d.in[l * l], 0.0) : make_double2(d.in[l * l + 2 * m - 1], d.in[l * l + 2 * m]);
   }
   __syncthreads();
-  for (int u = threadIdx.x; u < 3 * n1; u += blockDim.x) {
-    if (u < n1) pha[u] = in_phase(g_e.ea, u);
-    else if (u < 2 * n1) ebB[u - n1] = beta_phase(g_e.cb, 2.0 * g_e.ch * g_e.sh, u - n1);
-    else phg[u - 2 * n1] = out_phase(g_e.eg, u - 2 * n1);
+  for (int tt = threadIdx.x >> 5; tt < 3; tt += blockDim.x >> 5) {
+    const int lane = threadIdx.x & 31;
+    if (tt == 0) in_phases(pha, make_double2(g_e.ea[0], g_e.ea[1]), L, lane);
+    else if (tt == 1) beta_phases(ebB, g_e.cb, g_e.sb, L, lane);
+    else out_phases(phg, make_double2(g_e.eg[0], g_e.eg[1]), L, lane);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < nq; k += blockDim.x) {
@@ -1041,7 +1016,7 @@ void contract_tables(double* t) {
   }
   for (int l = 0; l < kZN; ++l)
     for (int k = 0; k <= l; ++k)
-      for (int m = 0; m <= l; ++m) t[kZ_DPI2 + dpi2_off(l) + k * (l + 1) + m] = dpi2_entry(l, k, m, C, fact);
+      for (int m = 0; m <= l; ++m) t[kZ_DPI2 + dpi2_off(l) + k * dpi2_stride(l) + m] = dpi2_entry(l, k, m, C, fact);
 }
 
 int direct_blocks(long long na) { return (int)((na + kDirectThreads - 1) / kDirectThreads); }

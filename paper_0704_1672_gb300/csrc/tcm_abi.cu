@@ -661,7 +661,8 @@ int tcm_energy(tcm_ctx_t c, const tcm_moments_t* A, const tcm_moments_t* B, cons
   geoms[0].a = A->radius;
   geoms[1].a = B->radius;
   std::vector<PairDesc> items(1);
-  items[0] = PairDesc{0, 1, 0, 1, lmax, kBLab, {R0[0], R0[1], R0[2]}, 0};
+  items[0] = PairDesc{0, 1, 0, 1, lmax, kBLab, 0, {}};
+  pair_frame(R0, items[0]);
   Packer pk;
   const size_t o_job = pk.add(jobs), o_geo = pk.add(geoms), o_it = pk.add(items);
   char* base = nullptr;
@@ -807,7 +808,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
     job_of[key] = id;
     return id;
   };
-  std::vector<double> rots;  // 3x3 per rotate-from-cache item
+  std::vector<EulerZYZ> rots;  // Euler record of W rotB per rotate-from-cache item
   for (int64_t k = 0; k < n_items; ++k) {
     const tcm_pair_item& it = items[k];
     const int ja = get_job(it.a, it.lmax, -1, nullptr);
@@ -817,11 +818,13 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
       double W[9];
       frame_rotation(it.R0, W);
       jb = get_job(it.b, it.lmax, -1, nullptr);
-      pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, kBRotate, {it.R0[0], it.R0[1], it.R0[2]},
-                       (long long)(rots.size() / 9)};
+      pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, kBRotate, (long long)rots.size(), {}};
+      pair_frame(it.R0, pd[k]);
+      double M[9];
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
-          rots.push_back(W[3 * i + 0] * it.rotB[0 + j] + W[3 * i + 1] * it.rotB[3 + j] + W[3 * i + 2] * it.rotB[6 + j]);
+          M[3 * i + j] = W[3 * i + 0] * it.rotB[0 + j] + W[3 * i + 1] * it.rotB[3 + j] + W[3 * i + 2] * it.rotB[6 + j];
+      rots.push_back(euler_zyz(M));
       continue;
     }
     if (it.has_rot) {
@@ -836,7 +839,8 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
     } else {
       jb = get_job(it.b, it.lmax, -1, nullptr);
     }
-    pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, it.has_rot ? kBInFrame : kBLab, {it.R0[0], it.R0[1], it.R0[2]}, 0};
+    pd[k] = PairDesc{ja, jb, it.a, it.b, it.lmax, it.has_rot ? kBInFrame : kBLab, 0, {}};
+    pair_frame(it.R0, pd[k]);
   }
   P.n_tile_ids = next_id;
   TRY(dev_ensure(c, c->moms, std::max<size_t>(moff, 1) * sizeof(double)));
