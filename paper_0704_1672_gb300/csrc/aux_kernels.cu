@@ -409,14 +409,15 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const MomJob* __r
 // multiply-adds per product and degree, no table of d^l(beta) per energy.
 constexpr int kContractThreads = 256;
 
-// Layout of ztab (doubles): k! for k < 2 kZN, 1/sqrt((l+m)!(l-m)!) at [l][m], and the rows of
+// Layout of ztab (doubles): k! and 2 k! for k < 2 kZN, 1/sqrt((l+m)!(l-m)!) at [l][m], and the rows of
 // D^l = d^l(pi/2): D^l_{km}, 0 <= k, m <= l, at kZ_DPI2 + dpi2_off(l) + k dpi2_stride(l) + m.  The
 // row stride is odd (rows of even length get one zero), so that the lanes of a warp reading
 // one entry of consecutive rows hit distinct shared-memory banks; shared memory holds the
 // same layout.
 constexpr int kZN = kLmaxMax + 1;
 constexpr int kZ_FACT = 0;
-constexpr int kZ_ISF = kZ_FACT + 2 * kZN;
+constexpr int kZ_FACT2 = kZ_FACT + 2 * kZN;
+constexpr int kZ_ISF = kZ_FACT2 + 2 * kZN;
 constexpr int kZ_DPI2 = kZ_ISF + kZN * kZN;
 __host__ __device__ constexpr int dpi2_stride(int l) { return (l + 1) | 1; }
 __host__ __device__ constexpr int dpi2_off(int l) {  // sum over l' < l of (l'+1) dpi2_stride(l')
@@ -582,8 +583,11 @@ __device__ void block_sum_n(double (&v)[N], double* sh) {
 //   tau_B = sum c (Im P, -Re P, -Z),  tau_A = sum c (Im P', -Re P', Z),  P' = (L+1) S+ - P
 //   (infinitesimal rotations act on Qhat_lm through L_z and the ladder operators with the
 //   integer weights (l+m+1), (l-m+1)).  The vectors go back to the lab frame with W^T.
+// Launch bounds: the energy kernel stays within 64 registers (4 CTAs of 256 threads per SM for
+// large batches); the gradient kernel, with nine sums per thread, may take more (at the default
+// it was held to 64 and spilled).
 template <bool kGrad>
-__global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* __restrict__ items,
+__global__ void __launch_bounds__(kContractThreads, kGrad ? 1 : 4) k_contract(const PairDesc* __restrict__ items,
                                                                const MomJob* __restrict__ jobs,
                                                                const SysGeom* __restrict__ geoms,
                                                                const double* __restrict__ ztab,
@@ -607,7 +611,9 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
   double2* ebB = pha + n1;
   double2* phg = ebB + n1;
   double* rp = reinterpret_cast<double*>(phg + n1);  // R^-(k+1), k <= 2L + 1
-  double* Ds = rp + 2 * L + 2;                        // rows of D^l, l <= L
+  double* c2t = rp + 2 * L + 2;                       // 2 n! R^-(n+1), n <= 2L
+  double* hb0 = c2t + 2 * L + 1;                      // Qhat'^B_l0 / 2
+  double* Ds = hb0 + L + 1;                           // rows of D^l, l <= L
   load_dpi2(Ds, ztab, L);
   pdl_wait();  // the moments (and centres and radii) of the launches before are complete
   const double* pa = jobs[d.jobA].out;
@@ -668,8 +674,10 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     } else {
       const double f = ztab[kZ_ISF + l * kZN + m];
       qb[k] = make_double2(qb[k].x * f, qb[k].y * f);
+      if (m == 0) hb0[l] = 0.5 * qb[k].x;
     }
   }
+  for (int n = threadIdx.x; n <= 2 * L; n += blockDim.x) c2t[n] = ztab[kZ_FACT2 + n] * rp[n];
   __syncthreads();
   const int nrot = bmode == kBInFrame ? 1 : 2;
   for (int it = threadIdx.x; it < nrot * nq; it += blockDim.x) {
@@ -682,8 +690,14 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
   for (int it = threadIdx.x; it < nrot * nq; it += blockDim.x) {
     const int side = it >= nq;
     const int k = it - side * nq;
-    if (side) qb[k] = rot_second(Ds, tb, bmode == kBRotate ? phg : nullptr, ztab, true, k);
-    else qa[k] = rot_second(Ds, ta, nullptr, ztab, true, k);
+    if (side) {
+      const double2 q = rot_second(Ds, tb, bmode == kBRotate ? phg : nullptr, ztab, true, k);
+      qb[k] = q;
+      const int l = tri_l(k);
+      if (k == l * (l + 1) / 2) hb0[l] = 0.5 * q.x;
+    } else {
+      qa[k] = rot_second(Ds, ta, nullptr, ztab, true, k);
+    }
   }
   __syncthreads();
   const double2* ra = qa;  // Qhat' of A and B in the frame
@@ -704,7 +718,9 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
     const double2* a = ra + l1 * (l1 + 1) / 2;
     const double2* b = rb + l2 * (l2 + 1) / 2;
     const int mm = l1 < l2 ? l1 : l2;
-    double se = 0.0, so = 0.0;  // even and odd m: sum_m (-1)^m Re(a_m conj b_m) = se - so
+    // even and odd m: with the m = 0 term at half weight, s / 2 = a_0 b_0 / 2 + sum_{m>=1} (-1)^m
+    // Re(a_m conj b_m) = se - so, and the factor 2 sits in the table c2t
+    double se = a[0].x * hb0[l2], so = 0.0;
     int m = 1;
     for (; m + 1 <= mm; m += 2) {
       so = fma(a[m].x, b[m].x, so);
@@ -716,10 +732,11 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
       so = fma(a[m].x, b[m].x, so);
       so = fma(a[m].y, b[m].y, so);
     }
-    double s = fma(2.0, se - so, a[0].x * b[0].x);
-    const double c = flip(ztab[kZ_FACT + l1 + l2] * rp[l1 + l2], l2);
-    acc = fma(c, s, acc);
+    const double h = se - so;
+    acc = fma(flip(c2t[l1 + l2], l2), h, acc);
     if (kGrad) {
+      const double s = h + h;
+      const double c = flip(ztab[kZ_FACT + l1 + l2] * rp[l1 + l2], l2);
       // S+ and P: pairs (m1, m2) = (m, 1 - m), m >= 1, and (-m, m + 1), m >= 0
       double spr = 0.0, spi = 0.0, pr = 0.0, pi = 0.0, z = 0.0;
       const int m1a = l1 < l2 + 1 ? l1 : l2 + 1;
@@ -776,6 +793,7 @@ __global__ void __launch_bounds__(kContractThreads) k_contract(const PairDesc* _
       const double ta[3] = {v[7], v[8], -v[6]};
       const double tb[3] = {v[4], v[5], v[6]};
       double* o = G + 9LL * blockIdx.x;
+#pragma unroll
       for (int i = 0; i < 3; ++i) {
         o[i] = W[i] * f[0] + W[3 + i] * f[1] + W[6 + i] * f[2];
         o[3 + i] = W[i] * ta[0] + W[3 + i] * ta[1] + W[6 + i] * ta[2];
@@ -919,7 +937,7 @@ int contract_threads(int L) {
 
 int contract_smem_bytes(int L) {
   const int nq = (L + 1) * (L + 2) / 2;
-  return (4 * nq + 5 * (L + 1)) * (int)sizeof(double2) + (2 * L + 2 + dpi2_off(L + 1)) * (int)sizeof(double);
+  return (4 * nq + 5 * (L + 1)) * (int)sizeof(double2) + (5 * L + 4 + dpi2_off(L + 1)) * (int)sizeof(double);
 }
 
 int rotate_smem_bytes(int L) {
@@ -1006,7 +1024,10 @@ void contract_tables(double* t) {
   long double fact[2 * kZN + 2];
   fact[0] = 1.0L;
   for (int k = 1; k < 2 * kZN + 2; ++k) fact[k] = fact[k - 1] * (long double)k;
-  for (int k = 0; k < 2 * kZN; ++k) t[kZ_FACT + k] = (double)fact[k];
+  for (int k = 0; k < 2 * kZN; ++k) {
+    t[kZ_FACT + k] = (double)fact[k];
+    t[kZ_FACT2 + k] = (double)(2.0L * fact[k]);
+  }
   for (int l = 0; l < kZN; ++l)
     for (int m = 0; m <= l; ++m) t[kZ_ISF + l * kZN + m] = (double)(1.0L / sqrtl(fact[l + m] * fact[l - m]));
   static long long C[2 * kZN + 1][2 * kZN + 1];  // binomials up to C(2 kLmaxMax, .), exact
