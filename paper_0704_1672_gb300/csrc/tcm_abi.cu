@@ -86,7 +86,7 @@ struct tcm_ctx {
   cudaStream_t stream = nullptr;
   // tables
   double* d_fmap = nullptr;  // F_lm of the component each (chunk, slot) holds
-  double* d_ztab = nullptr;  // contraction tables (Wigner-d recursion, factorials, 1/sqrt((l+m)!(l-m)!))
+  double* d_ztab = nullptr;  // contraction tables (factorials, 1/sqrt((l+m)!(l-m)!), the rows of d^l(pi/2))
   int* d_imap = nullptr;      // (chunk, slot) -> packed component, both precisions
   int* d_imap_off = nullptr;  // [precision][L] offsets into d_imap
   // scratch
