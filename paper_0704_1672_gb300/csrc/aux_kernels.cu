@@ -469,22 +469,12 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// x^n and z^n by binary powering (n >= 0): O(log n) multiplications, so every entry of a
-// power table is computed by its own thread instead of along one serial chain.
+// x^n by binary powering (n >= 0).
 __device__ __forceinline__ double rpow(double x, int n) {
   double r = 1.0;
   while (n) {
     if (n & 1) r *= x;
     x *= x;
-    n >>= 1;
-  }
-  return r;
-}
-__device__ __forceinline__ double2 cpow(double2 z, int n) {
-  double2 r = make_double2(1.0, 0.0);
-  while (n) {
-    if (n & 1) r = cmul(r, z);
-    z = cmul(z, z);
     n >>= 1;
   }
   return r;
