@@ -80,10 +80,13 @@ constexpr int kGeomThreads = 128;
 // and the CTAs combine their partial sums through distributed shared memory, so the two passes
 // need neither a second launch nor global tickets.  The per-atom arithmetic is float:
 //   * centroid: each thread adds its coordinates with an error-free two-sum (value + error),
-//     the pairs go to double for the block and cluster sums (fixed order);
+//     the pairs are reduced in float-float over the warp and the CTA, and every CTA adds the
+//     CTAs' double sums in rank order (the same centre in all of them, no second barrier);
 //   * radius: |x - c|^2 in float from the split centre (c_hi + c_lo) picks the candidates
 //     within a relative 4e-6 of the largest (the float value is within 1e-6 of the exact one),
 //     and only those are recomputed in double; their maximum is the exact double radius^2.
+//     Both maxima go to rank 0 by atomicMax on distributed shared memory (non-negative floats
+//     and doubles order like their bit patterns): three cluster barriers in all.
 namespace cg = cooperative_groups;
 __device__ __forceinline__ void two_sum_add(float& s, float& e, float x) {
   const float t = s + x;
@@ -117,9 +120,9 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
   __shared__ float2 s_wsum[3][kWarps];       // warp sums as float-float pairs (value, error)
   __shared__ float s_wmax[kWarps];
   __shared__ double s_part[3];               // this CTA's coordinate sums
-  __shared__ float s_fmax;                   // this CTA's float maximum of |x - c|^2
-  __shared__ unsigned long long s_dmax;      // its exact double maximum over the candidates (bits)
-  __shared__ double s_c[3];                  // the centre (rank 0)
+  __shared__ unsigned int s_fmax;            // rank 0: the cluster's float maximum of |x - c|^2 (bits)
+  __shared__ unsigned long long s_dmax;      // rank 0: the exact double maximum over the candidates (bits)
+  __shared__ double s_c[3];                  // the centre
   __shared__ float2 s_cf[3];                 // and its split c = hi + lo into floats
   __shared__ float s_thr;
   cg::cluster_group cluster = cg::this_cluster();
@@ -139,7 +142,10 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
     y[k] = v.y;
     z[k] = v.z;
   }
-  if (threadIdx.x == 0) s_dmax = 0ull;
+  if (threadIdx.x == 0) {
+    s_fmax = 0u;
+    s_dmax = 0ull;
+  }
   // pass 1: coordinate sums, float-float within the CTA, double across the CTAs
   float sx = 0.f, ex = 0.f, sy = 0.f, ey = 0.f, sz = 0.f, ez = 0.f;
 #pragma unroll
@@ -166,8 +172,8 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
     }
     s_part[threadIdx.x] = (double)t + (double)te;
   }
-  cluster.sync();
-  if (rank == 0 && threadIdx.x < 3) {  // rank order
+  cluster.sync();  // (1) every CTA's sums are in place, rank 0's maxima are cleared
+  if (threadIdx.x < 3) {  // every CTA adds the CTAs' sums in rank order: the same centre in all of them
     double t = 0.0;
     for (int r = 0; r < kGeomClusterCTAs; ++r) t += cluster.map_shared_rank(s_part, r)[threadIdx.x];
     const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
@@ -176,10 +182,9 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
     s_c[threadIdx.x] = c;
     s_cf[threadIdx.x] = make_float2(hi, (float)(c - (double)hi));
   }
-  cluster.sync();
+  __syncthreads();
   // pass 2: largest |x - c|^2, float filter then exact double on the candidates
-  const float2* cf0 = cluster.map_shared_rank(s_cf, 0);
-  const float2 fx = cf0[0], fy = cf0[1], fz = cf0[2];
+  const float2 fx = s_cf[0], fy = s_cf[1], fz = s_cf[2];
   const float chx = fx.x, chy = fy.x, chz = fz.x, clx = fx.y, cly = fy.y, clz = fz.y;
   float r2f[kGeomClusterPer];
   float mf = 0.f;
@@ -192,43 +197,33 @@ __global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeom
   mf = warp_max_f(mf);
   if (lane == 0) s_wmax[warp] = mf;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {  // non-negative floats order like their bit patterns
     float m = 0.f;
     for (int w = 0; w < kWarps; ++w) m = fmaxf(m, s_wmax[w]);
-    s_fmax = m;
+    atomicMax(cluster.map_shared_rank(&s_fmax, 0), __float_as_uint(m));
   }
-  cluster.sync();  // every CTA's float maximum is in place; rank 0's centre has been read
-  if (threadIdx.x == 0) {
-    float m = 0.f;
-    for (int r = 0; r < kGeomClusterCTAs; ++r) m = fmaxf(m, *cluster.map_shared_rank(&s_fmax, r));
-    s_thr = m * (1.0f - 4e-6f);
-  }
+  cluster.sync();  // (2) the cluster's float maximum is in rank 0
+  if (threadIdx.x == 0) s_thr = __uint_as_float(*cluster.map_shared_rank(&s_fmax, 0)) * (1.0f - 4e-6f);
   __syncthreads();
   const float thr = s_thr;
-  const double* c0 = cluster.map_shared_rank(s_c, 0);
-  const double cx = c0[0], cy = c0[1], cz = c0[2];
+  const double cx = s_c[0], cy = s_c[1], cz = s_c[2];
+  unsigned long long* dmax0 = cluster.map_shared_rank(&s_dmax, 0);
 #pragma unroll
   for (int k = 0; k < kGeomClusterPer; ++k) {
     if (r2f[k] >= thr) {  // a handful of atoms: their exact squared distance, max through the bits
       const double dx = (double)x[k] - cx, dy = (double)y[k] - cy, dz = (double)z[k] - cz;
-      atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(dx * dx + dy * dy + dz * dz));
+      atomicMax(dmax0, (unsigned long long)__double_as_longlong(dx * dx + dy * dy + dz * dz));
     }
   }
-  cluster.sync();  // every CTA's candidates are in
+  cluster.sync();  // (3) every candidate is in rank 0; after this no CTA reads another's shared memory
   if (rank == 0 && threadIdx.x == 0) {
-    unsigned long long m = 0ull;
-    for (int r = 0; r < kGeomClusterCTAs; ++r) {
-      const unsigned long long v = *cluster.map_shared_rank(&s_dmax, r);
-      m = v > m ? v : m;  // non-negative doubles order like their bit patterns
-    }
     if (j.need_center) {
       geoms[j.geom].c[0] = cx;
       geoms[j.geom].c[1] = cy;
       geoms[j.geom].c[2] = cz;
     }
-    if (j.need_radius) geoms[j.geom].a = sqrt(__longlong_as_double((long long)m));
+    if (j.need_radius) geoms[j.geom].a = sqrt(__longlong_as_double((long long)s_dmax));
   }
-  cluster.sync();  // no CTA exits while its shared memory may still be read
 }
 
 // a1, pass 1: per-tile sums of the coordinates (double); the last CTA of a system to
