@@ -373,7 +373,9 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const MomJob* __r
     int l = (int)sqrtf((float)p);
     while (l * l > p) --l;
     while ((l + 1) * (l + 1) <= p) ++l;
-    job.out[p] = f * ldexp(1.0, e * l) * s;
+    const int ex = e * l;  // a'^l = 2^ex, built from its exponent bits when it is a normal double
+    const double al = (ex >= -1022 && ex <= 1023) ? __longlong_as_double((long long)(ex + 1023) << 52) : ldexp(1.0, ex);
+    job.out[p] = f * al * s;
   }
 }
 
