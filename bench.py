@@ -258,6 +258,13 @@ def run_ours(args, rank, world, dist):
     B = torch.tensor(s.B, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     ctx = tcm.Context(lmax_cap=L, stream=stream)
+    # the moment pass's warp-tile size and grid chosen by the library's autotuner on this batch,
+    # before any timed step (the batching pillar: tiles chosen by timing, not by a constant)
+    from paper_0704_1672_gb300 import autotune
+    tuned = autotune.tune(ctx, [(A, None, None), (B, None, None)], np.zeros(k, int), np.ones(k, int),
+                          np.full(k, L), s.R0, rotB=s.rotB, precision=prec)
+    tiling = {"lmax": L, "atoms_per_lane": tuned.best[L][0], "ctas_per_sm": tuned.best[L][1],
+              "moment_phase_ms_by_candidate": {f"{a}x{c}": round(ms, 5) for (a, c), ms in tuned.timings[L].items()}}
     pb = tcm.pack_batch([(A, None, None), (B, None, None)], np.zeros(k, int), np.ones(k, int), np.full(k, L),
                         s.R0, rotB=s.rotB)
     E = torch.empty(k, dtype=torch.float64, device="cuda")
@@ -440,7 +447,7 @@ def run_ours(args, rank, world, dist):
                 "step_latency_ms": {"p50": p50, "p99": p99},
                 "phase_ms_per_step": phases, "gpu_launches": int(sum(launches.values())),
                 "gpu_launches_per_step": {p: launches[p] / args.steps for p in launches},
-                "roofline": roofline, "clocks": ck, "e2e": e2e, "graph_replay": graph_replay,
+                "roofline": roofline, "tiling": tiling, "clocks": ck, "e2e": e2e, "graph_replay": graph_replay,
                 "rotate_cached": rotate_cached, "pes_grid": pes_grid,
                 "fp64_plain_gpu": fp64_plain, "fp64_batched_gpu": fp64_batched,
                 "cpu_baseline": cpu}

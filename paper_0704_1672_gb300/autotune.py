@@ -20,7 +20,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-DEFAULT_ATOMS_PER_LANE = (16, 32, 64, 128, 256)
+DEFAULT_ATOMS_PER_LANE = (16, 32, 48, 64, 96, 128, 256)
 DEFAULT_CTAS_PER_SM = (1, 2)
 
 
