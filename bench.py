@@ -485,6 +485,7 @@ def run_pes_grid(torch, tcm, prec, n_sm, sm_mhz, stream):
     peak = n_sm * FP64_PER_SM_CLK * sm_mhz * 1e6 / 1e9
     return {"workload": g.name, "points": n, "lmax": list(g.lmax),
             "tcm_energies": n * len(g.lmax), "tcm_ms": t["tcm_energies"], "moments_ms": t["moments"],
+            "item_packing_host_ms": t["item_packing_host"],
             "tcm_energies_per_s": n * len(g.lmax) / (t["tcm_energies"] * 1e-3),
             "direct_ms": t["direct"], "direct_pairs_per_s": pairs / (t["direct"] * 1e-3),
             "direct_roofline": {"bound": "fp64", "kernel": "k_direct", "achieved": achieved, "peak": peak,
