@@ -63,14 +63,22 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
-// Host-side builder of one call's descriptor block (uploaded with a single copy).
+// Layout of one call's descriptor block: add() records where each host array goes (256-byte
+// aligned offsets); upload() copies the arrays straight into a pinned staging buffer and
+// sends the block with a single copy.  The arrays must stay unchanged until upload().
 struct Packer {
-  std::vector<char> buf;
+  struct Span {
+    const void* p;
+    size_t bytes;
+    size_t off;
+  };
+  std::vector<Span> spans;
+  size_t size = 0;
   template <typename T>
   size_t add(const std::vector<T>& v) {
-    const size_t off = align_up(buf.size());
-    buf.resize(off + std::max<size_t>(v.size() * sizeof(T), 1));
-    if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
+    const size_t off = align_up(size);
+    spans.push_back(Span{v.data(), v.size() * sizeof(T), off});
+    size = off + std::max<size_t>(v.size() * sizeof(T), 1);
     return off;
   }
 };
@@ -171,7 +179,7 @@ int dev_ensure(tcm_ctx* c, DevBuf& b, size_t bytes) {
 // Copy the packed descriptors to the device through a pinned slot; returns the
 // device base address in *dbase.
 int upload(tcm_ctx* c, const Packer& pk, char** dbase) {
-  const size_t bytes = std::max<size_t>(pk.buf.size(), 1);
+  const size_t bytes = std::max<size_t>(pk.size, 1);
   TRY(dev_ensure(c, c->desc, bytes));
   Stage& st = c->stage[c->stage_next];
   c->stage_next = (c->stage_next + 1) % kStages;
@@ -190,7 +198,8 @@ int upload(tcm_ctx* c, const Packer& pk, char** dbase) {
     }
     st.cap = nc;
   }
-  std::memcpy(st.host, pk.buf.data(), pk.buf.size());
+  for (const Packer::Span& sp : pk.spans)
+    if (sp.bytes) std::memcpy(static_cast<char*>(st.host) + sp.off, sp.p, sp.bytes);
   TRY_CUDA(cudaMemcpyAsync(c->desc.p, st.host, bytes, cudaMemcpyHostToDevice, c->stream));
   TRY_CUDA(cudaEventRecord(st.ev, c->stream));
   st.pending = true;
