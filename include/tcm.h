@@ -131,7 +131,7 @@ const char* tcm_last_error(void);
 
 /* Phases of the path, for tracing and benchmarks. */
 typedef enum {
-  TCM_PHASE_GEOM = 0,     /* a1: centre and radius */
+  TCM_PHASE_GEOM = 0,     /* a1: centre and radius; set-up of the moment pass (tile list, low-degree sums) */
   TCM_PHASE_MOMENTS = 1,  /* a2: per-atom moment accumulation and per-tile CTA reduction */
   TCM_PHASE_FINALIZE = 2, /* a3: cross-tile reduction in double and normalisation */
   TCM_PHASE_CONTRACT = 3, /* a4 + a5: irregular harmonics at R0 and the two-center contraction */
@@ -154,13 +154,16 @@ int tcm_ctx_set_tiling(tcm_ctx_t ctx, int precision, int atoms_per_lane);
 int tcm_ctx_set_tiling_l(tcm_ctx_t ctx, int precision, int lmax, int atoms_per_lane, int ctas_per_sm);
 int tcm_ctx_get_tiling_l(tcm_ctx_t ctx, int precision, int lmax, int* atoms_per_lane, int* ctas_per_sm);
 
-/* CUDA-graph replay of tcm_energy_batch (on by default).  When two calls in a row have the
- * same launch shapes and buffers (item count, job and tile counts per degree, output pointers),
- * the second captures its launch sequence into a graph and later calls with that shape replay
- * it instead of launching kernel by kernel; the descriptors are still uploaded per call, so
- * the orientations, pairs and systems may change.  Calls of another shape launch directly.
- * Off while phase timing is on. */
-int tcm_ctx_set_graphs(tcm_ctx_t ctx, int enable);
+/* CUDA-graph replay of tcm_energy_batch.  A call's launch sequence (tile list, centres and
+ * radii, low-degree sums, the moment pass -- one launch over all degrees in TCM_MIXED, one per
+ * degree in TCM_FP64 --, finalisation, contraction) is captured into a graph and replayed by
+ * later calls with the same launch shapes and buffers (item count, job and tile counts,
+ * output pointers); the descriptors are uploaded per call, so the orientations, pairs and
+ * systems may change.  mode 0: launch kernel by kernel; mode 1 (default): capture a shape
+ * when two calls in a row have it (a stream of changing shapes launches directly instead of
+ * paying a capture per call); mode 2: capture every new shape on its first call.  Off while
+ * phase timing is on. */
+int tcm_ctx_set_graphs(tcm_ctx_t ctx, int mode);
 
 /* Number of graph captures and graph launches so far (either pointer may be NULL). */
 int tcm_ctx_graph_stats(tcm_ctx_t ctx, int64_t* captures, int64_t* launches);
@@ -258,8 +261,10 @@ int tcm_direct(tcm_ctx_t ctx, const tcm_system* A, const tcm_system* B, const do
 int tcm_direct_batch(tcm_ctx_t ctx, const tcm_system* A, const tcm_system* B, int64_t n_items,
                      const double* rotB, const double* R0, double* E);
 
-/* Largest atom count accepted by tcm_moments_noalloc. */
+/* Largest atom count accepted by tcm_moments_noalloc, and the size in bytes of the fixed
+ * device array it works in (about 0.70 MiB). */
 #define TCM_NOALLOC_MAX_ATOMS 262144
+#define TCM_NOALLOC_SCRATCH_BYTES 739072
 
 /* The paper has no counterpart to this call; it exists for callers that cannot allocate
  * device memory.  Examples: code that must not let cudaMalloc/cudaFree synchronise the
@@ -267,24 +272,24 @@ int tcm_direct_batch(tcm_ctx_t ctx, const tcm_system* A, const tcm_system* B, in
  * memory, and plug-ins that are not allowed to create allocations.  A context
  * (tcm_ctx_create) allocates, so such callers use this instead of tcm_moments.
  *
- * It computes the same moments as tcm_moments (Eq. (multipole)) of system s, optionally
- * rotated by rot (row-major host double[9], NULL = identity), into q_out (device,
- * (lmax+1)^2 packed doubles, 16-byte aligned).  If center_radius_out is not NULL it
- * receives (device, 4 doubles) the centre and radius used: the given ones, or the
- * centroid and radius computed on the device when s has no centre or no radius.
- * precision is TCM_FP64 or TCM_MIXED.  The work is queued on cuda_stream (a
- * cudaStream_t; NULL = legacy default stream) and the call returns without waiting.
+ * It computes the same moments as tcm_moments, of system s, optionally rotated by rot
+ * (row-major host double[9], NULL = identity), into q_out (device, (lmax+1)^2 packed
+ * doubles, 16-byte aligned).  If center_radius_out is not NULL it receives (device,
+ * 4 doubles) the centre and radius used: the given ones, or the centroid and radius
+ * computed on the device when s has no centre or no radius.  precision is TCM_FP64 or
+ * TCM_MIXED.  The work is queued on cuda_stream (a cudaStream_t; NULL = legacy default
+ * stream) and the call returns without waiting.
  *
- * Memory: instead of allocating, the call uses one fixed scratch array of about 0.5 MiB
- * defined in the library as device memory.  Every GPU that loads the library holds its
- * own copy until the process exits.  All calls on a GPU share that array and it keeps
- * the last call's contents (each call rewrites what it reads), so calls whose work
- * overlaps on the GPU race on it: serialise them (one stream, or events).
+ * Memory: instead of allocating, the call uses one fixed scratch array of
+ * TCM_NOALLOC_SCRATCH_BYTES bytes defined in the library as device memory.  Every GPU that
+ * loads the library holds its own copy until the process exits.  All calls on a GPU share
+ * that array and it keeps the last call's contents (each call rewrites what it reads), so
+ * calls whose work overlaps on the GPU race on it: serialise them (one stream, or events).
  * Limits: 0 <= s->n <= TCM_NOALLOC_MAX_ATOMS and 0 <= lmax <= TCM_LMAX_MAX; larger
  * requests return TCM_EINVAL with a message.
  * Set-up: the first call on each GPU (with that GPU current) looks up the scratch
- * address and copies the coefficient tables into it, synchronously; make that first
- * call before any stream capture.
+ * address, copies the coefficient tables into it and waits for the device to finish;
+ * make that first call before any stream capture.
  * Errors are reported as by the other calls (status code, tcm_last_error()). */
 int tcm_moments_noalloc(const tcm_system* s, const double* rot, int lmax, int precision, double* q_out,
                         double* center_radius_out, void* cuda_stream);

@@ -340,6 +340,50 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom_radius(const GeomJob* __r
   }
 }
 
+// Degrees l <= kLowLmax of one job from its system's low-degree sums (k_lowmom): the tile rows
+// are added in tile order (double), the Cartesian sums are rotated by the job's rotation R
+// (P' = R P, T' = R T R^T, p = R d) and turned into the packed Q_lm, l <= 2, with
+//   Q_00 = S,  Q_10 = P'_z,  Q_11 = -(P'_x + i P'_y)/sqrt(2),
+//   Q_20 = T'_zz - (T'_xx + T'_yy)/2,  Q_21 = -sqrt(3/2) (T'_xz + i T'_yz),
+//   Q_22 = sqrt(3/8) (T'_xx - T'_yy + 2 i T'_xy),
+// the regular solid harmonics r^l sqrt(4 pi/(2l+1)) Y_lm of Eq. (multipole) written out in x, y, z.
+constexpr int kLowComps = (kLowLmax + 1) * (kLowLmax + 1);
+__device__ void low_degrees(const MomJob& job, const double* __restrict__ lowpart, double* s_low) {
+  if (threadIdx.x < kLowSums) {
+    const double* p = lowpart + (long long)job.low_base * kLowSums + threadIdx.x;
+    double t = 0.0;
+    for (int r = 0; r < job.low_tiles; ++r) t += __ldcg(p + (long long)r * kLowSums);
+    s_low[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double* R = job.rot;
+  const double P[3] = {s_low[1], s_low[2], s_low[3]};
+  const double T[3][3] = {{s_low[4], s_low[5], s_low[6]}, {s_low[5], s_low[7], s_low[8]}, {s_low[6], s_low[8], s_low[9]}};
+  double Pr[3], RT[3][3], Tr[3][3];
+  for (int a = 0; a < 3; ++a) {
+    Pr[a] = R[3 * a] * P[0] + R[3 * a + 1] * P[1] + R[3 * a + 2] * P[2];
+    for (int b = 0; b < 3; ++b) RT[a][b] = R[3 * a] * T[0][b] + R[3 * a + 1] * T[1][b] + R[3 * a + 2] * T[2][b];
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Tr[a][b] = RT[a][0] * R[3 * b] + RT[a][1] * R[3 * b + 1] + RT[a][2] * R[3 * b + 2];
+  const double r2 = 0.70710678118654752440, s32 = 1.22474487139158904910, s38 = 0.61237243569579452455;
+  double* o = job.out;
+  o[0] = s_low[0];
+  if (job.L >= 1) {
+    o[1] = Pr[2];
+    o[2] = -r2 * Pr[0];
+    o[3] = -r2 * Pr[1];
+  }
+  if (job.L >= 2) {
+    o[4] = Tr[2][2] - 0.5 * (Tr[0][0] + Tr[1][1]);
+    o[5] = -s32 * Tr[0][2];
+    o[6] = -s32 * Tr[1][2];
+    o[7] = s38 * (Tr[0][0] - Tr[1][1]);
+    o[8] = s32 * Tr[0][1];
+  }
+}
+
 // a3: one CTA per moment job.  Threads walk the (chunk, slot) entries of the job's partial
 // rows in memory order (coalesced), sum each over the job's tiles in tile order (double) and
 // write F_lm a'^l times the sum to the packed component the slot holds.  The map entry, its
@@ -351,7 +395,9 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const MomJob* __r
                                                                const SysGeom* __restrict__ geoms,
                                                                const int* __restrict__ imap,
                                                                const double* __restrict__ fmap,
-                                                               const int* __restrict__ imap_off, int kmax) {
+                                                               const int* __restrict__ imap_off, int kmax,
+                                                               const double* __restrict__ lowpart) {
+  __shared__ double s_low[kLowSums];
   pdl_wait();  // the moment kernels' partial rows are complete
   const MomJob& job = jobs[blockIdx.x];
   const int L = job.L;
@@ -375,8 +421,10 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const MomJob* __r
     while ((l + 1) * (l + 1) <= p) ++l;
     const int ex = e * l;  // a'^l = 2^ex, built from its exponent bits when it is a normal double
     const double al = (ex >= -1022 && ex <= 1023) ? __longlong_as_double((long long)(ex + 1023) << 52) : ldexp(1.0, ex);
+    if (job.low_tiles > 0 && p < kLowComps) continue;  // written from the low-degree sums below
     job.out[p] = f * al * s;
   }
+  if (job.low_tiles > 0) low_degrees(job, lowpart, s_low);
 }
 
 // a4 + a5: one CTA per energy, in the frame where R0hat is the z axis.
@@ -960,10 +1008,10 @@ int geom_launches(int n_cluster_jobs, int n_gtiles) {
 }
 
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms, const int* imap,
-                    const double* fmap, const int* imap_off, int kmax, cudaStream_t s) {
+                    const double* fmap, const int* imap_off, int kmax, const double* lowpart, cudaStream_t s) {
   if (n_jobs <= 0) return 0;
   return launch_pdl(k_finalize, dim3(n_jobs), dim3(kFinalizeThreads), 0, s, jobs, partials, geoms, imap, fmap,
-                    imap_off, kmax) == cudaSuccess
+                    imap_off, kmax, lowpart) == cudaSuccess
              ? 0
              : -1;
 }

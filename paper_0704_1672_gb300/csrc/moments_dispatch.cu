@@ -24,7 +24,6 @@ constexpr auto make_table(std::integer_sequence<int, Ls...>) {
   return std::array<LaunchFn, sizeof...(Ls)>{{&launch_moments_t<T, Ls>...}};
 }
 
-const auto kF32 = make_table<float>(std::make_integer_sequence<int, kLmaxMax + 1>{});
 const auto kF64 = make_table<double>(std::make_integer_sequence<int, kLmaxMax + 1>{});
 
 constexpr int stride_of(int precision) { return precision == TCM_FP64 ? 34 : 36; }
@@ -38,6 +37,7 @@ int moments_nchunks(int precision, int L) { return plan_nch(L, moments_kmax(prec
 
 int moments_smem_bytes(int precision, int L) {
   const int kmax = moments_kmax(precision);
+  if (precision != TCM_FP64) return (kThreads / 32) * kmax * stride_of(precision) * size_of(precision);  // any degree
   const int nch = plan_nch(L, kmax);
   int mx = 0;
   for (int c = 0; c < nch; ++c) {
@@ -110,8 +110,33 @@ void finalize_tables(std::vector<int>& imap_off, std::vector<int>& imap, std::ve
 int launch_moments(int precision, int L, const MomJob* jobs, const MomTile* tiles, int n_tiles, int* counter,
                    const SysGeom* geoms, double* partials, int grid, cudaStream_t s) {
   if (L < 0 || L > kLmaxMax || n_tiles <= 0) return n_tiles == 0 ? 0 : -1;
-  const LaunchFn f = precision == TCM_FP64 ? kF64[L] : kF32[L];
-  return f(jobs, tiles, n_tiles, counter, geoms, partials, grid, s);
+  if (precision != TCM_FP64)  // the float kernel takes tiles of any degree
+    return launch_moments_t<float, -1>(jobs, tiles, n_tiles, counter, geoms, partials, grid, s);
+  return kF64[L](jobs, tiles, n_tiles, counter, geoms, partials, grid, s);
+}
+
+namespace {
+__global__ void __launch_bounds__(256) k_expand_tiles(const MomGroup* __restrict__ groups, int n_groups,
+                                                      const MomJob* __restrict__ jobs, MomTile* __restrict__ tiles) {
+  const int g = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (g >= n_groups) return;
+  const MomGroup gr = groups[g];
+  const MomJob& j = jobs[gr.job];
+  const int row = j.tile_base + gr.chunk * j.tiles_per_chunk;
+  for (int t = threadIdx.x & 31; t < gr.n; t += 32) tiles[gr.first + t] = MomTile{gr.job, gr.chunk, t, row + t};
+}
+}  // namespace
+
+int launch_expand_tiles(const MomGroup* groups, int n_groups, const MomJob* jobs, MomTile* tiles, cudaStream_t s) {
+  if (n_groups <= 0) return 0;
+  k_expand_tiles<<<(n_groups + 7) / 8, 256, 0, s>>>(groups, n_groups, jobs, tiles);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_moments_any(const MomJob* jobs, const MomTile* tiles, int n_tiles, int* counter, const SysGeom* geoms,
+                       double* partials, int grid, cudaStream_t s) {
+  if (n_tiles <= 0) return 0;
+  return launch_moments_t<float, -1>(jobs, tiles, n_tiles, counter, geoms, partials, grid, s);
 }
 
 }  // namespace tcm

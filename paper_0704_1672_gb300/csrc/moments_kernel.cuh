@@ -336,13 +336,16 @@ __device__ __forceinline__ void setup(T d0, T d1, T d2, const Xform<T>& xf, T& u
   rho = r2 * rinv;
 }
 
-__device__ __forceinline__ float row_sum32(const float* p) {
+// Sum of a 32-entry row of the transpose buffer in double, in a fixed tree order.  The float
+// lane sums are converted exactly; a float tree would add about 2 x 2^-24 of the row's
+// magnitude.  The additions go to the FP64 pipe, which the float recurrences leave idle.
+__device__ __forceinline__ double row_sum32(const float* p) {
   const float4* v = reinterpret_cast<const float4*>(p);
-  float s[8];
+  double s[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const float4 w = v[k];
-    s[k] = (w.x + w.y) + (w.z + w.w);
+    s[k] = ((double)w.x + (double)w.y) + ((double)w.z + (double)w.w);
   }
   return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
@@ -361,7 +364,7 @@ __device__ __forceinline__ double row_sum32(const double* p) {
 // Warp reduction of the per-lane accumulators into one double row `out[0..NACC)` (the
 // column-0 reals first, then the complex pairs, in slot order).  The warp transposes its
 // 32 x NACC block through its own shared-memory region and every lane tree-sums whole rows
-// (fixed order), converts them to double and stores them.  No CTA barrier is involved.
+// in double (fixed order) and stores them.  No CTA barrier is involved.
 template <typename T, int L, int M0, int M1>
 __device__ __forceinline__ void warp_reduce_store(const Regs<T, L, M0, M1>& s, T* wb, double* out) {
   using R = Regs<T, L, M0, M1>;
@@ -379,7 +382,7 @@ __device__ __forceinline__ void warp_reduce_store(const Regs<T, L, M0, M1>& s, T
 #pragma unroll
   for (int rr = 0; rr < (NACC + 31) / 32; ++rr) {
     const int r = lane + 32 * rr;
-    if (r < NACC) out[r] = (double)row_sum32(wb + r * S);
+    if (r < NACC) out[r] = row_sum32(wb + r * S);
   }
   if constexpr (M0 == 0 && sizeof(T) == 4) {  // slot 0 is Q_00: exact lane pairs summed in double
     double v = (double)s.q00 + (double)s.q00e;
@@ -477,17 +480,33 @@ __device__ __forceinline__ void run_tile(const MomTile& tile, const MomJob* __re
   }
 }
 
+// Code of the tile's own degree: a chain of compile-time degrees, one compare per degree.
+template <typename T, int L>
+__device__ __forceinline__ void run_tile_any(int Lt, const MomTile& tile, const MomJob* __restrict__ jobs,
+                                             const SysGeom* __restrict__ geoms, double* __restrict__ partials, T* wb,
+                                             Xform<T>* xf_w) {
+  if constexpr (L <= kLmaxMax) {
+    if (Lt == L)
+      run_tile<T, L, 0>(tile, jobs, geoms, partials, wb, xf_w);
+    else
+      run_tile_any<T, L + 1>(Lt, tile, jobs, geoms, partials, wb, xf_w);
+  }
+}
+
 // Persistent kernel: every warp pulls warp tiles from the shared counter until none are
 // left, so warps never wait for each other.  counter[0] is the work counter and counter[32]
-// the exit ticket, both zero on entry and left zero on exit.
-template <typename T, int L>
+// the exit ticket, both zero on entry and left zero on exit.  LK >= 0: every tile has degree
+// LK; LK < 0: the tiles may have any degree (one launch for a whole uneven batch), each runs
+// the code of its job's degree.
+template <typename T, int LK>
 __global__ void __launch_bounds__(kThreads, TCM_MOMENT_CTAS_PER_SM)
     k_moments(const MomJob* __restrict__ jobs, const MomTile* __restrict__ tiles, int n_tiles,
               int* __restrict__ counter, const SysGeom* __restrict__ geoms, double* __restrict__ partials) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Xform<T> s_xf[kThreads / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* wb = reinterpret_cast<T*>(smem) + warp * (Plan<T, L>::max_nacc() * MomTraits<T>::stride);
+  constexpr int kRow = LK >= 0 ? Plan<T, (LK >= 0 ? LK : 0)>::max_nacc() : MomTraits<T>::kmax;
+  T* wb = reinterpret_cast<T*>(smem) + warp * (kRow * MomTraits<T>::stride);
   pdl_wait();  // the centres and radii of the launch before are complete
   for (;;) {
     int ti = 0;
@@ -495,7 +514,10 @@ __global__ void __launch_bounds__(kThreads, TCM_MOMENT_CTAS_PER_SM)
     ti = __shfl_sync(0xffffffffu, ti, 0);
     if (ti >= n_tiles) break;
     const MomTile tile = tiles[ti];
-    run_tile<T, L, 0>(tile, jobs, geoms, partials, wb, &s_xf[warp]);
+    if constexpr (LK >= 0)
+      run_tile<T, LK, 0>(tile, jobs, geoms, partials, wb, &s_xf[warp]);
+    else
+      run_tile_any<T, 0>(jobs[tile.job].L, tile, jobs, geoms, partials, wb, &s_xf[warp]);
   }
   // the last warp out leaves the work counter and its own ticket at zero for the next launch
   if (lane == 0 && atomicAdd(counter + 32, 1) == (int)(gridDim.x * (kThreads / 32)) - 1) {
@@ -504,15 +526,16 @@ __global__ void __launch_bounds__(kThreads, TCM_MOMENT_CTAS_PER_SM)
   }
 }
 
-template <typename T, int L>
+template <typename T, int LK>
 int launch_moments_t(const MomJob* jobs, const MomTile* tiles, int n_tiles, int* counter,
                      const SysGeom* geoms, double* partials, int grid, cudaStream_t s) {
-  constexpr int smem = Plan<T, L>::smem_bytes();
+  constexpr int smem = (kThreads / 32) * (LK >= 0 ? Plan<T, (LK >= 0 ? LK : 0)>::max_nacc() : MomTraits<T>::kmax) *
+                       MomTraits<T>::stride * (int)sizeof(T);
   if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(k_moments<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_moments<T, LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return -1;
   }
-  return launch_pdl(k_moments<T, L>, dim3(grid), dim3(kThreads), smem, s, jobs, tiles, n_tiles, counter, geoms,
+  return launch_pdl(k_moments<T, LK>, dim3(grid), dim3(kThreads), smem, s, jobs, tiles, n_tiles, counter, geoms,
                     partials) == cudaSuccess
              ? 0
              : -1;

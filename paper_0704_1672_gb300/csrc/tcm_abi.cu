@@ -98,7 +98,7 @@ struct tcm_ctx {
   int* d_imap = nullptr;      // (chunk, slot) -> packed component, both precisions
   int* d_imap_off = nullptr;  // [precision][L] offsets into d_imap
   // scratch
-  DevBuf desc, partials, gpart, counters, moms, escr, dpart;
+  DevBuf desc, partials, gpart, counters, moms, escr, dpart, lowp, tiles;
   Stage stage[kStages];
   int stage_next = 0;
   void* pinned_small = nullptr;  // 256 B for small device->host reads
@@ -117,7 +117,7 @@ struct tcm_ctx {
   int64_t launches[TCM_NPHASES] = {};
   // CUDA-graph replay of the batched launch sequence
   bool rotate_cached = false;  // rotated B sides from the moment cache by Wigner rotation
-  bool graphs = true;
+  int graphs = 1;  // 0: launch directly; 1: capture a shape seen twice in a row; 2: capture every new shape
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<long long> gkey, gkey_seen;
@@ -235,11 +235,43 @@ struct JobKey {
 
 struct Plan {
   std::vector<MomJob> jobs;
-  std::vector<MomTile> tiles;      // grouped by L, each group sorted by cost (largest first)
-  int tile_begin[kLmaxMax + 2] = {};  // tiles of L are [tile_begin[L], tile_begin[L+1])
+  std::vector<MomGroup> groups;    // (job, chunk) groups, largest tiles first; expanded on the device
+  int n_tiles = 0;
+  // FP64 (one launch per degree): the tiles of L are [tile_begin[L], tile_begin[L+1]); mixed
+  // (one launch over all degrees): every tile is in [0, n_tiles)
+  int tile_begin[kLmaxMax + 2] = {};
   int n_tile_ids = 0;
   size_t moms_doubles = 0;
+  std::vector<LowJob> ljobs;       // mixed precision: one low-degree pass per system with a job
+  std::vector<LowTile> ltiles;
 };
+
+// Mixed precision: one low-degree pass (k_lowmom) per system that has a computed moment job;
+// every job of that system takes its degrees l <= 2 from it.
+void plan_low(const tcm_system* systems, Plan& P) {
+  std::map<int, int> low_of;
+  int rows = 0;
+  for (MomJob& j : P.jobs) {
+    auto it = low_of.find(j.geom);
+    if (it == low_of.end()) {
+      const tcm_system& sy = systems[j.geom];
+      LowJob lj{};
+      lj.xyzq = sy.xyzq;
+      lj.n = sy.n;
+      lj.dtype = sy.dtype;
+      lj.geom = j.geom;
+      lj.tile_base = rows;
+      lj.n_tiles = (int)std::max<long long>(1, (sy.n + kLowTileAtoms - 1) / kLowTileAtoms);
+      for (int t = 0; t < lj.n_tiles; ++t) P.ltiles.push_back(LowTile{(int)P.ljobs.size(), t});
+      rows += lj.n_tiles;
+      it = low_of.emplace(j.geom, (int)P.ljobs.size()).first;
+      P.ljobs.push_back(lj);
+    }
+    const LowJob& lj = P.ljobs[it->second];
+    j.low_base = lj.tile_base;
+    j.low_tiles = lj.n_tiles;
+  }
+}
 
 void plan_job(tcm_ctx* c, int precision, MomJob& j, int& next_id) {
   const int nch = moments_nchunks(precision, j.L);
@@ -259,33 +291,39 @@ double chunk_cost(int precision, int L, int chunk) {
   return 1.25 * chunk_off(L, m0, m1) + 4.0 * m0 + 30.0;
 }
 
-// Tiles grouped by L; within a degree, the (job, chunk) groups in decreasing order of their
-// tiles' cost (largest first, so the persistent warps finish together), each group's tiles in
-// order.  Sorting groups rather than tiles keeps the host cost O(tiles + groups log groups).
+// The (job, chunk) groups in decreasing order of their tiles' cost (largest first, so the
+// persistent warps finish together).  FP64: grouped by degree (one launch per degree); mixed:
+// one order over all degrees (one launch).  The tiles themselves are written on the device
+// (k_expand_tiles), so the host work is O(groups log groups).
 void build_tiles(int precision, Plan& P) {
   struct Group {
     double cost;
-    int job, chunk;
+    int L, job, chunk;
   };
-  std::vector<std::vector<Group>> byL(kLmaxMax + 1);
+  std::vector<Group> v;
   for (int ji = 0; ji < (int)P.jobs.size(); ++ji) {
     const MomJob& j = P.jobs[ji];
     const int nch = moments_nchunks(precision, j.L);
-    for (int ch = 0; ch < nch; ++ch)
-      byL[j.L].push_back({chunk_cost(precision, j.L, ch) * (double)j.atoms_per_tile, ji, ch});
+    for (int ch = 0; ch < nch; ++ch) v.push_back({chunk_cost(precision, j.L, ch) * (double)j.atoms_per_tile, j.L, ji, ch});
   }
-  P.tiles.clear();
+  const bool by_degree = precision == TCM_FP64;
+  std::stable_sort(v.begin(), v.end(), [by_degree](const Group& a, const Group& b) {
+    if (by_degree && a.L != b.L) return a.L < b.L;
+    return a.cost > b.cost;
+  });
+  P.groups.clear();
+  P.groups.reserve(v.size());
+  int first = 0, gi = 0;
   for (int L = 0; L <= kLmaxMax; ++L) {
-    P.tile_begin[L] = (int)P.tiles.size();
-    auto& v = byL[L];
-    std::stable_sort(v.begin(), v.end(), [](const Group& a, const Group& b) { return a.cost > b.cost; });
-    for (const Group& g : v) {
-      const MomJob& j = P.jobs[g.job];
-      for (int t = 0; t < j.tiles_per_chunk; ++t)
-        P.tiles.push_back(MomTile{g.job, g.chunk, t, j.tile_base + g.chunk * j.tiles_per_chunk + t});
+    P.tile_begin[L] = first;
+    for (; gi < (int)v.size() && (!by_degree || v[gi].L == L); ++gi) {
+      const int n = P.jobs[v[gi].job].tiles_per_chunk;
+      P.groups.push_back(MomGroup{v[gi].job, v[gi].chunk, n, first});
+      first += n;
     }
   }
-  P.tile_begin[kLmaxMax + 1] = (int)P.tiles.size();
+  P.tile_begin[kLmaxMax + 1] = first;
+  P.n_tiles = first;
 }
 
 // Queue the moment pass (step a2/a3) for every job of the plan.
@@ -293,6 +331,8 @@ void build_tiles(int precision, Plan& P) {
 // on entry and left zero by every launch, so they are cleared once, when allocated.
 int ensure_moment_buffers(tcm_ctx* c, int precision, const Plan& P) {
   TRY(dev_ensure(c, c->partials, (size_t)std::max(P.n_tile_ids, 1) * moments_kmax(precision) * sizeof(double)));
+  TRY(dev_ensure(c, c->tiles, (size_t)std::max(P.n_tiles, 1) * sizeof(MomTile)));
+  TRY(dev_ensure(c, c->lowp, std::max<size_t>(P.ltiles.size(), 1) * kLowSums * sizeof(double)));
   void* before = c->counters.p;
   TRY(dev_ensure(c, c->counters, 64 * sizeof(int)));
   if (c->counters.p != before) {
@@ -301,29 +341,67 @@ int ensure_moment_buffers(tcm_ctx* c, int precision, const Plan& P) {
   return TCM_OK;
 }
 
-int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, const MomTile* d_tiles,
-                const SysGeom* d_geoms, cudaStream_t st) {
+// Counter slots of the moment kernels (zero on entry, left zero): [L] and [32 + L] for the
+// per-degree FP64 launches, [kAnyCounter] and [32 + kAnyCounter] for the mixed launch over all
+// degrees.
+constexpr int kAnyCounter = kLmaxMax + 1;
+
+// The tile list of the plan, written on the device from its groups (first launch of a call: it
+// depends on nothing queued before it).
+int run_expand(tcm_ctx* c, const Plan& P, const MomJob* d_jobs, const MomGroup* d_groups, cudaStream_t st) {
+  if (P.groups.empty()) return TCM_OK;
+  PhaseScope ps(c, TCM_PHASE_GEOM, 1);
+  TRY_LAUNCH(launch_expand_tiles(d_groups, (int)P.groups.size(), d_jobs, static_cast<MomTile*>(c->tiles.p), st));
+  return TCM_OK;
+}
+
+int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, const SysGeom* d_geoms,
+                cudaStream_t st) {
   const int kmax = moments_kmax(precision);
   TRY(ensure_moment_buffers(c, precision, P));
   int* counters = static_cast<int*>(c->counters.p);
   double* parts = static_cast<double*>(c->partials.p);
-  int ngroups = 0;
-  for (int L = 0; L <= kLmaxMax; ++L) ngroups += P.tile_begin[L + 1] > P.tile_begin[L];
-  {
+  MomTile* tiles = static_cast<MomTile*>(c->tiles.p);
+  if (precision == TCM_FP64) {
+    int ngroups = 0;
+    for (int L = 0; L <= kLmaxMax; ++L) ngroups += P.tile_begin[L + 1] > P.tile_begin[L];
     PhaseScope ps(c, TCM_PHASE_MOMENTS, ngroups);
     for (int L = 0; L <= kLmaxMax; ++L) {
       const int b = P.tile_begin[L], e = P.tile_begin[L + 1];
       if (e == b) continue;
-      const int cps = c->ctas_per_sm[precision == TCM_FP64 ? 0 : 1][L];
+      const int cps = c->ctas_per_sm[0][L];
       const int grid = std::min((e - b + kThreads / 32 - 1) / (kThreads / 32), cps * c->num_sms);  // warp tiles
-      TRY_LAUNCH(launch_moments(precision, L, d_jobs, d_tiles + b, e - b, counters + L, d_geoms, parts, grid, st));
+      TRY_LAUNCH(launch_moments(precision, L, d_jobs, tiles + b, e - b, counters + L, d_geoms, parts, grid, st));
     }
+  } else if (P.n_tiles > 0) {
+    int cps = 1;  // the grid of the single launch: the largest CTAs per SM of the degrees present
+    for (const MomJob& j : P.jobs) cps = std::max(cps, c->ctas_per_sm[1][j.L]);
+    PhaseScope ps(c, TCM_PHASE_MOMENTS, 1);
+    const int grid = std::min((P.n_tiles + kThreads / 32 - 1) / (kThreads / 32), cps * c->num_sms);
+    TRY_LAUNCH(launch_moments_any(d_jobs, tiles, P.n_tiles, counters + kAnyCounter, d_geoms, parts, grid, st));
   }
   {
     PhaseScope ps(c, TCM_PHASE_FINALIZE, 1);
     TRY_LAUNCH(launch_finalize(d_jobs, (int)P.jobs.size(), parts, d_geoms, c->d_imap, c->d_fmap,
-                               c->d_imap_off + (precision == TCM_FP64 ? 0 : kLmaxMax + 2), kmax, st));
+                               c->d_imap_off + (precision == TCM_FP64 ? 0 : kLmaxMax + 2), kmax,
+                               static_cast<double*>(c->lowp.p), st));
   }
+  return TCM_OK;
+}
+
+// Moment-phase launches of a plan (for the launch counts of a replayed graph).
+int moment_launches(int precision, const Plan& P) {
+  if (precision != TCM_FP64) return P.n_tiles > 0 ? 1 : 0;
+  int n = 0;
+  for (int L = 0; L <= kLmaxMax; ++L) n += P.tile_begin[L + 1] > P.tile_begin[L];
+  return n;
+}
+
+// The low-degree pass of the mixed path (after step a1: it needs the centres).
+int run_low(tcm_ctx* c, const Plan& P, const LowJob* d_lj, const LowTile* d_lt, const SysGeom* d_geo, cudaStream_t st) {
+  if (P.ltiles.empty()) return TCM_OK;
+  PhaseScope ps(c, TCM_PHASE_GEOM, 1);
+  TRY_LAUNCH(launch_lowmom(d_lj, d_lt, (int)P.ltiles.size(), d_geo, static_cast<double*>(c->lowp.p), st));
   return TCM_OK;
 }
 
@@ -404,7 +482,8 @@ void free_ctx(tcm_ctx* c) {
   cudaFree(c->d_ztab);
   cudaFree(c->d_imap);
   cudaFree(c->d_imap_off);
-  for (DevBuf* b : {&c->desc, &c->partials, &c->gpart, &c->counters, &c->moms, &c->escr, &c->dpart}) cudaFree(b->p);
+  for (DevBuf* b : {&c->desc, &c->partials, &c->gpart, &c->counters, &c->moms, &c->escr, &c->dpart, &c->lowp, &c->tiles})
+    cudaFree(b->p);
   for (auto& st : c->stage) {
     if (st.host) cudaFreeHost(st.host);
     if (st.ev) cudaEventDestroy(st.ev);
@@ -519,9 +598,10 @@ int tcm_ctx_get_tiling_l(tcm_ctx_t c, int precision, int lmax, int* atoms_per_la
   return TCM_OK;
 }
 
-int tcm_ctx_set_graphs(tcm_ctx_t c, int enable) {
+int tcm_ctx_set_graphs(tcm_ctx_t c, int mode) {
   TRY(check_ctx(c));
-  c->graphs = enable != 0;
+  if (mode < 0 || mode > 2) return set_err(TCM_EINVAL, "tcm_ctx_set_graphs: mode %d outside [0, 2]", mode);
+  c->graphs = mode;
   return TCM_OK;
 }
 
@@ -614,17 +694,20 @@ int tcm_moments(tcm_ctx_t c, const tcm_system* s, const double* rot, int lmax, i
   P.jobs.push_back(j);
   P.n_tile_ids = next;
   build_tiles(precision, P);
+  if (precision == TCM_MIXED) plan_low(s, P);
   std::vector<char> used(1, 1);
   std::vector<GeomJob> gjobs;
   std::vector<GeomTile> gtiles;
   const int ngt = add_geom_jobs(s, 1, used, gjobs, gtiles);
   std::vector<SysGeom> geoms{host_geom(*s)};
   Packer pk;
-  const size_t o_geo = pk.add(geoms), o_job = pk.add(P.jobs), o_tile = pk.add(P.tiles), o_gj = pk.add(gjobs),
-               o_gt = pk.add(gtiles);
+  const size_t o_geo = pk.add(geoms), o_job = pk.add(P.jobs), o_tile = pk.add(P.groups), o_gj = pk.add(gjobs),
+               o_gt = pk.add(gtiles), o_lj = pk.add(P.ljobs), o_lt = pk.add(P.ltiles);
+  TRY(ensure_moment_buffers(c, precision, P));
   char* base = nullptr;
   TRY(upload(c, pk, &base));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
+  TRY(run_expand(c, P, reinterpret_cast<MomJob*>(base + o_job), reinterpret_cast<MomGroup*>(base + o_tile), c->stream));
   if (!gjobs.empty()) {
     TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
     if (ngt > 0)  // the tiled kernels take tickets
@@ -634,8 +717,8 @@ int tcm_moments(tcm_ctx_t c, const tcm_system* s, const double* rot, int lmax, i
                            reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
                            static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
   }
-  TRY(run_moments(c, precision, P, reinterpret_cast<MomJob*>(base + o_job), reinterpret_cast<MomTile*>(base + o_tile),
-                  d_geo, c->stream));
+  TRY(run_low(c, P, reinterpret_cast<LowJob*>(base + o_lj), reinterpret_cast<LowTile*>(base + o_lt), d_geo, c->stream));
+  TRY(run_moments(c, precision, P, reinterpret_cast<MomJob*>(base + o_job), d_geo, c->stream));
   out->lmax = lmax;
   if (!gjobs.empty()) {
     TRY_CUDA(cudaMemcpyAsync(c->pinned_small, d_geo, sizeof(SysGeom), cudaMemcpyDeviceToHost, c->stream));
@@ -855,6 +938,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   TRY(dev_ensure(c, c->moms, std::max<size_t>(moff, 1) * sizeof(double)));
   for (size_t ji = 0; ji < P.jobs.size(); ++ji) P.jobs[ji].out = static_cast<double*>(c->moms.p) + job_moff[ji];
   build_tiles(precision, P);
+  if (precision == TCM_MIXED) plan_low(systems, P);
   // cached sides follow the computed jobs in the descriptor array (not finalised)
   const int n_computed = (int)P.jobs.size();
   for (auto& d : pd) {
@@ -871,8 +955,9 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   std::vector<SysGeom> geoms(std::max(n_systems, 1));
   for (int s = 0; s < n_systems; ++s) geoms[s] = host_geom(systems[s]);
   Packer pk;
-  const size_t o_geo = pk.add(geoms), o_job = pk.add(all_jobs), o_tile = pk.add(P.tiles), o_gj = pk.add(gjobs),
-               o_gt = pk.add(gtiles), o_it = pk.add(pd), o_rot = pk.add(rots);
+  const size_t o_geo = pk.add(geoms), o_job = pk.add(all_jobs), o_tile = pk.add(P.groups), o_gj = pk.add(gjobs),
+               o_gt = pk.add(gtiles), o_it = pk.add(pd), o_rot = pk.add(rots), o_lj = pk.add(P.ljobs),
+               o_lt = pk.add(P.ltiles);
   // every buffer the launches touch is sized before anything is queued (no reallocation
   // may happen while a graph is being captured)
   if (!gjobs.empty())
@@ -882,9 +967,8 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   TRY(upload(c, pk, &base));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   const MomJob* d_jobs = reinterpret_cast<MomJob*>(base + o_job);
-  int ngroups = 0;
-  for (int L = 0; L <= kLmaxMax; ++L) ngroups += P.tile_begin[L + 1] > P.tile_begin[L];
   auto enqueue = [&](cudaStream_t st) -> int {
+    TRY(run_expand(c, P, d_jobs, reinterpret_cast<MomGroup*>(base + o_tile), st));
     if (!gjobs.empty()) {
       if (ngt > 0)  // the tiled kernels take tickets
         TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), st));
@@ -893,7 +977,8 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
                              reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
                              static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, st));
     }
-    TRY(run_moments(c, precision, P, d_jobs, reinterpret_cast<MomTile*>(base + o_tile), d_geo, st));
+    TRY(run_low(c, P, reinterpret_cast<LowJob*>(base + o_lj), reinterpret_cast<LowTile*>(base + o_lt), d_geo, st));
+    TRY(run_moments(c, precision, P, d_jobs, d_geo, st));
     PhaseScope ps(c, TCM_PHASE_CONTRACT, 1);
     TRY_LAUNCH(launch_contract(reinterpret_cast<PairDesc*>(base + o_it), (int)n_items, Lmax_items, d_jobs, d_geo,
                                c->d_ztab, rots.empty() ? nullptr : reinterpret_cast<double*>(base + o_rot), E,
@@ -908,12 +993,14 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
                                 (long long)o_gj, (long long)o_gt, (long long)o_it, (long long)o_rot, (long long)rots.empty(), (long long)(uintptr_t)base,
                                 (long long)(uintptr_t)c->gpart.p, (long long)(uintptr_t)c->partials.p,
                                 (long long)(uintptr_t)c->counters.p, (long long)(uintptr_t)E,
-                                (long long)(uintptr_t)status};
+                                (long long)(uintptr_t)status, (long long)P.ltiles.size(), (long long)o_lj,
+                                (long long)o_lt, (long long)(uintptr_t)c->lowp.p, (long long)P.groups.size(),
+                                (long long)P.n_tiles, (long long)(uintptr_t)c->tiles.p};
   for (int L = 0; L <= kLmaxMax + 1; ++L) key.push_back(P.tile_begin[L]);
   if (!c->gexec || key != c->gkey) {
-    // capture only a shape seen twice in a row: a stream of changing shapes (continuous
-    // batching) launches directly instead of paying a capture per call
-    if (key != c->gkey_seen) {
+    // by default capture only a shape seen twice in a row: a stream of changing shapes
+    // (continuous batching) launches directly instead of paying a capture per call
+    if (c->graphs == 1 && key != c->gkey_seen) {
       c->gkey_seen = key;
       return enqueue(c->stream);
     }
@@ -943,8 +1030,9 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   }
   TRY_CUDA(cudaGraphLaunch(c->gexec, c->stream));
   ++c->graph_launches;
-  c->launches[TCM_PHASE_GEOM] += geom_launches(cluster_jobs(gjobs), ngt);
-  c->launches[TCM_PHASE_MOMENTS] += ngroups;
+  c->launches[TCM_PHASE_GEOM] += geom_launches(cluster_jobs(gjobs), ngt) + (P.ltiles.empty() ? 0 : 1) +
+                                  (P.groups.empty() ? 0 : 1);
+  c->launches[TCM_PHASE_MOMENTS] += moment_launches(precision, P);
   c->launches[TCM_PHASE_FINALIZE] += 1;
   c->launches[TCM_PHASE_CONTRACT] += 1;
   return TCM_OK;

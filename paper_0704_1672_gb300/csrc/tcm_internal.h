@@ -146,6 +146,8 @@ struct MomJob {    // one moment set: a system at one Lmax under one rotation
   int tile_base;   // id of the job's first tile; tile id = base + chunk * tpc + t
   double rot[9];   // row-major, identity when unrotated
   double* out;     // packed moments, (L+1)^2 doubles
+  int low_base;    // mixed precision: first tile of the system's low-degree sums (LowJob), and
+  int low_tiles;   // their count; 0 = the degrees l <= 2 keep the float kernel's values
 };
 
 struct MomTile {   // one tile of moment work
@@ -153,6 +155,13 @@ struct MomTile {   // one tile of moment work
   int chunk;
   int t;           // tile index inside the chunk
   int id;          // global tile id (row of the partials buffer)
+};
+
+struct MomGroup {  // the tiles of one (job, chunk), written to the tile list on the device
+  int job;
+  int chunk;
+  int n;           // tiles (the job's tiles_per_chunk)
+  int first;       // position of its first tile in the tile list
 };
 
 struct GeomJob {   // a1: centroid and/or radius of one system
@@ -168,6 +177,32 @@ struct GeomJob {   // a1: centroid and/or radius of one system
 
 struct GeomTile {
   int gjob;
+  int t;
+};
+
+// Low-degree sums of one system in float-float arithmetic (mixed precision): about the
+// system's centre c, with d = x - c and no rotation or scaling,
+//   S = sum q,  P_k = sum q d_k,  T_kl = sum q d_k d_l  (k <= l),
+// the kLowSums values from which k_finalize forms Q_lm, l <= 2, of every job of the system
+// under that job's rotation.  The degrees that carry most of a well-separated pair's energy
+// are then accurate to about 2^-44 of their terms instead of the float recurrence's 2^-24.
+constexpr int kLowSums = 10;            // S, P_x, P_y, P_z, T_xx, T_xy, T_xz, T_yy, T_yz, T_zz
+constexpr int kLowLmax = 2;             // degrees replaced by the low-degree sums
+constexpr int kLowAtomsPerLane = 64;
+constexpr int kLowTileAtoms = 32 * kLowAtomsPerLane;  // atoms per warp tile
+constexpr int kLowThreads = 256;
+
+struct LowJob {
+  const void* xyzq;
+  long long n;
+  int dtype;
+  int geom;        // index into the SysGeom array
+  int tile_base;   // row of its first tile in the low-sum partials (kLowSums doubles per row)
+  int n_tiles;
+};
+
+struct LowTile {
+  int job;
   int t;
 };
 
@@ -210,6 +245,13 @@ cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
 // counter[32] must be zero on entry; the launch leaves them zero.
 int launch_moments(int precision, int L, const MomJob* jobs, const MomTile* tiles, int n_tiles,
                    int* counter, const SysGeom* geoms, double* partials, int grid, cudaStream_t s);
+// The tile list of a moment pass from its groups: tiles[g.first + t] = (g.job, g.chunk, t, row),
+// t < g.n, row = jobs[g.job].tile_base + g.chunk * tiles_per_chunk + t.  One warp per group.
+int launch_expand_tiles(const MomGroup* groups, int n_groups, const MomJob* jobs, MomTile* tiles, cudaStream_t s);
+// Mixed precision: one persistent launch over tiles of any degrees (each tile runs the code of
+// its job's degree); the tiles are taken in array order.
+int launch_moments_any(const MomJob* jobs, const MomTile* tiles, int n_tiles, int* counter, const SysGeom* geoms,
+                       double* partials, int grid, cudaStream_t s);
 int moments_smem_bytes(int precision, int L);
 int moments_kmax(int precision);
 int moments_nchunks(int precision, int L);
@@ -226,11 +268,18 @@ void finalize_tables(std::vector<int>& imap_off, std::vector<int>& imap, std::ve
 int launch_geom(const GeomJob* gjobs, int n_gjobs, int n_cluster_jobs, const GeomTile* gtiles, int n_gtiles,
                 double* gpart, int* tickets, SysGeom* geoms, cudaStream_t s);
 int geom_launches(int n_cluster_jobs, int n_gtiles);
+// Low-degree sums (LowJob): one warp per tile, kLowSums doubles per tile row of lowpart.  Needs
+// the systems' centres (launched after launch_geom, programmatic serialization).
+int launch_lowmom(const LowJob* ljobs, const LowTile* ltiles, int n_ltiles, const SysGeom* geoms, double* lowpart,
+                  cudaStream_t s);
 // Step a3: one CTA per job.  imap + imap_off[L] lists, per (chunk, slot) of degree L, the packed
 // component it holds (-1 for none), nch(L) x kmax entries; fmap beside it holds that
 // component's F_lm with the sign of the kernels' H variables.
+// Jobs with low_tiles > 0 take their degrees l <= min(kLowLmax, L) from the low-degree sums
+// (lowpart rows [low_base, low_base + low_tiles)) rotated by the job's rotation.
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms,
-                    const int* imap, const double* fmap, const int* imap_off, int kmax, cudaStream_t s);
+                    const int* imap, const double* fmap, const int* imap_off, int kmax, const double* lowpart,
+                    cudaStream_t s);
 
 
 

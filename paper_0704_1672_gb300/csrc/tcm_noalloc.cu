@@ -1,4 +1,4 @@
-// tcm_moments_noalloc: the moment pass (Eq. (multipole)) without any device allocation.
+// tcm_moments_noalloc: the moment pass of tcm_moments without any device allocation.
 //
 // Some callers cannot allocate device memory: code that runs where cudaMalloc/cudaFree
 // would synchronise the device and break its latency budget, host applications whose
@@ -6,9 +6,9 @@
 // create allocations of their own.  tcm_moments needs a context, and a context
 // allocates (tables at creation, scratch on first use).  This entry point instead keeps
 // everything it needs -- the coefficient tables, the job and tile descriptors, the
-// centre/radius partials and the per-tile moment partials -- in one file-scope
-// __device__ array of fixed size, so a call allocates nothing.  The caller passes the
-// coordinates and the output buffer, as for tcm_moments.
+// centre/radius partials, the low-degree sums and the per-tile moment partials -- in one
+// file-scope __device__ array of fixed size, so a call allocates nothing.  The caller
+// passes the coordinates and the output buffer, as for tcm_moments.
 //
 // The array exists once per device (every GPU that loads the library holds it until the
 // process exits) and all calls on a device share it: two calls whose work overlaps on
@@ -50,7 +50,13 @@ constexpr int kNaImapInts = 4 * kNaCompTotal;  // room for both precisions' (chu
 constexpr size_t kOffImapOff = align256(kOffCounters + sizeof(int) * 64);
 constexpr size_t kOffImap = align256(kOffImapOff + sizeof(int) * 2 * (kLmaxMax + 2));
 constexpr size_t kOffFmap = align256(kOffImap + sizeof(int) * kNaImapInts);
-constexpr size_t kScratchBytes = align256(kOffFmap + sizeof(double) * kNaImapInts);
+constexpr int kNaLowTiles = (int)((kNaMaxAtoms + kLowTileAtoms - 1) / kLowTileAtoms);
+constexpr size_t kOffLowJob = align256(kOffFmap + sizeof(double) * kNaImapInts);
+constexpr size_t kOffLowTiles = align256(kOffLowJob + sizeof(LowJob));
+constexpr size_t kOffLowPart = align256(kOffLowTiles + sizeof(LowTile) * kNaLowTiles);
+constexpr size_t kScratchBytes = align256(kOffLowPart + sizeof(double) * kLowSums * kNaLowTiles);
+// The size stated in include/tcm.h (TCM_NOALLOC_SCRATCH_BYTES) must be this layout's.
+static_assert(kScratchBytes == TCM_NOALLOC_SCRATCH_BYTES, "tcm.h states the wrong scratch size");
 
 // The scratch.  In host code this name is only a stand-in for the symbol; kernels get
 // the device address obtained with cudaGetSymbolAddress.
@@ -81,6 +87,10 @@ int setup_device(int dev, char** out) {
       cudaMemcpy(base + kOffImapOff, imap_off.data(), imap_off.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(base + kOffImap, imap.data(), imap.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: copying the tables into the scratch failed");
+  // A copy from pageable host memory may return before the data reach the device; the
+  // kernels of this call may run on another (non-blocking) stream, so wait for the tables.
+  if (cudaDeviceSynchronize() != cudaSuccess)
+    return na_err(TCM_ECUDA, "tcm_moments_noalloc: waiting for the table copies failed");
   g_scratch_ptr[dev] = base;
   *out = base;
   return TCM_OK;
@@ -88,17 +98,21 @@ int setup_device(int dev, char** out) {
 
 // Writes one call's descriptors into the scratch and clears the work counters.  The
 // descriptors travel as kernel arguments, so no host staging buffer is involved.
-__global__ void k_noalloc_prepare(char* base, MomJob job, SysGeom geom, GeomJob gjob, int n_gtiles, int nch, int tpc) {
+__global__ void k_noalloc_prepare(char* base, MomJob job, SysGeom geom, GeomJob gjob, LowJob ljob, int n_gtiles,
+                                  int nch, int tpc) {
   MomTile* tiles = reinterpret_cast<MomTile*>(base + kOffTiles);
   GeomTile* gtiles = reinterpret_cast<GeomTile*>(base + kOffGTiles);
+  LowTile* ltiles = reinterpret_cast<LowTile*>(base + kOffLowTiles);
   int* counters = reinterpret_cast<int*>(base + kOffCounters);
   if (threadIdx.x == 0) {
     *reinterpret_cast<MomJob*>(base + kOffJob) = job;
     *reinterpret_cast<SysGeom*>(base + kOffGeom) = geom;
     *reinterpret_cast<GeomJob*>(base + kOffGJob) = gjob;
+    *reinterpret_cast<LowJob*>(base + kOffLowJob) = ljob;
   }
   for (int k = threadIdx.x; k < 64; k += blockDim.x) counters[k] = 0;
   for (int k = threadIdx.x; k < n_gtiles; k += blockDim.x) gtiles[k] = GeomTile{0, k};
+  for (int k = threadIdx.x; k < job.low_tiles; k += blockDim.x) ltiles[k] = LowTile{0, k};
   for (int k = threadIdx.x; k < nch * tpc; k += blockDim.x) tiles[k] = MomTile{0, k / tpc, k % tpc, k};
 }
 
@@ -140,6 +154,16 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   job.tile_base = 0;
   for (int k = 0; k < 9; ++k) job.rot[k] = rot ? rot[k] : ((k % 4 == 0) ? 1.0 : 0.0);
   job.out = q_out;
+  LowJob lj{};  // mixed precision: degrees l <= 2 from the float-float low-degree sums, as tcm_moments
+  lj.xyzq = s->xyzq;
+  lj.n = s->n;
+  lj.dtype = s->dtype;
+  lj.geom = 0;
+  lj.tile_base = 0;
+  lj.n_tiles = (int)std::max<long long>(1, (s->n + kLowTileAtoms - 1) / kLowTileAtoms);
+  if (lj.n_tiles > kNaLowTiles) return na_err(TCM_EINVAL, "tcm_moments_noalloc: request exceeds the fixed scratch");
+  job.low_base = 0;
+  job.low_tiles = precision == TCM_MIXED ? lj.n_tiles : 0;
   const bool known = s->has_center && s->radius >= 0.0;
   SysGeom geom{};
   for (int d = 0; d < 3; ++d) geom.c[d] = s->has_center ? s->center[d] : 0.0;
@@ -158,13 +182,17 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
 
   MomJob* d_job = reinterpret_cast<MomJob*>(base + kOffJob);
   SysGeom* d_geom = reinterpret_cast<SysGeom*>(base + kOffGeom);
-  k_noalloc_prepare<<<1, 256, 0, st>>>(base, job, geom, gj, known ? 0 : gj.n_tiles, nch, tpc);
+  k_noalloc_prepare<<<1, 256, 0, st>>>(base, job, geom, gj, lj, known ? 0 : gj.n_tiles, nch, tpc);
   if (cudaPeekAtLastError() != cudaSuccess) return na_err(TCM_ECUDA, "tcm_moments_noalloc: launch failed");
   if (!known && launch_geom(reinterpret_cast<GeomJob*>(base + kOffGJob), 1, gj.n_tiles == 0 ? 1 : 0,
                             reinterpret_cast<GeomTile*>(base + kOffGTiles),
                             gj.n_tiles, reinterpret_cast<double*>(base + kOffGPart),
                             reinterpret_cast<int*>(base + kOffCounters) + 40, d_geom, st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: centre/radius launch failed");
+  if (job.low_tiles > 0 && launch_lowmom(reinterpret_cast<LowJob*>(base + kOffLowJob),
+                                          reinterpret_cast<LowTile*>(base + kOffLowTiles), job.low_tiles, d_geom,
+                                          reinterpret_cast<double*>(base + kOffLowPart), st) != 0)
+    return na_err(TCM_ECUDA, "tcm_moments_noalloc: low-degree launch failed");
   int num_sms = 0;
   if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: cudaDeviceGetAttribute failed");
@@ -176,7 +204,7 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   if (launch_finalize(d_job, 1, reinterpret_cast<double*>(base + kOffPartials), d_geom,
                       reinterpret_cast<int*>(base + kOffImap), reinterpret_cast<double*>(base + kOffFmap),
                       reinterpret_cast<int*>(base + kOffImapOff) + (precision == TCM_FP64 ? 0 : kLmaxMax + 2),
-                      kmax, st) != 0)
+                      kmax, reinterpret_cast<double*>(base + kOffLowPart), st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: finalisation launch failed");
   if (geom_out && cudaMemcpyAsync(geom_out, d_geom, sizeof(SysGeom), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: copy of the centre and radius failed");

@@ -227,8 +227,10 @@ class Context:
             o.radius = res[i].radius
         return outs[0] if single else outs
 
-    def tcm_ctx_set_graphs(self, enable: bool):
-        _check(lib().tcm_ctx_set_graphs(self._h, 1 if enable else 0))
+    def tcm_ctx_set_graphs(self, mode):
+        """0 (or False): launch kernel by kernel; 1 (or True, default): capture a shape seen twice in
+        a row; 2: capture every new shape on its first call."""
+        _check(lib().tcm_ctx_set_graphs(self._h, int(mode)))
 
     def tcm_ctx_graph_stats(self):
         cap, lau = ctypes.c_int64(), ctypes.c_int64()
@@ -352,19 +354,32 @@ def tcm_moments_noalloc(xyzq, lmax, precision=TCM_MIXED, rot=None, center=None, 
                         center_radius_out=None, stream=None):
     """The C entry point that allocates no device memory (for callers that cannot allocate).
 
-    ``out`` (device float64, (lmax+1)^2) and ``center_radius_out`` (device float64, 4) should be
-    passed preallocated by such callers; the library call itself allocates nothing and queues
-    its work on ``stream`` (default: the current torch stream).  Calls that overlap on the GPU
-    race on the library's shared scratch, so serialise them.
+    ``out`` (contiguous float64 CUDA tensor of at least (lmax+1)^2 entries) and
+    ``center_radius_out`` (contiguous float64 CUDA tensor of at least 4 entries) must be on the
+    device of ``xyzq``; such callers pass them preallocated.  The library call itself allocates
+    nothing and queues its work on ``stream`` (default: the current torch stream of that
+    device).  Calls that overlap on the GPU race on the library's shared scratch, so serialise
+    them.
     """
     s = make_system(xyzq, center=center, radius=radius)
+    dev = xyzq.device
     if out is None:
-        out = torch.empty((lmax + 1) ** 2, dtype=torch.float64, device=xyzq.device)
-    stream = stream if stream is not None else torch.cuda.current_stream()
-    r = None if rot is None else np.ascontiguousarray(rot, dtype=np.float64).reshape(9)
-    g = None if center_radius_out is None else ctypes.c_void_p(center_radius_out.data_ptr())
-    _check(lib().tcm_moments_noalloc(ctypes.byref(s), _dptr(r), int(lmax), int(precision), ctypes.c_void_p(out.data_ptr()),
-                                     g, ctypes.c_void_p(stream.cuda_stream)))
+        out = torch.empty((lmax + 1) ** 2, dtype=torch.float64, device=dev)
+
+    def _check_out(t, n, what):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or t.device != dev \
+                or not t.is_contiguous() or t.numel() < n:
+            raise TcmError(TCM_EINVAL, f"{what} must be a contiguous float64 CUDA tensor of at least {n} entries on {dev}")
+
+    _check_out(out, (max(int(lmax), 0) + 1) ** 2, "out")
+    if center_radius_out is not None:
+        _check_out(center_radius_out, 4, "center_radius_out")
+    with torch.cuda.device(dev):
+        stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        r = None if rot is None else np.ascontiguousarray(rot, dtype=np.float64).reshape(9)
+        g = None if center_radius_out is None else ctypes.c_void_p(center_radius_out.data_ptr())
+        _check(lib().tcm_moments_noalloc(ctypes.byref(s), _dptr(r), int(lmax), int(precision),
+                                         ctypes.c_void_p(out.data_ptr()), g, ctypes.c_void_p(stream.cuda_stream)))
     return out
 
 

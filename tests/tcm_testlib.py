@@ -1,14 +1,12 @@
 """Shared helpers for the parity tests: tolerance measures and threaded oracle calls.
 
-Tolerances (readings of the paper recorded in the design doc):
+Tolerances (the readings of the paper's error measures for near-zero quantities):
   * moments, per degree l:  max_m |dQ_lm| / max(||Q_l.||_2, KAPPA * S_l)
         where S_l = sum_i |q_i| r_i^l is the magnitude scale of the degree-l sum; a
         degree whose norm cancels below KAPPA * S_l is measured against that floor.
-  * energy, double path: |dE| / max(|E|, 1e-3 * sum_{l1,l2} |U_l1l2|)
-  * energy, mixed path: |dE| / sum_{l1,l2} |U_l1l2|  (the condition scale of Eq. (Formula); equal
-        to |E| when the (l1, l2) blocks do not cancel).  Float per-atom arithmetic leaves each
-        moment term with a relative error of about l * 2^-24 that no reduction removes, so the
-        mixed path's energy error is bounded by the magnitudes of the blocks, not by |E|.
+  * energy, both paths:  |dE| / max(|E|, 1e-3 * sum_{l1,l2} |U_l1l2|)
+        i.e. relative to |E|, falling back to the condition scale sum |U_l1l2| of Eq. (Formula)
+        only when the (l1, l2) blocks cancel to below a thousandth of their magnitude.
   * direct sum: |dU| / sum_ij |q_i q_j| / r_ij
   * bars: 1e-12 for the double path, 1e-5 (moments) and 1e-6 (energy) for the mixed path.
 """
@@ -49,16 +47,68 @@ def moment_error(Q_test, Q_ref, S):
     return worst
 
 
-def energy_error(E_test, E_ref, blocks, mixed=False):
-    if mixed:
-        scale = np.sum(np.abs(blocks))
-    else:
-        scale = max(abs(E_ref), 1e-3 * np.sum(np.abs(blocks)))
+E_FLOOR = 1e-3  # fraction of sum |U_l1l2| below which |E| is replaced by that floor
+
+
+def energy_error(E_test, E_ref, blocks):
+    """|E_test - E_ref| / max(|E_ref|, E_FLOOR * sum |U_l1l2|)."""
+    scale = max(abs(E_ref), E_FLOOR * np.sum(np.abs(blocks)))
     return abs(E_test - E_ref) / scale
+
+
+def energy_error_cond(E_test, E_ref, blocks):
+    """|E_test - E_ref| / sum |U_l1l2| (reported beside energy_error, not a bar)."""
+    return abs(E_test - E_ref) / np.sum(np.abs(blocks))
 
 
 def energy_error_vs_e(E_test, E_ref):
     return abs(E_test - E_ref) / abs(E_ref)
+
+
+# The mixed path's per-atom float arithmetic leaves every (l1, l2) block of Eq. (Formula) with a
+# relative error of order 1e-7 (the rounding of the scaled, rotated coordinates and of the
+# recurrence, about l * 2^-24 per term, for the degrees l >= 3 that are not taken from the exact
+# low-degree sums), so its energy error is bounded by a small multiple of sum |U_l1l2|, whatever
+# |E| is.  Measured over every sampled item of every workload: at most 1.9e-7 sum |U|.  Where the
+# blocks cancel (|E| well below sum |U|) the 1e-6 bar relative to |E| is therefore out of reach
+# of float per-atom arithmetic: it is asserted on every item with |E| >= COND_MIX sum |U|
+# (1e-6 * COND_MIX = 2.5e-7 sum |U| covers the measured maximum), and on every item the error is
+# held to GUARD_MIX sum |U|.  Items below COND_MIX that miss the bar are counted and printed as
+# misses of the bar, not as passes.
+COND_MIX = 0.25
+GUARD_MIX = 5e-7
+
+
+class MixedEnergyReport:
+    """Collects mixed-path energies against the oracle and applies the bar as stated above."""
+
+    def __init__(self, name):
+        self.name = name
+        self.rows = []
+
+    def add(self, E_test, E_ref, blocks, label=""):
+        sU = float(np.sum(np.abs(blocks)))
+        self.rows.append((label, abs(E_ref) / sU, energy_error(E_test, E_ref, blocks), abs(E_test - E_ref) / sU))
+
+    def add_vec(self, v_test, v_ref, scale, label=""):
+        """A vector result (force, torque) with its condition scale (the sum of its block lengths)."""
+        d = float(np.linalg.norm(np.asarray(v_test) - np.asarray(v_ref)))
+        n = float(np.linalg.norm(v_ref))
+        self.rows.append((label, n / scale, d / max(n, E_FLOOR * scale), d / scale))
+
+    def check(self):
+        misses = [r for r in self.rows if r[2] > TOL_MIX_E]
+        cond = [r for r in self.rows if r[1] >= COND_MIX]
+        print(f"{self.name}: {len(self.rows)} items, {len(self.rows) - len(misses)} within the 1e-6 bar of the stated "
+              f"measure; worst {max(r[2] for r in self.rows):.3e} (|E|/sum|U| = "
+              f"{max(self.rows, key=lambda r: r[2])[1]:.3g}); worst |dE|/sum|U| {max(r[3] for r in self.rows):.3e}")
+        for label, ratio, err, errc in misses:
+            print(f"  bar missed: {label} |E|/sum|U| = {ratio:.3g}, error {err:.3e} (|dE|/sum|U| {errc:.3e})")
+        bad = [r for r in cond if r[2] > TOL_MIX_E]
+        assert not bad, f"{self.name}: well-conditioned items over the bar: {bad}"
+        guard = [r for r in self.rows if r[3] > GUARD_MIX]
+        assert not guard, f"{self.name}: items over the float error bound: {guard}"
+        return misses
 
 
 _POOL = None

@@ -2,15 +2,16 @@
 the force on B is -grad_R0 of the truncated energy, the torques are minus its derivatives under
 rotations of A and of B about their centres.
 
-Error measures: force |dF| / max(|F|, 1e-3 S_F) (double path) or |dF| / S_F (mixed path), with
-S_F the sum of the (l1, l2) block force lengths; torques the same against |R0| S_F."""
+Error measures: force |dF| / max(|F|, 1e-3 S_F), with S_F the sum of the (l1, l2) block force
+lengths; torques the same against |R0| S_F.  The mixed path's bar is applied as for energies
+(tcm_testlib.MixedEnergyReport)."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 from paper_0704_1672_gb300 import synth
-from tcm_testlib import TOL_FP64, TOL_MIX_E, oracle_moments_threaded
+from tcm_testlib import TOL_FP64, MixedEnergyReport, oracle_moments_threaded
 
 pytestmark = pytest.mark.gpu
 
@@ -44,10 +45,10 @@ def oracle_grads(A, cA, B, cB, L, R0, rot):
     return oracle.tcm_energy(L, QA, QB, R0), F, tA, tB, blocks.sum()
 
 
-def errors(G, F, tA, tB, SF, R0, mixed):
+def errors(G, F, tA, tB, SF, R0, mixed=False):
     R = np.linalg.norm(R0)
     def err(v, ref, S):
-        return np.linalg.norm(v - ref) / (S if mixed else max(np.linalg.norm(ref), 1e-3 * S))
+        return np.linalg.norm(v - ref) / max(np.linalg.norm(ref), 1e-3 * S)
     return err(G[:3], F, SF), err(G[3:6], tA, R * SF), err(G[6:], tB, R * SF)
 
 
@@ -126,13 +127,14 @@ def test_mixed_batch_forces_and_torques(tcm, rotate_cached):
         Bf = s.B.astype(np.float32).astype(np.float64)
         cA, _ = oracle.center_radius(Af)
         cB, _ = oracle.center_radius(Bf)
-        worst = 0.0
+        rep = MixedEnergyReport("mixed forces and torques")
         for i in (0, 13, 31):
             Eo, F, tA, tB, SF = oracle_grads(Af, cA, Bf, cB, s.L, s.R0[i], s.rotB[i])
-            e = errors(G[i], F, tA, tB, SF, s.R0[i], mixed=True)
-            worst = max(worst, max(e))
-        print(f"mixed forces/torques, worst error {worst:.2e} of the condition scale")
-        assert worst < TOL_MIX_E
+            R = np.linalg.norm(s.R0[i])
+            rep.add_vec(G[i][:3], F, SF, f"orientation {i}, force on B")
+            rep.add_vec(G[i][3:6], tA, R * SF, f"orientation {i}, torque on A")
+            rep.add_vec(G[i][6:], tB, R * SF, f"orientation {i}, torque on B")
+        rep.check()
     finally:
         ctx.close()
 

@@ -6,7 +6,7 @@ import torch
 
 import oracle
 from paper_0704_1672_gb300 import synth
-from tcm_testlib import TOL_FP64, TOL_MIX_E, energy_error, energy_error_vs_e, oracle_moments_threaded
+from tcm_testlib import TOL_FP64, MixedEnergyReport, energy_error, oracle_moments_threaded
 
 pytestmark = pytest.mark.gpu
 
@@ -33,20 +33,30 @@ def f32(a):
     return a.astype(np.float32).astype(np.float64)
 
 
-def check_items(sysA, sysB, rot, R0, L, E, sample, mixed=True):
-    worst = 0.0
+def check_items(name, sysA, sysB, rot, R0, L, E, sample):
+    rep = MixedEnergyReport(name)
     for k in sample:
         A, B = f32(sysA(k)), f32(sysB(k))
         cA, _ = oracle.center_radius(A)
         cB, _ = oracle.center_radius(B)
         QA = oracle_moments_threaded(A, cA, L[k])
         QB = oracle_moments_threaded(B, cB, L[k], rot=rot[k])
-        Eo = oracle.tcm_energy(L[k], QA, QB, R0[k])
-        err = energy_error(float(E[k]), Eo, oracle.tcm_blocks(L[k], QA, QB, R0[k]), mixed=mixed)
-        print(f"item {k}: L={L[k]} N=({len(A)},{len(B)}) error {err:.3e} of the condition scale, "
-              f"{energy_error_vs_e(float(E[k]), Eo):.3e} of |E|")
-        worst = max(worst, err)
-    return worst
+        rep.add(float(E[k]), oracle.tcm_energy(L[k], QA, QB, R0[k]), oracle.tcm_blocks(L[k], QA, QB, R0[k]),
+                f"item {k} (L={L[k]}, N=({len(A)},{len(B)}))")
+    rep.check()
+
+
+def uneven_sample(b, per_cell=2):
+    """Items of every degree in every decile of the pair size (N_A + N_B): per_cell each."""
+    n = np.array([len(s) for s in b.systems])
+    sizes = n[b.pair_a] + n[b.pair_b]
+    edges = np.quantile(sizes, np.linspace(0, 1, 11))
+    sample = []
+    for L in sorted(set(int(x) for x in b.L)):
+        for d in range(10):
+            idx = np.where((b.L == L) & (sizes >= edges[d]) & (sizes <= edges[d + 1]))[0]
+            sample += [int(i) for i in idx[np.linspace(0, len(idx) - 1, min(per_cell, len(idx))).astype(int)]]
+    return sorted(set(sample))
 
 
 def test_uneven_batch_full_size(ctx, tcm):
@@ -69,15 +79,17 @@ def test_uneven_batch_full_size(ctx, tcm):
     assert np.all(np.isfinite(E))
     n = np.array([len(s) for s in b.systems])
     sizes = n[b.pair_a] + n[b.pair_b]
-    # sample: each L, small and large systems
-    sample = []
+    # sample: every degree in every size decile, plus the smallest and largest pair of each degree
+    sample = uneven_sample(b)
     for L in (8, 12, 16, 24):
         idx = np.where(b.L == L)[0]
         sample += [int(idx[np.argmin(sizes[idx])]), int(idx[np.argmax(sizes[idx])])]
-    worst = check_items(lambda k: b.systems[b.pair_a[k]], lambda k: b.systems[b.pair_b[k]], b.rotB, b.R0, b.L, E, sample)
-    assert worst < TOL_MIX_E, worst
+    sample = sorted(set(sample))
+    assert len(sample) >= 64
+    check_items("uneven batch", lambda k: b.systems[b.pair_a[k]], lambda k: b.systems[b.pair_b[k]], b.rotB, b.R0,
+                b.L, E, sample)
     # the same items alone give bit-identical energies
-    for k in sample[:4]:
+    for k in sample[::16]:
         E1, _ = ctx.tcm_energy_batch(T, [b.pair_a[k]], [b.pair_b[k]], [b.L[k]], b.R0[k:k + 1], rotB=b.rotB[k:k + 1],
                                      precision=tcm.TCM_MIXED)
         torch.cuda.synchronize()
@@ -103,14 +115,13 @@ def test_large_assembly_full_size(ctx, tcm):
     cA, _ = oracle.center_radius(Af)
     cB, _ = oracle.center_radius(Bf)
     QA = oracle_moments_threaded(Af, cA, a.L)
-    worst = 0.0
-    for kk in (0, 4321, 9999):
+    rep = MixedEnergyReport("large assembly, 16 of 10,000 orientations")
+    for kk in np.unique(np.concatenate([np.linspace(0, k - 1, 16).astype(int), [4321]])):
         QB = oracle_moments_threaded(Bf, cB, a.L, rot=a.rotB[kk])
-        Eo = oracle.tcm_energy(a.L, QA, QB, a.R0[kk])
-        err = energy_error(float(E[kk]), Eo, oracle.tcm_blocks(a.L, QA, QB, a.R0[kk]), mixed=True)
-        print(f"orientation {kk}: error {err:.3e} of the condition scale, {energy_error_vs_e(float(E[kk]), Eo):.3e} of |E|")
-        worst = max(worst, err)
-    assert worst < TOL_MIX_E, worst
+        rep.add(float(E[kk]), oracle.tcm_energy(a.L, QA, QB, a.R0[kk]), oracle.tcm_blocks(a.L, QA, QB, a.R0[kk]),
+                f"orientation {kk}")
+    assert len(rep.rows) >= 16
+    rep.check()
 
 
 def test_uneven_batch_fp64_subset(ctx, tcm):
