@@ -1,11 +1,9 @@
 // Kernels around the moment pass:
-//   a1  centre and radius of a system (Section II: any centre; the centroid by default)
 //   a3  cross-tile reduction of the moment partials in double, fixed order, plus the
 //       deferred normalisation F_lm a^l                                  (Eq. (multipole))
 //   a4  irregular solid harmonics of the separation vector R0            (Eq. (Formula))
 //   a5  two-center contraction in double                                 (Eq. (Formula))
 //   a6  exact pairwise Coulomb sum in double                             (Eq. (Coulomb))
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "contract.h"
@@ -19,12 +17,6 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-  return v;
-}
-
 // Fixed-order block sum (deterministic); result valid in thread 0.  blockDim <= 1024.
 __device__ double block_sum(double v, double* sh) {
   v = warp_sum(v);
@@ -40,21 +32,6 @@ __device__ double block_sum(double v, double* sh) {
   __syncthreads();
   return r;
 }
-__device__ double block_max(double v, double* sh) {
-  v = warp_max(v);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (w == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    r = lane < nw ? sh[lane] : 0.0;
-    r = warp_max(r);
-  }
-  __syncthreads();
-  return r;
-}
-
 __device__ __forceinline__ void load_xyz(const void* p, int dtype, long long i, double& x, double& y, double& z,
                                          double& q) {
   if (dtype == TCM_F32) {
@@ -73,274 +50,7 @@ __device__ __forceinline__ void load_xyz(const void* p, int dtype, long long i, 
   }
 }
 
-constexpr int kGeomThreads = 128;
-
-// a1 for a float32 system of at most kGeomClusterAtoms atoms, in one launch: a cluster of
-// kGeomClusterCTAs CTAs per system holds the atoms in registers (kGeomClusterPer per thread),
-// and the CTAs combine their partial sums through distributed shared memory, so the two passes
-// need neither a second launch nor global tickets.  The per-atom arithmetic is float:
-//   * centroid: each thread adds its coordinates with an error-free two-sum (value + error),
-//     the pairs are reduced in float-float over the warp and the CTA, and every CTA adds the
-//     CTAs' double sums in rank order (the same centre in all of them, no second barrier);
-//   * radius: |x - c|^2 in float from the split centre (c_hi + c_lo) picks the candidates
-//     within a relative 4e-6 of the largest (the float value is within 1e-6 of the exact one),
-//     and only those are recomputed in double; their maximum is the exact double radius^2.
-//     Both maxima go to rank 0 by atomicMax on distributed shared memory (non-negative floats
-//     and doubles order like their bit patterns): three cluster barriers in all.
-namespace cg = cooperative_groups;
-__device__ __forceinline__ void two_sum_add(float& s, float& e, float x) {
-  const float t = s + x;
-  const float bb = t - s;
-  e += (s - (t - bb)) + (x - bb);
-  s = t;
-}
-
-// Warp sum of float-float values (s + e): each level adds the partner's pair with a two-sum,
-// so the warp total keeps about 48 bits; float instructions only (the FP64 pipe is 1/64 of
-// the FP32 one, so double reductions over 16 warps would dominate this kernel).
-__device__ __forceinline__ void warp_sum_ff(float& s, float& e) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
-    const float e2 = __shfl_xor_sync(0xffffffffu, e, o);
-    two_sum_add(s, e, s2);
-    e += e2;
-  }
-}
-
-__device__ __forceinline__ float warp_max_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-__global__ void __cluster_dims__(kGeomClusterCTAs, 1, 1) __launch_bounds__(kGeomClusterThreads)
-    k_geom_cluster(const GeomJob* __restrict__ gj, SysGeom* __restrict__ geoms) {
-  constexpr int kWarps = kGeomClusterThreads / 32;
-  __shared__ float2 s_wsum[3][kWarps];       // warp sums as float-float pairs (value, error)
-  __shared__ float s_wmax[kWarps];
-  __shared__ double s_part[3];               // this CTA's coordinate sums
-  __shared__ unsigned int s_fmax;            // rank 0: the cluster's float maximum of |x - c|^2 (bits)
-  __shared__ unsigned long long s_dmax;      // rank 0: the exact double maximum over the candidates (bits)
-  __shared__ double s_c[3];                  // the centre
-  __shared__ float2 s_cf[3];                 // and its split c = hi + lo into floats
-  __shared__ float s_thr;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const GeomJob j = gj[blockIdx.x / kGeomClusterCTAs];
-  const float4* xyzq = reinterpret_cast<const float4*>(j.xyzq);
-  const long long stride = (long long)kGeomClusterCTAs * kGeomClusterThreads;
-  const long long i0 = (long long)rank * kGeomClusterThreads + threadIdx.x;
-  float x[kGeomClusterPer], y[kGeomClusterPer], z[kGeomClusterPer];
-#pragma unroll
-  for (int k = 0; k < kGeomClusterPer; ++k) {
-    const long long i = i0 + k * stride;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i < j.n) v = __ldg(xyzq + i);
-    x[k] = v.x;
-    y[k] = v.y;
-    z[k] = v.z;
-  }
-  if (threadIdx.x == 0) {
-    s_fmax = 0u;
-    s_dmax = 0ull;
-  }
-  // pass 1: coordinate sums, float-float within the CTA, double across the CTAs
-  float sx = 0.f, ex = 0.f, sy = 0.f, ey = 0.f, sz = 0.f, ez = 0.f;
-#pragma unroll
-  for (int k = 0; k < kGeomClusterPer; ++k) {  // padding atoms add exact zeros
-    two_sum_add(sx, ex, x[k]);
-    two_sum_add(sy, ey, y[k]);
-    two_sum_add(sz, ez, z[k]);
-  }
-  warp_sum_ff(sx, ex);
-  warp_sum_ff(sy, ey);
-  warp_sum_ff(sz, ez);
-  if (lane == 0) {
-    s_wsum[0][warp] = make_float2(sx, ex);
-    s_wsum[1][warp] = make_float2(sy, ey);
-    s_wsum[2][warp] = make_float2(sz, ez);
-  }
-  __syncthreads();
-  if (threadIdx.x < 3) {  // warp order, float-float; one conversion to double per CTA
-    float t = 0.f, te = 0.f;
-    for (int w = 0; w < kWarps; ++w) {
-      const float2 v = s_wsum[threadIdx.x][w];
-      two_sum_add(t, te, v.x);
-      te += v.y;
-    }
-    s_part[threadIdx.x] = (double)t + (double)te;
-  }
-  cluster.sync();  // (1) every CTA's sums are in place, rank 0's maxima are cleared
-  if (threadIdx.x < 3) {  // every CTA adds the CTAs' sums in rank order: the same centre in all of them
-    double t = 0.0;
-    for (int r = 0; r < kGeomClusterCTAs; ++r) t += cluster.map_shared_rank(s_part, r)[threadIdx.x];
-    const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
-    const double c = j.need_center ? t * inv : geoms[j.geom].c[threadIdx.x];
-    const float hi = (float)c;
-    s_c[threadIdx.x] = c;
-    s_cf[threadIdx.x] = make_float2(hi, (float)(c - (double)hi));
-  }
-  __syncthreads();
-  // pass 2: largest |x - c|^2, float filter then exact double on the candidates
-  const float2 fx = s_cf[0], fy = s_cf[1], fz = s_cf[2];
-  const float chx = fx.x, chy = fy.x, chz = fz.x, clx = fx.y, cly = fy.y, clz = fz.y;
-  float r2f[kGeomClusterPer];
-  float mf = 0.f;
-#pragma unroll
-  for (int k = 0; k < kGeomClusterPer; ++k) {
-    const float dx = (x[k] - chx) - clx, dy = (y[k] - chy) - cly, dz = (z[k] - chz) - clz;
-    r2f[k] = (i0 + k * stride < j.n) ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : -1.f;
-    mf = fmaxf(mf, r2f[k]);
-  }
-  mf = warp_max_f(mf);
-  if (lane == 0) s_wmax[warp] = mf;
-  __syncthreads();
-  if (threadIdx.x == 0) {  // non-negative floats order like their bit patterns
-    float m = 0.f;
-    for (int w = 0; w < kWarps; ++w) m = fmaxf(m, s_wmax[w]);
-    atomicMax(cluster.map_shared_rank(&s_fmax, 0), __float_as_uint(m));
-  }
-  cluster.sync();  // (2) the cluster's float maximum is in rank 0
-  if (threadIdx.x == 0) s_thr = __uint_as_float(*cluster.map_shared_rank(&s_fmax, 0)) * (1.0f - 4e-6f);
-  __syncthreads();
-  const float thr = s_thr;
-  const double cx = s_c[0], cy = s_c[1], cz = s_c[2];
-  unsigned long long* dmax0 = cluster.map_shared_rank(&s_dmax, 0);
-#pragma unroll
-  for (int k = 0; k < kGeomClusterPer; ++k) {
-    if (r2f[k] >= thr) {  // a handful of atoms: their exact squared distance, max through the bits
-      const double dx = (double)x[k] - cx, dy = (double)y[k] - cy, dz = (double)z[k] - cz;
-      atomicMax(dmax0, (unsigned long long)__double_as_longlong(dx * dx + dy * dy + dz * dz));
-    }
-  }
-  cluster.sync();  // (3) every candidate is in rank 0; after this no CTA reads another's shared memory
-  if (rank == 0 && threadIdx.x == 0) {
-    if (j.need_center) {
-      geoms[j.geom].c[0] = cx;
-      geoms[j.geom].c[1] = cy;
-      geoms[j.geom].c[2] = cz;
-    }
-    if (j.need_radius) geoms[j.geom].a = sqrt(__longlong_as_double((long long)s_dmax));
-  }
-}
-
-// a1, pass 1: per-tile sums of the coordinates (double); the last CTA of a system to
-// finish (ticket) adds the tile sums in tile order and writes the centroid.
-__global__ void __launch_bounds__(kGeomThreads) k_geom_centroid(const GeomJob* __restrict__ gj,
-                                                                const GeomTile* __restrict__ gt,
-                                                                double* __restrict__ gpart, int* __restrict__ tickets,
-                                                                SysGeom* __restrict__ geoms) {
-  __shared__ double sh[32];
-  __shared__ int s_last;
-  const GeomTile tile = gt[blockIdx.x];
-  const GeomJob j = gj[tile.gjob];
-  const long long i0 = (long long)tile.t * kGeomTileAtoms;
-  const long long i1 = min(j.n, i0 + (long long)kGeomTileAtoms);
-  // all of this thread's loads are issued before the sums (the data arrive from DRAM)
-  constexpr int kPer = kGeomTileAtoms / kGeomThreads;
-  double x[kPer], y[kPer], z[kPer];
-#pragma unroll
-  for (int k = 0; k < kPer; ++k) {
-    const long long i = i0 + threadIdx.x + (long long)k * kGeomThreads;
-    double q;
-    x[k] = y[k] = z[k] = 0.0;
-    if (i < i1) load_xyz(j.xyzq, j.dtype, i, x[k], y[k], z[k], q);
-  }
-  double sx = 0.0, sy = 0.0, sz = 0.0;
-#pragma unroll
-  for (int k = 0; k < kPer; ++k) {
-    sx += x[k];
-    sy += y[k];
-    sz += z[k];
-  }
-  sx = block_sum(sx, sh);
-  sy = block_sum(sy, sh);
-  sz = block_sum(sz, sh);
-  if (threadIdx.x == 0) {
-    double* o = gpart + 4LL * (j.tile_base + tile.t);
-    o[0] = sx;
-    o[1] = sy;
-    o[2] = sz;
-    __threadfence();
-    s_last = atomicAdd(&tickets[tile.gjob], 1) == j.n_tiles - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  // the last CTA adds the tile sums: every thread a strided subset in tile order (loads in
-  // parallel, through L2), then the fixed-order block sum
-  __threadfence();
-  const double* p = gpart + 4LL * j.tile_base;
-  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-  for (int t = threadIdx.x; t < j.n_tiles; t += kGeomThreads) {
-    t0 += __ldcg(p + 4 * t);
-    t1 += __ldcg(p + 4 * t + 1);
-    t2 += __ldcg(p + 4 * t + 2);
-  }
-  t0 = block_sum(t0, sh);
-  t1 = block_sum(t1, sh);
-  t2 = block_sum(t2, sh);
-  if (threadIdx.x == 0) {
-    tickets[tile.gjob] = 0;
-    if (j.need_center) {
-      const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
-      geoms[j.geom].c[0] = t0 * inv;
-      geoms[j.geom].c[1] = t1 * inv;
-      geoms[j.geom].c[2] = t2 * inv;
-    }
-  }
-}
-
-// a1, pass 2: per-tile max of |x - c|^2; the last CTA of a system writes the radius.
-__global__ void __launch_bounds__(kGeomThreads) k_geom_radius(const GeomJob* __restrict__ gj,
-                                                              const GeomTile* __restrict__ gt,
-                                                              double* __restrict__ gpart, int* __restrict__ tickets,
-                                                              SysGeom* __restrict__ geoms) {
-  __shared__ double sh[32];
-  __shared__ int s_last;
-  const GeomTile tile = gt[blockIdx.x];
-  const GeomJob j = gj[tile.gjob];
-  const double cx = geoms[j.geom].c[0], cy = geoms[j.geom].c[1], cz = geoms[j.geom].c[2];
-  const long long i0 = (long long)tile.t * kGeomTileAtoms;
-  const long long i1 = min(j.n, i0 + (long long)kGeomTileAtoms);
-  constexpr int kPer = kGeomTileAtoms / kGeomThreads;
-  double x[kPer], y[kPer], z[kPer];
-  bool ok[kPer];
-#pragma unroll
-  for (int k = 0; k < kPer; ++k) {
-    const long long i = i0 + threadIdx.x + (long long)k * kGeomThreads;
-    double q;
-    ok[k] = i < i1;
-    x[k] = y[k] = z[k] = 0.0;
-    if (ok[k]) load_xyz(j.xyzq, j.dtype, i, x[k], y[k], z[k], q);
-  }
-  double mx = 0.0;
-#pragma unroll
-  for (int k = 0; k < kPer; ++k) {
-    const double dx = x[k] - cx, dy = y[k] - cy, dz = z[k] - cz;
-    if (ok[k]) mx = fmax(mx, dx * dx + dy * dy + dz * dz);
-  }
-  mx = block_max(mx, sh);
-  if (threadIdx.x == 0) {
-    gpart[4LL * (j.tile_base + tile.t) + 3] = mx;
-    __threadfence();
-    s_last = atomicAdd(&tickets[tile.gjob], 1) == j.n_tiles - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  const double* p = gpart + 4LL * j.tile_base;
-  double m = 0.0;
-  for (int t = threadIdx.x; t < j.n_tiles; t += kGeomThreads) m = fmax(m, __ldcg(p + 4 * t + 3));
-  m = block_max(m, sh);
-  if (threadIdx.x == 0) {
-    tickets[tile.gjob] = 0;
-    if (j.need_radius) geoms[j.geom].a = sqrt(m);
-  }
-}
-
-// Degrees l <= kLowLmax of one job from its system's low-degree sums (k_lowmom): the tile rows
+// Degrees l <= kLowLmax of one job from its system's low-degree sums (system pass 2): the tile rows
 // are added in tile order (double), the Cartesian sums are rotated by the job's rotation R
 // (P' = R P, T' = R T R^T, p = R d) and turned into the packed Q_lm, l <= 2, with
 //   Q_00 = S,  Q_10 = P'_z,  Q_11 = -(P'_x + i P'_y)/sqrt(2),
@@ -348,11 +58,11 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom_radius(const GeomJob* __r
 //   Q_22 = sqrt(3/8) (T'_xx - T'_yy + 2 i T'_xy),
 // the regular solid harmonics r^l sqrt(4 pi/(2l+1)) Y_lm of Eq. (multipole) written out in x, y, z.
 constexpr int kLowComps = (kLowLmax + 1) * (kLowLmax + 1);
-__device__ void low_degrees(const MomJob& job, const double* __restrict__ lowpart, double* s_low) {
+__device__ void low_degrees(const MomJob& job, const double* __restrict__ syspart, double* s_low) {
   if (threadIdx.x < kLowSums) {
-    const double* p = lowpart + (long long)job.low_base * kLowSums + threadIdx.x;
+    const double* p = syspart + (long long)job.low_base * kSysPart + kSysPartLow + threadIdx.x;
     double t = 0.0;
-    for (int r = 0; r < job.low_tiles; ++r) t += __ldcg(p + (long long)r * kLowSums);
+    for (int r = 0; r < job.low_tiles; ++r) t += __ldcg(p + (long long)r * kSysPart);
     s_low[threadIdx.x] = t;
   }
   __syncthreads();
@@ -396,7 +106,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const MomJob* __r
                                                                const int* __restrict__ imap,
                                                                const double* __restrict__ fmap,
                                                                const int* __restrict__ imap_off, int kmax,
-                                                               const double* __restrict__ lowpart) {
+                                                               const double* __restrict__ syspart) {
   __shared__ double s_low[kLowSums];
   pdl_wait();  // the moment kernels' partial rows are complete
   const MomJob& job = jobs[blockIdx.x];
@@ -424,7 +134,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const MomJob* __r
     if (job.low_tiles > 0 && p < kLowComps) continue;  // written from the low-degree sums below
     job.out[p] = f * al * s;
   }
-  if (job.low_tiles > 0) low_degrees(job, lowpart, s_low);
+  if (job.low_tiles > 0) low_degrees(job, syspart, s_low);
 }
 
 // a4 + a5: one CTA per energy, in the frame where R0hat is the z axis.
@@ -991,27 +701,11 @@ int launch_rotate_moments(const RotDesc* sets, int n_sets, int Lmax_sets, const 
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_geom(const GeomJob* gjobs, int n_gjobs, int n_cluster_jobs, const GeomTile* gtiles, int n_gtiles,
-                double* gpart, int* tickets, SysGeom* geoms, cudaStream_t s) {
-  if (n_gjobs <= 0) return 0;
-  if (n_cluster_jobs > 0)
-    k_geom_cluster<<<n_cluster_jobs * kGeomClusterCTAs, kGeomClusterThreads, 0, s>>>(gjobs, geoms);
-  if (n_gtiles > 0) {
-    k_geom_centroid<<<n_gtiles, kGeomThreads, 0, s>>>(gjobs, gtiles, gpart, tickets, geoms);
-    k_geom_radius<<<n_gtiles, kGeomThreads, 0, s>>>(gjobs, gtiles, gpart, tickets, geoms);
-  }
-  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
-}
-
-int geom_launches(int n_cluster_jobs, int n_gtiles) {
-  return (n_cluster_jobs > 0 ? 1 : 0) + (n_gtiles > 0 ? 2 : 0);
-}
-
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms, const int* imap,
-                    const double* fmap, const int* imap_off, int kmax, const double* lowpart, cudaStream_t s) {
+                    const double* fmap, const int* imap_off, int kmax, const double* syspart, cudaStream_t s) {
   if (n_jobs <= 0) return 0;
   return launch_pdl(k_finalize, dim3(n_jobs), dim3(kFinalizeThreads), 0, s, jobs, partials, geoms, imap, fmap,
-                    imap_off, kmax, lowpart) == cudaSuccess
+                    imap_off, kmax, syspart) == cudaSuccess
              ? 0
              : -1;
 }

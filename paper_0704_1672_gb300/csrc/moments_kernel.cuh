@@ -336,18 +336,38 @@ __device__ __forceinline__ void setup(T d0, T d1, T d2, const Xform<T>& xf, T& u
   rho = r2 * rinv;
 }
 
-// Sum of a 32-entry row of the transpose buffer in double, in a fixed tree order.  The float
-// lane sums are converted exactly; a float tree would add about 2 x 2^-24 of the row's
-// magnitude.  The additions go to the FP64 pipe, which the float recurrences leave idle.
+// Sum of a 32-entry row of the transpose buffer in a fixed tree order, compensated: every
+// addition is an error-free two-sum whose rounding error is carried along, so the float row
+// sum keeps about 48 bits (a plain float tree would add about 2 x 2^-24 of the row's
+// magnitude).  Float instructions only: on GB300 the FP64 pipe runs at 1/64 of the FP32 rate,
+// and a double tree (with its conversions) held the warps at the end of every tile.
+__device__ __forceinline__ void two_sum_ff(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
 __device__ __forceinline__ double row_sum32(const float* p) {
   const float4* v = reinterpret_cast<const float4*>(p);
-  double s[8];
+  float s[8], e[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const float4 w = v[k];
-    s[k] = ((double)w.x + (double)w.y) + ((double)w.z + (double)w.w);
+    float a, ea, b, eb;
+    two_sum_ff(w.x, w.y, a, ea);
+    two_sum_ff(w.z, w.w, b, eb);
+    two_sum_ff(a, b, s[k], e[k]);
+    e[k] += ea + eb;
   }
-  return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+#pragma unroll
+  for (int h = 4; h >= 1; h >>= 1)
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      float t, et;
+      two_sum_ff(s[k], s[k + h], t, et);
+      e[k] = (e[k] + e[k + h]) + et;
+      s[k] = t;
+    }
+  return (double)s[0] + (double)e[0];
 }
 
 __device__ __forceinline__ double row_sum32(const double* p) {
@@ -364,7 +384,7 @@ __device__ __forceinline__ double row_sum32(const double* p) {
 // Warp reduction of the per-lane accumulators into one double row `out[0..NACC)` (the
 // column-0 reals first, then the complex pairs, in slot order).  The warp transposes its
 // 32 x NACC block through its own shared-memory region and every lane tree-sums whole rows
-// in double (fixed order) and stores them.  No CTA barrier is involved.
+// (fixed order, compensated) and stores them in double.  No CTA barrier is involved.
 template <typename T, int L, int M0, int M1>
 __device__ __forceinline__ void warp_reduce_store(const Regs<T, L, M0, M1>& s, T* wb, double* out) {
   using R = Regs<T, L, M0, M1>;

@@ -98,7 +98,7 @@ struct tcm_ctx {
   int* d_imap = nullptr;      // (chunk, slot) -> packed component, both precisions
   int* d_imap_off = nullptr;  // [precision][L] offsets into d_imap
   // scratch
-  DevBuf desc, partials, gpart, counters, moms, escr, dpart, lowp, tiles;
+  DevBuf desc, partials, gpart, systk, counters, moms, escr, dpart, tiles;
   Stage stage[kStages];
   int stage_next = 0;
   void* pinned_small = nullptr;  // 256 B for small device->host reads
@@ -242,36 +242,7 @@ struct Plan {
   int tile_begin[kLmaxMax + 2] = {};
   int n_tile_ids = 0;
   size_t moms_doubles = 0;
-  std::vector<LowJob> ljobs;       // mixed precision: one low-degree pass per system with a job
-  std::vector<LowTile> ltiles;
 };
-
-// Mixed precision: one low-degree pass (k_lowmom) per system that has a computed moment job;
-// every job of that system takes its degrees l <= 2 from it.
-void plan_low(const tcm_system* systems, Plan& P) {
-  std::map<int, int> low_of;
-  int rows = 0;
-  for (MomJob& j : P.jobs) {
-    auto it = low_of.find(j.geom);
-    if (it == low_of.end()) {
-      const tcm_system& sy = systems[j.geom];
-      LowJob lj{};
-      lj.xyzq = sy.xyzq;
-      lj.n = sy.n;
-      lj.dtype = sy.dtype;
-      lj.geom = j.geom;
-      lj.tile_base = rows;
-      lj.n_tiles = (int)std::max<long long>(1, (sy.n + kLowTileAtoms - 1) / kLowTileAtoms);
-      for (int t = 0; t < lj.n_tiles; ++t) P.ltiles.push_back(LowTile{(int)P.ljobs.size(), t});
-      rows += lj.n_tiles;
-      it = low_of.emplace(j.geom, (int)P.ljobs.size()).first;
-      P.ljobs.push_back(lj);
-    }
-    const LowJob& lj = P.ljobs[it->second];
-    j.low_base = lj.tile_base;
-    j.low_tiles = lj.n_tiles;
-  }
-}
 
 void plan_job(tcm_ctx* c, int precision, MomJob& j, int& next_id) {
   const int nch = moments_nchunks(precision, j.L);
@@ -332,7 +303,6 @@ void build_tiles(int precision, Plan& P) {
 int ensure_moment_buffers(tcm_ctx* c, int precision, const Plan& P) {
   TRY(dev_ensure(c, c->partials, (size_t)std::max(P.n_tile_ids, 1) * moments_kmax(precision) * sizeof(double)));
   TRY(dev_ensure(c, c->tiles, (size_t)std::max(P.n_tiles, 1) * sizeof(MomTile)));
-  TRY(dev_ensure(c, c->lowp, std::max<size_t>(P.ltiles.size(), 1) * kLowSums * sizeof(double)));
   void* before = c->counters.p;
   TRY(dev_ensure(c, c->counters, 64 * sizeof(int)));
   if (c->counters.p != before) {
@@ -384,7 +354,7 @@ int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, 
     PhaseScope ps(c, TCM_PHASE_FINALIZE, 1);
     TRY_LAUNCH(launch_finalize(d_jobs, (int)P.jobs.size(), parts, d_geoms, c->d_imap, c->d_fmap,
                                c->d_imap_off + (precision == TCM_FP64 ? 0 : kLmaxMax + 2), kmax,
-                               static_cast<double*>(c->lowp.p), st));
+                               static_cast<double*>(c->gpart.p), st));
   }
   return TCM_OK;
 }
@@ -397,52 +367,76 @@ int moment_launches(int precision, const Plan& P) {
   return n;
 }
 
-// The low-degree pass of the mixed path (after step a1: it needs the centres).
-int run_low(tcm_ctx* c, const Plan& P, const LowJob* d_lj, const LowTile* d_lt, const SysGeom* d_geo, cudaStream_t st) {
-  if (P.ltiles.empty()) return TCM_OK;
-  PhaseScope ps(c, TCM_PHASE_GEOM, 1);
-  TRY_LAUNCH(launch_lowmom(d_lj, d_lt, (int)P.ltiles.size(), d_geo, static_cast<double*>(c->lowp.p), st));
+// The pass over the systems' atoms before the moment pass (syspass.cu): step a1 for the systems
+// whose centre or radius is not given, and the low-degree sums of the mixed path for every
+// system with a computed moment job.
+struct SysPlan {
+  std::vector<SysJob> jobs;
+  std::vector<SysTile> t1, t2;  // tiles of pass 1 (centroid) and pass 2 (radius, low-degree sums)
+  std::vector<int> of_system;   // system -> index of its SysJob, or -1
+  int rows = 0;
+};
+
+// used[s]: system s takes part in the call; low[s]: its low-degree sums are needed.
+void plan_sys(const tcm_system* systems, int n_systems, const std::vector<char>& used, const std::vector<char>& low,
+              SysPlan& S) {
+  S.of_system.assign(std::max(n_systems, 0), -1);
+  for (int s = 0; s < n_systems; ++s) {
+    if (!used[s]) continue;
+    const tcm_system& sy = systems[s];
+    const bool nc = !sy.has_center;
+    const bool nr = nc || sy.radius < 0.0;  // a radius given without its centre is recomputed
+    const bool nl = !low.empty() && low[s];
+    if (!nc && !nr && !nl) continue;
+    SysJob j{};
+    j.xyzq = sy.xyzq;
+    j.n = sy.n;
+    j.dtype = sy.dtype;
+    j.geom = s;
+    j.need_center = nc;
+    j.need_radius = nr;
+    j.need_low = nl;
+    j.atoms_per_tile = sys_tile_atoms(sy.n);
+    j.n_tiles = (int)std::max<long long>(1, (sy.n + j.atoms_per_tile - 1) / j.atoms_per_tile);
+    j.tile_base = S.rows;
+    S.rows += j.n_tiles;
+    const int ji = (int)S.jobs.size();
+    for (int t = 0; t < j.n_tiles; ++t) {
+      if (nc) S.t1.push_back(SysTile{ji, t});
+      if (nr || nl) S.t2.push_back(SysTile{ji, t});
+    }
+    S.of_system[s] = ji;
+    S.jobs.push_back(j);
+  }
+}
+
+// Mixed path: every computed moment job takes its degrees l <= 2 from its system's low sums.
+void link_low(const SysPlan& S, Plan& P) {
+  for (MomJob& j : P.jobs) {
+    const int si = S.of_system[j.geom];
+    if (si < 0 || !S.jobs[si].need_low) continue;
+    j.low_base = S.jobs[si].tile_base;
+    j.low_tiles = S.jobs[si].n_tiles;
+  }
+}
+
+// Partial rows and tickets of the system pass; the tickets are zeroed when allocated and every
+// launch leaves them zero.
+int ensure_sys_buffers(tcm_ctx* c, const SysPlan& S) {
+  TRY(dev_ensure(c, c->gpart, (size_t)std::max(S.rows, 1) * kSysPart * sizeof(double)));
+  void* before = c->systk.p;
+  TRY(dev_ensure(c, c->systk, std::max<size_t>(2 * S.jobs.size(), 64) * sizeof(int)));
+  if (c->systk.p != before) TRY_CUDA(cudaMemsetAsync(c->systk.p, 0, c->systk.cap, c->stream));
   return TCM_OK;
 }
 
-// Ticket counters of the a1 kernels: the tail of the gpart buffer (after ngt 4-double rows).
-int* geom_tickets(tcm_ctx* c, int ngt, int) {
-  return reinterpret_cast<int*>(static_cast<char*>(c->gpart.p) + (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64);
-}
-
-// Step a1 for the systems that need it (device only, no host round trip).
-// Step a1 jobs for the systems that need it (device only, no host round trip).  Float32
-// systems of at most kGeomClusterAtoms atoms come first and have no tiles (one cluster each);
-// the others are cut into kGeomTileAtoms tiles.  Returns the number of tiles.
-int add_geom_jobs(const tcm_system* systems, int n_systems, const std::vector<char>& used,
-                  std::vector<GeomJob>& gjobs, std::vector<GeomTile>& gtiles) {
-  int base = 0;
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int s = 0; s < n_systems; ++s) {
-      if (!used[s] || geom_known(systems[s])) continue;
-      const bool cluster = systems[s].dtype == TCM_F32 && systems[s].n <= kGeomClusterAtoms;
-      if (cluster != (pass == 0)) continue;
-      GeomJob g{};
-      g.xyzq = systems[s].xyzq;
-      g.n = systems[s].n;
-      g.dtype = systems[s].dtype;
-      g.geom = s;
-      g.need_center = systems[s].has_center ? 0 : 1;
-      g.need_radius = 1;
-      g.n_tiles = cluster ? 0 : (int)std::max<long long>(1, (g.n + kGeomTileAtoms - 1) / kGeomTileAtoms);
-      g.tile_base = base;
-      base += g.n_tiles;
-      for (int t = 0; t < g.n_tiles; ++t) gtiles.push_back(GeomTile{(int)gjobs.size(), t});
-      gjobs.push_back(g);
-    }
-  }
-  return base;
-}
-
-int cluster_jobs(const std::vector<GeomJob>& gjobs) {
-  int n = 0;
-  for (const GeomJob& g : gjobs) n += g.n_tiles == 0;
-  return n;
+int run_sys(tcm_ctx* c, const SysPlan& S, const SysJob* d_sj, const SysTile* d_t1, const SysTile* d_t2, SysGeom* d_geo,
+            cudaStream_t st) {
+  if (S.jobs.empty()) return TCM_OK;
+  PhaseScope ps(c, TCM_PHASE_GEOM, sys_launches((int)S.t1.size(), (int)S.t2.size()));
+  TRY_LAUNCH(launch_sys(d_sj, d_t1, (int)S.t1.size(), d_t2, (int)S.t2.size(), static_cast<double*>(c->gpart.p),
+                        static_cast<int*>(c->systk.p), d_geo, st));
+  return TCM_OK;
 }
 
 SysGeom host_geom(const tcm_system& s) {
@@ -482,7 +476,7 @@ void free_ctx(tcm_ctx* c) {
   cudaFree(c->d_ztab);
   cudaFree(c->d_imap);
   cudaFree(c->d_imap_off);
-  for (DevBuf* b : {&c->desc, &c->partials, &c->gpart, &c->counters, &c->moms, &c->escr, &c->dpart, &c->lowp, &c->tiles})
+  for (DevBuf* b : {&c->desc, &c->partials, &c->gpart, &c->systk, &c->counters, &c->moms, &c->escr, &c->dpart, &c->tiles})
     cudaFree(b->p);
   for (auto& st : c->stage) {
     if (st.host) cudaFreeHost(st.host);
@@ -642,24 +636,17 @@ int tcm_prepare(tcm_ctx_t c, tcm_system* s) {
   TRY(check_system(s, "tcm_prepare"));
   if (geom_known(*s)) return TCM_OK;
   std::vector<char> used(1, 1);
-  std::vector<GeomJob> gjobs;
-  std::vector<GeomTile> gtiles;
-  const int ngt = add_geom_jobs(s, 1, used, gjobs, gtiles);
+  SysPlan S;
+  plan_sys(s, 1, used, {}, S);
   std::vector<SysGeom> geoms{host_geom(*s)};
   Packer pk;
-  const size_t o_geo = pk.add(geoms), o_gj = pk.add(gjobs), o_gt = pk.add(gtiles);
+  const size_t o_geo = pk.add(geoms), o_sj = pk.add(S.jobs), o_t1 = pk.add(S.t1), o_t2 = pk.add(S.t2);
+  TRY(ensure_sys_buffers(c, S));
   char* base = nullptr;
   TRY(upload(c, pk, &base));
-  TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
-  if (ngt > 0)  // the tiled kernels take tickets
-    TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
-  {
-    PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches(cluster_jobs(gjobs), ngt));
-    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(), cluster_jobs(gjobs),
-                           reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
-                           static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
-  }
+  TRY(run_sys(c, S, reinterpret_cast<SysJob*>(base + o_sj), reinterpret_cast<SysTile*>(base + o_t1),
+              reinterpret_cast<SysTile*>(base + o_t2), d_geo, c->stream));
   TRY_CUDA(cudaMemcpyAsync(c->pinned_small, d_geo, sizeof(SysGeom), cudaMemcpyDeviceToHost, c->stream));
   TRY_CUDA(cudaStreamSynchronize(c->stream));
   const SysGeom* g = static_cast<const SysGeom*>(c->pinned_small);
@@ -694,33 +681,25 @@ int tcm_moments(tcm_ctx_t c, const tcm_system* s, const double* rot, int lmax, i
   P.jobs.push_back(j);
   P.n_tile_ids = next;
   build_tiles(precision, P);
-  if (precision == TCM_MIXED) plan_low(s, P);
-  std::vector<char> used(1, 1);
-  std::vector<GeomJob> gjobs;
-  std::vector<GeomTile> gtiles;
-  const int ngt = add_geom_jobs(s, 1, used, gjobs, gtiles);
+  std::vector<char> used(1, 1), low(1, precision == TCM_MIXED ? 1 : 0);
+  SysPlan S;
+  plan_sys(s, 1, used, low, S);
+  link_low(S, P);
   std::vector<SysGeom> geoms{host_geom(*s)};
   Packer pk;
-  const size_t o_geo = pk.add(geoms), o_job = pk.add(P.jobs), o_tile = pk.add(P.groups), o_gj = pk.add(gjobs),
-               o_gt = pk.add(gtiles), o_lj = pk.add(P.ljobs), o_lt = pk.add(P.ltiles);
+  const size_t o_geo = pk.add(geoms), o_job = pk.add(P.jobs), o_tile = pk.add(P.groups), o_sj = pk.add(S.jobs),
+               o_t1 = pk.add(S.t1), o_t2 = pk.add(S.t2);
   TRY(ensure_moment_buffers(c, precision, P));
+  TRY(ensure_sys_buffers(c, S));
   char* base = nullptr;
   TRY(upload(c, pk, &base));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   TRY(run_expand(c, P, reinterpret_cast<MomJob*>(base + o_job), reinterpret_cast<MomGroup*>(base + o_tile), c->stream));
-  if (!gjobs.empty()) {
-    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
-    if (ngt > 0)  // the tiled kernels take tickets
-      TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
-    PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches(cluster_jobs(gjobs), ngt));
-    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(), cluster_jobs(gjobs),
-                           reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
-                           static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
-  }
-  TRY(run_low(c, P, reinterpret_cast<LowJob*>(base + o_lj), reinterpret_cast<LowTile*>(base + o_lt), d_geo, c->stream));
+  TRY(run_sys(c, S, reinterpret_cast<SysJob*>(base + o_sj), reinterpret_cast<SysTile*>(base + o_t1),
+              reinterpret_cast<SysTile*>(base + o_t2), d_geo, c->stream));
   TRY(run_moments(c, precision, P, reinterpret_cast<MomJob*>(base + o_job), d_geo, c->stream));
   out->lmax = lmax;
-  if (!gjobs.empty()) {
+  if (!geom_known(*s)) {
     TRY_CUDA(cudaMemcpyAsync(c->pinned_small, d_geo, sizeof(SysGeom), cudaMemcpyDeviceToHost, c->stream));
     TRY_CUDA(cudaStreamSynchronize(c->stream));
     const SysGeom* g = static_cast<const SysGeom*>(c->pinned_small);
@@ -880,8 +859,10 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
       return -2 - ((int)cached.size() - 1);
     }
     JobKey key{sys, L, rot_item};
-    auto itr = job_of.find(key);
-    if (itr != job_of.end()) return itr->second;
+    if (rot_item < 0) {  // rotated jobs are unique to their item: no lookup
+      auto itr = job_of.find(key);
+      if (itr != job_of.end()) return itr->second;
+    }
     MomJob j{};
     j.xyzq = systems[sys].xyzq;
     j.n = systems[sys].n;
@@ -897,7 +878,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
     moff += (size_t)(L + 1) * (L + 1);
     const int id = (int)P.jobs.size();
     P.jobs.push_back(j);
-    job_of[key] = id;
+    if (rot_item < 0) job_of[key] = id;
     return id;
   };
   std::vector<EulerZYZ> rots;  // Euler record of W rotB per rotate-from-cache item
@@ -938,7 +919,12 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   TRY(dev_ensure(c, c->moms, std::max<size_t>(moff, 1) * sizeof(double)));
   for (size_t ji = 0; ji < P.jobs.size(); ++ji) P.jobs[ji].out = static_cast<double*>(c->moms.p) + job_moff[ji];
   build_tiles(precision, P);
-  if (precision == TCM_MIXED) plan_low(systems, P);
+  std::vector<char> low(n_systems, 0);
+  if (precision == TCM_MIXED)
+    for (const MomJob& j : P.jobs) low[j.geom] = 1;
+  SysPlan S;
+  plan_sys(systems, n_systems, used, low, S);
+  link_low(S, P);
   // cached sides follow the computed jobs in the descriptor array (not finalised)
   const int n_computed = (int)P.jobs.size();
   for (auto& d : pd) {
@@ -949,19 +935,14 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   all_jobs.insert(all_jobs.end(), cached.begin(), cached.end());
   int Lmax_items = 0;
   for (int64_t k = 0; k < n_items; ++k) Lmax_items = std::max(Lmax_items, (int)items[k].lmax);
-  std::vector<GeomJob> gjobs;
-  std::vector<GeomTile> gtiles;
-  const int ngt = add_geom_jobs(systems, n_systems, used, gjobs, gtiles);
   std::vector<SysGeom> geoms(std::max(n_systems, 1));
   for (int s = 0; s < n_systems; ++s) geoms[s] = host_geom(systems[s]);
   Packer pk;
-  const size_t o_geo = pk.add(geoms), o_job = pk.add(all_jobs), o_tile = pk.add(P.groups), o_gj = pk.add(gjobs),
-               o_gt = pk.add(gtiles), o_it = pk.add(pd), o_rot = pk.add(rots), o_lj = pk.add(P.ljobs),
-               o_lt = pk.add(P.ltiles);
+  const size_t o_geo = pk.add(geoms), o_job = pk.add(all_jobs), o_tile = pk.add(P.groups), o_sj = pk.add(S.jobs),
+               o_t1 = pk.add(S.t1), o_t2 = pk.add(S.t2), o_it = pk.add(pd), o_rot = pk.add(rots);
   // every buffer the launches touch is sized before anything is queued (no reallocation
   // may happen while a graph is being captured)
-  if (!gjobs.empty())
-    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
+  TRY(ensure_sys_buffers(c, S));
   TRY(ensure_moment_buffers(c, precision, P));
   char* base = nullptr;
   TRY(upload(c, pk, &base));
@@ -969,15 +950,8 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   const MomJob* d_jobs = reinterpret_cast<MomJob*>(base + o_job);
   auto enqueue = [&](cudaStream_t st) -> int {
     TRY(run_expand(c, P, d_jobs, reinterpret_cast<MomGroup*>(base + o_tile), st));
-    if (!gjobs.empty()) {
-      if (ngt > 0)  // the tiled kernels take tickets
-        TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), st));
-      PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches(cluster_jobs(gjobs), ngt));
-      TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(), cluster_jobs(gjobs),
-                             reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
-                             static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, st));
-    }
-    TRY(run_low(c, P, reinterpret_cast<LowJob*>(base + o_lj), reinterpret_cast<LowTile*>(base + o_lt), d_geo, st));
+    TRY(run_sys(c, S, reinterpret_cast<SysJob*>(base + o_sj), reinterpret_cast<SysTile*>(base + o_t1),
+                reinterpret_cast<SysTile*>(base + o_t2), d_geo, st));
     TRY(run_moments(c, precision, P, d_jobs, d_geo, st));
     PhaseScope ps(c, TCM_PHASE_CONTRACT, 1);
     TRY_LAUNCH(launch_contract(reinterpret_cast<PairDesc*>(base + o_it), (int)n_items, Lmax_items, d_jobs, d_geo,
@@ -988,14 +962,14 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   if (!c->graphs || c->prof || !c->cap_stream) return enqueue(c->stream);
   // Replay a captured graph of the launch sequence when this call has the same shape and
   // buffers as the captured one (only the uploaded descriptor contents differ).
-  std::vector<long long> key = {precision, G != nullptr, (long long)(uintptr_t)G, ngt, (long long)gjobs.size(), (long long)P.jobs.size(), P.n_tile_ids,
-                                (long long)n_items, Lmax_items, (long long)cluster_jobs(gjobs), (long long)o_geo, (long long)o_job, (long long)o_tile,
-                                (long long)o_gj, (long long)o_gt, (long long)o_it, (long long)o_rot, (long long)rots.empty(), (long long)(uintptr_t)base,
-                                (long long)(uintptr_t)c->gpart.p, (long long)(uintptr_t)c->partials.p,
-                                (long long)(uintptr_t)c->counters.p, (long long)(uintptr_t)E,
-                                (long long)(uintptr_t)status, (long long)P.ltiles.size(), (long long)o_lj,
-                                (long long)o_lt, (long long)(uintptr_t)c->lowp.p, (long long)P.groups.size(),
-                                (long long)P.n_tiles, (long long)(uintptr_t)c->tiles.p};
+  std::vector<long long> key = {precision, G != nullptr, (long long)(uintptr_t)G, (long long)S.jobs.size(),
+                                (long long)S.t1.size(), (long long)S.t2.size(), (long long)P.jobs.size(), P.n_tile_ids,
+                                (long long)n_items, Lmax_items, (long long)o_geo, (long long)o_job, (long long)o_tile,
+                                (long long)o_sj, (long long)o_t1, (long long)o_t2, (long long)o_it, (long long)o_rot,
+                                (long long)rots.empty(), (long long)(uintptr_t)base, (long long)(uintptr_t)c->gpart.p,
+                                (long long)(uintptr_t)c->systk.p, (long long)(uintptr_t)c->partials.p,
+                                (long long)(uintptr_t)c->counters.p, (long long)(uintptr_t)E, (long long)(uintptr_t)status,
+                                (long long)P.groups.size(), (long long)P.n_tiles, (long long)(uintptr_t)c->tiles.p};
   for (int L = 0; L <= kLmaxMax + 1; ++L) key.push_back(P.tile_begin[L]);
   if (!c->gexec || key != c->gkey) {
     // by default capture only a shape seen twice in a row: a stream of changing shapes
@@ -1030,7 +1004,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   }
   TRY_CUDA(cudaGraphLaunch(c->gexec, c->stream));
   ++c->graph_launches;
-  c->launches[TCM_PHASE_GEOM] += geom_launches(cluster_jobs(gjobs), ngt) + (P.ltiles.empty() ? 0 : 1) +
+  c->launches[TCM_PHASE_GEOM] += (S.jobs.empty() ? 0 : sys_launches((int)S.t1.size(), (int)S.t2.size())) +
                                   (P.groups.empty() ? 0 : 1);
   c->launches[TCM_PHASE_MOMENTS] += moment_launches(precision, P);
   c->launches[TCM_PHASE_FINALIZE] += 1;
@@ -1048,9 +1022,8 @@ int direct_items(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, int64_t 
   for (auto& s : sys)
     if (s.has_center) s.radius = std::max(s.radius, 0.0);  // the direct sum needs centres only
   std::vector<char> used(2, 1);
-  std::vector<GeomJob> gjobs;
-  std::vector<GeomTile> gtiles;
-  const int ngt = add_geom_jobs(sys, 2, used, gjobs, gtiles);
+  SysPlan S;
+  plan_sys(sys, 2, used, {}, S);
   std::vector<SysGeom> geoms{host_geom(sys[0]), host_geom(sys[1])};
   std::vector<double> xf(12 * (size_t)n);
   for (int64_t k = 0; k < n; ++k) {
@@ -1061,22 +1034,16 @@ int direct_items(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, int64_t 
     for (int d = 0; d < 3; ++d) xf[12 * k + 9 + d] = R0[3 * k + d];
   }
   Packer pk;
-  const size_t o_geo = pk.add(geoms), o_xf = pk.add(xf), o_gj = pk.add(gjobs), o_gt = pk.add(gtiles);
+  const size_t o_geo = pk.add(geoms), o_xf = pk.add(xf), o_sj = pk.add(S.jobs), o_t1 = pk.add(S.t1),
+               o_t2 = pk.add(S.t2);
   const int nblk = direct_blocks(A->n);
-  if (!gjobs.empty())
-    TRY(dev_ensure(c, c->gpart, (size_t)std::max(ngt, 1) * 4 * sizeof(double) + 64 + sizeof(int) * gjobs.size()));
+  TRY(ensure_sys_buffers(c, S));
   TRY(dev_ensure(c, c->dpart, (size_t)std::max<int64_t>(nblk * n, 1) * sizeof(double)));
   char* base = nullptr;
   TRY(upload(c, pk, &base));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
-  if (!gjobs.empty()) {
-    if (ngt > 0)  // the tiled kernels take tickets
-      TRY_CUDA(cudaMemsetAsync(geom_tickets(c, ngt, (int)gjobs.size()), 0, sizeof(int) * gjobs.size(), c->stream));
-    PhaseScope ps(c, TCM_PHASE_GEOM, geom_launches(cluster_jobs(gjobs), ngt));
-    TRY_LAUNCH(launch_geom(reinterpret_cast<GeomJob*>(base + o_gj), (int)gjobs.size(), cluster_jobs(gjobs),
-                           reinterpret_cast<GeomTile*>(base + o_gt), (int)gtiles.size(),
-                           static_cast<double*>(c->gpart.p), geom_tickets(c, ngt, (int)gjobs.size()), d_geo, c->stream));
-  }
+  TRY(run_sys(c, S, reinterpret_cast<SysJob*>(base + o_sj), reinterpret_cast<SysTile*>(base + o_t1),
+              reinterpret_cast<SysTile*>(base + o_t2), d_geo, c->stream));
   const int nlaunch = (int)((n + 65534) / 65535) * (nblk > 0 ? 2 : 1);
   PhaseScope ps(c, TCM_PHASE_DIRECT, nlaunch);
   TRY_LAUNCH(launch_direct(A->xyzq, A->n, A->dtype, B->xyzq, B->n, B->dtype, d_geo,

@@ -146,7 +146,7 @@ struct MomJob {    // one moment set: a system at one Lmax under one rotation
   int tile_base;   // id of the job's first tile; tile id = base + chunk * tpc + t
   double rot[9];   // row-major, identity when unrotated
   double* out;     // packed moments, (L+1)^2 doubles
-  int low_base;    // mixed precision: first tile of the system's low-degree sums (LowJob), and
+  int low_base;    // mixed precision: first tile row of the system's low-degree sums (SysJob), and
   int low_tiles;   // their count; 0 = the degrees l <= 2 keep the float kernel's values
 };
 
@@ -164,19 +164,22 @@ struct MomGroup {  // the tiles of one (job, chunk), written to the tile list on
   int first;       // position of its first tile in the tile list
 };
 
-struct GeomJob {   // a1: centroid and/or radius of one system
+// The pass over a system's atoms before the moment pass (syspass.cu): pass 1 its centroid
+// (need_center), pass 2 its radius (need_radius) and, for the mixed path, its low-degree sums
+// (need_low).  A system's warp tiles depend on its atom count only (sys_tile_atoms).
+struct SysJob {
   const void* xyzq;
   long long n;
   int dtype;
-  int geom;
-  int need_center;
-  int need_radius;
-  int tile_base;
+  int geom;          // index into the SysGeom array
+  int need_center, need_radius, need_low;
+  int tile_base;     // row of its first tile in the partials (kSysPart doubles per row)
   int n_tiles;
+  int atoms_per_tile;
 };
 
-struct GeomTile {
-  int gjob;
+struct SysTile {
+  int job;
   int t;
 };
 
@@ -188,29 +191,11 @@ struct GeomTile {
 // are then accurate to about 2^-44 of their terms instead of the float recurrence's 2^-24.
 constexpr int kLowSums = 10;            // S, P_x, P_y, P_z, T_xx, T_xy, T_xz, T_yy, T_yz, T_zz
 constexpr int kLowLmax = 2;             // degrees replaced by the low-degree sums
-constexpr int kLowAtomsPerLane = 64;
-constexpr int kLowTileAtoms = 32 * kLowAtomsPerLane;  // atoms per warp tile
-constexpr int kLowThreads = 256;
 
-struct LowJob {
-  const void* xyzq;
-  long long n;
-  int dtype;
-  int geom;        // index into the SysGeom array
-  int tile_base;   // row of its first tile in the low-sum partials (kLowSums doubles per row)
-  int n_tiles;
-};
-
-struct LowTile {
-  int job;
-  int t;
-};
-
-constexpr int kGeomTileAtoms = 256;  // small tiles: the per-atom double arithmetic spreads over many SMs
-constexpr int kGeomClusterCTAs = 8;     // CTAs per cluster (portable cluster size)
-constexpr int kGeomClusterThreads = 512;
-constexpr int kGeomClusterPer = 8;      // atoms per thread, held in registers
-constexpr long long kGeomClusterAtoms = (long long)kGeomClusterCTAs * kGeomClusterThreads * kGeomClusterPer;
+constexpr int kSysThreads = 256;
+constexpr int kSysPartR2 = 3;    // partial row: the centroid sums [0, 3), the tile's max |x - c|^2,
+constexpr int kSysPartLow = 4;   // and the low-degree sums [4, 4 + kLowSums)
+constexpr int kSysPart = kSysPartLow + kLowSums;
 
 // Programmatic dependent launch: a kernel launched with programmatic stream serialization
 // is set up while its predecessor drains; pdl_wait() blocks until the predecessor grid has
@@ -259,26 +244,22 @@ int moments_nchunks(int precision, int L);
 // 2 (kLmaxMax + 2) entries, FP64 first, each block ending with its total).
 void finalize_tables(std::vector<int>& imap_off, std::vector<int>& imap, std::vector<double>& fmap);
 
-// a1.  The first n_cluster_jobs geometry jobs (float32 systems of at most kGeomClusterAtoms atoms,
-// no tiles) take one launch of one thread-block cluster each; the others go through two tiled
-// launches (the coordinate sums, then the largest |x - c|^2) spread over many SMs, because their
-// per-atom double arithmetic would saturate the FP64 pipe of a few.  tickets: one int per
-// geometry job, zero on entry (left zero on exit).  geom_launches gives the number of kernels
-// launch_geom queues.
-int launch_geom(const GeomJob* gjobs, int n_gjobs, int n_cluster_jobs, const GeomTile* gtiles, int n_gtiles,
-                double* gpart, int* tickets, SysGeom* geoms, cudaStream_t s);
-int geom_launches(int n_cluster_jobs, int n_gtiles);
-// Low-degree sums (LowJob): one warp per tile, kLowSums doubles per tile row of lowpart.  Needs
-// the systems' centres (launched after launch_geom, programmatic serialization).
-int launch_lowmom(const LowJob* ljobs, const LowTile* ltiles, int n_ltiles, const SysGeom* geoms, double* lowpart,
-                  cudaStream_t s);
+// Step a1 and the low-degree sums: pass 1 over the n1 tiles of the systems that need a centroid,
+// then pass 2 over the n2 tiles of those that need a radius or low-degree sums (programmatic
+// serialization).  part: kSysPart doubles per tile row; tickets: two ints per job, zero on entry
+// and left zero.
+int launch_sys(const SysJob* jobs, const SysTile* t1, int n1, const SysTile* t2, int n2, double* part, int* tickets,
+               SysGeom* geoms, cudaStream_t s);
+int sys_launches(int n1, int n2);
+int sys_tile_atoms(long long n);
 // Step a3: one CTA per job.  imap + imap_off[L] lists, per (chunk, slot) of degree L, the packed
 // component it holds (-1 for none), nch(L) x kmax entries; fmap beside it holds that
 // component's F_lm with the sign of the kernels' H variables.
-// Jobs with low_tiles > 0 take their degrees l <= min(kLowLmax, L) from the low-degree sums
-// (lowpart rows [low_base, low_base + low_tiles)) rotated by the job's rotation.
+// Jobs with low_tiles > 0 take their degrees l <= min(kLowLmax, L) from the low-degree sums of
+// their system (rows [low_base, low_base + low_tiles) of the system-pass partials syspart)
+// rotated by the job's rotation.
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms,
-                    const int* imap, const double* fmap, const int* imap_off, int kmax, const double* lowpart,
+                    const int* imap, const double* fmap, const int* imap_off, int kmax, const double* syspart,
                     cudaStream_t s);
 
 

@@ -33,7 +33,8 @@ constexpr int kNaTilesPerChunk = (int)(kNaMaxAtoms / kNaTileAtoms);  // 64
 constexpr int kNaMaxChunks = 10;                                     // most chunks of any (precision, Lmax)
 constexpr int kNaPartialDoubles = kNaTilesPerChunk * 800;            // max over plans of chunks * kmax = 800
 constexpr int kNaMaxTiles = kNaTilesPerChunk * kNaMaxChunks;
-constexpr int kNaGeomTiles = (int)((kNaMaxAtoms + kGeomTileAtoms - 1) / kGeomTileAtoms);
+// system-pass tiles: sys_tile_atoms gives at most 64 tiles below 131,072 atoms and tiles of 2,048 above
+constexpr int kNaSysTiles = (int)((kNaMaxAtoms + 2047) / 2048) > 64 ? (int)((kNaMaxAtoms + 2047) / 2048) : 64;
 constexpr int kNaCompTotal = 5525;  // sum over L = 0..24 of (L+1)^2
 
 // Layout of the scratch array (byte offsets, 256-byte aligned sections).
@@ -42,19 +43,16 @@ constexpr size_t kOffPartials = 0;
 constexpr size_t kOffTiles = align256(kOffPartials + sizeof(double) * kNaPartialDoubles);
 constexpr size_t kOffJob = align256(kOffTiles + sizeof(MomTile) * kNaMaxTiles);
 constexpr size_t kOffGeom = align256(kOffJob + sizeof(MomJob));
-constexpr size_t kOffGJob = align256(kOffGeom + sizeof(SysGeom));
-constexpr size_t kOffGTiles = align256(kOffGJob + sizeof(GeomJob));
-constexpr size_t kOffGPart = align256(kOffGTiles + sizeof(GeomTile) * kNaGeomTiles);
-constexpr size_t kOffCounters = align256(kOffGPart + sizeof(double) * 4 * kNaGeomTiles);
+constexpr size_t kOffSJob = align256(kOffGeom + sizeof(SysGeom));
+constexpr size_t kOffSTiles1 = align256(kOffSJob + sizeof(SysJob));
+constexpr size_t kOffSTiles2 = align256(kOffSTiles1 + sizeof(SysTile) * kNaSysTiles);
+constexpr size_t kOffSPart = align256(kOffSTiles2 + sizeof(SysTile) * kNaSysTiles);
+constexpr size_t kOffCounters = align256(kOffSPart + sizeof(double) * kSysPart * kNaSysTiles);
 constexpr int kNaImapInts = 4 * kNaCompTotal;  // room for both precisions' (chunk, slot) maps
 constexpr size_t kOffImapOff = align256(kOffCounters + sizeof(int) * 64);
 constexpr size_t kOffImap = align256(kOffImapOff + sizeof(int) * 2 * (kLmaxMax + 2));
 constexpr size_t kOffFmap = align256(kOffImap + sizeof(int) * kNaImapInts);
-constexpr int kNaLowTiles = (int)((kNaMaxAtoms + kLowTileAtoms - 1) / kLowTileAtoms);
-constexpr size_t kOffLowJob = align256(kOffFmap + sizeof(double) * kNaImapInts);
-constexpr size_t kOffLowTiles = align256(kOffLowJob + sizeof(LowJob));
-constexpr size_t kOffLowPart = align256(kOffLowTiles + sizeof(LowTile) * kNaLowTiles);
-constexpr size_t kScratchBytes = align256(kOffLowPart + sizeof(double) * kLowSums * kNaLowTiles);
+constexpr size_t kScratchBytes = align256(kOffFmap + sizeof(double) * kNaImapInts);
 // The size stated in include/tcm.h (TCM_NOALLOC_SCRATCH_BYTES) must be this layout's.
 static_assert(kScratchBytes == TCM_NOALLOC_SCRATCH_BYTES, "tcm.h states the wrong scratch size");
 
@@ -98,21 +96,18 @@ int setup_device(int dev, char** out) {
 
 // Writes one call's descriptors into the scratch and clears the work counters.  The
 // descriptors travel as kernel arguments, so no host staging buffer is involved.
-__global__ void k_noalloc_prepare(char* base, MomJob job, SysGeom geom, GeomJob gjob, LowJob ljob, int n_gtiles,
-                                  int nch, int tpc) {
+__global__ void k_noalloc_prepare(char* base, MomJob job, SysGeom geom, SysJob sjob, int nch, int tpc) {
   MomTile* tiles = reinterpret_cast<MomTile*>(base + kOffTiles);
-  GeomTile* gtiles = reinterpret_cast<GeomTile*>(base + kOffGTiles);
-  LowTile* ltiles = reinterpret_cast<LowTile*>(base + kOffLowTiles);
+  SysTile* t1 = reinterpret_cast<SysTile*>(base + kOffSTiles1);
+  SysTile* t2 = reinterpret_cast<SysTile*>(base + kOffSTiles2);
   int* counters = reinterpret_cast<int*>(base + kOffCounters);
   if (threadIdx.x == 0) {
     *reinterpret_cast<MomJob*>(base + kOffJob) = job;
     *reinterpret_cast<SysGeom*>(base + kOffGeom) = geom;
-    *reinterpret_cast<GeomJob*>(base + kOffGJob) = gjob;
-    *reinterpret_cast<LowJob*>(base + kOffLowJob) = ljob;
+    *reinterpret_cast<SysJob*>(base + kOffSJob) = sjob;
   }
   for (int k = threadIdx.x; k < 64; k += blockDim.x) counters[k] = 0;
-  for (int k = threadIdx.x; k < n_gtiles; k += blockDim.x) gtiles[k] = GeomTile{0, k};
-  for (int k = threadIdx.x; k < job.low_tiles; k += blockDim.x) ltiles[k] = LowTile{0, k};
+  for (int k = threadIdx.x; k < sjob.n_tiles; k += blockDim.x) t1[k] = t2[k] = SysTile{0, k};
   for (int k = threadIdx.x; k < nch * tpc; k += blockDim.x) tiles[k] = MomTile{0, k / tpc, k % tpc, k};
 }
 
@@ -154,45 +149,38 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   job.tile_base = 0;
   for (int k = 0; k < 9; ++k) job.rot[k] = rot ? rot[k] : ((k % 4 == 0) ? 1.0 : 0.0);
   job.out = q_out;
-  LowJob lj{};  // mixed precision: degrees l <= 2 from the float-float low-degree sums, as tcm_moments
-  lj.xyzq = s->xyzq;
-  lj.n = s->n;
-  lj.dtype = s->dtype;
-  lj.geom = 0;
-  lj.tile_base = 0;
-  lj.n_tiles = (int)std::max<long long>(1, (s->n + kLowTileAtoms - 1) / kLowTileAtoms);
-  if (lj.n_tiles > kNaLowTiles) return na_err(TCM_EINVAL, "tcm_moments_noalloc: request exceeds the fixed scratch");
-  job.low_base = 0;
-  job.low_tiles = precision == TCM_MIXED ? lj.n_tiles : 0;
-  const bool known = s->has_center && s->radius >= 0.0;
   SysGeom geom{};
   for (int d = 0; d < 3; ++d) geom.c[d] = s->has_center ? s->center[d] : 0.0;
   geom.a = s->radius >= 0.0 ? s->radius : 0.0;
-  GeomJob gj{};
-  gj.xyzq = s->xyzq;
-  gj.n = s->n;
-  gj.dtype = s->dtype;
-  gj.geom = 0;
-  gj.need_center = s->has_center ? 0 : 1;
-  gj.need_radius = 1;
-  gj.tile_base = 0;
-  gj.n_tiles = (s->dtype == TCM_F32 && s->n <= kGeomClusterAtoms)
-                   ? 0
-                   : (int)std::max<long long>(1, (s->n + kGeomTileAtoms - 1) / kGeomTileAtoms);
+  // the pass over the atoms before the moment pass, as tcm_moments plans it: the centroid when
+  // no centre is given, the radius when no radius is given, and the low-degree sums of the
+  // mixed path (its degrees l <= 2)
+  SysJob sj{};
+  sj.xyzq = s->xyzq;
+  sj.n = s->n;
+  sj.dtype = s->dtype;
+  sj.geom = 0;
+  sj.need_center = s->has_center ? 0 : 1;
+  sj.need_radius = (sj.need_center || s->radius < 0.0) ? 1 : 0;
+  sj.need_low = precision == TCM_MIXED ? 1 : 0;
+  sj.atoms_per_tile = sys_tile_atoms(s->n);
+  sj.n_tiles = (int)std::max<long long>(1, (s->n + sj.atoms_per_tile - 1) / sj.atoms_per_tile);
+  sj.tile_base = 0;
+  if (sj.n_tiles > kNaSysTiles) return na_err(TCM_EINVAL, "tcm_moments_noalloc: request exceeds the fixed scratch");
+  job.low_base = 0;
+  job.low_tiles = sj.need_low ? sj.n_tiles : 0;
+  const int n1 = sj.need_center ? sj.n_tiles : 0;
+  const int n2 = (sj.need_radius || sj.need_low) ? sj.n_tiles : 0;
 
   MomJob* d_job = reinterpret_cast<MomJob*>(base + kOffJob);
   SysGeom* d_geom = reinterpret_cast<SysGeom*>(base + kOffGeom);
-  k_noalloc_prepare<<<1, 256, 0, st>>>(base, job, geom, gj, lj, known ? 0 : gj.n_tiles, nch, tpc);
+  k_noalloc_prepare<<<1, 256, 0, st>>>(base, job, geom, sj, nch, tpc);
   if (cudaPeekAtLastError() != cudaSuccess) return na_err(TCM_ECUDA, "tcm_moments_noalloc: launch failed");
-  if (!known && launch_geom(reinterpret_cast<GeomJob*>(base + kOffGJob), 1, gj.n_tiles == 0 ? 1 : 0,
-                            reinterpret_cast<GeomTile*>(base + kOffGTiles),
-                            gj.n_tiles, reinterpret_cast<double*>(base + kOffGPart),
-                            reinterpret_cast<int*>(base + kOffCounters) + 40, d_geom, st) != 0)
+  if ((n1 > 0 || n2 > 0) &&
+      launch_sys(reinterpret_cast<SysJob*>(base + kOffSJob), reinterpret_cast<SysTile*>(base + kOffSTiles1), n1,
+                 reinterpret_cast<SysTile*>(base + kOffSTiles2), n2, reinterpret_cast<double*>(base + kOffSPart),
+                 reinterpret_cast<int*>(base + kOffCounters) + 40, d_geom, st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: centre/radius launch failed");
-  if (job.low_tiles > 0 && launch_lowmom(reinterpret_cast<LowJob*>(base + kOffLowJob),
-                                          reinterpret_cast<LowTile*>(base + kOffLowTiles), job.low_tiles, d_geom,
-                                          reinterpret_cast<double*>(base + kOffLowPart), st) != 0)
-    return na_err(TCM_ECUDA, "tcm_moments_noalloc: low-degree launch failed");
   int num_sms = 0;
   if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: cudaDeviceGetAttribute failed");
@@ -204,7 +192,7 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   if (launch_finalize(d_job, 1, reinterpret_cast<double*>(base + kOffPartials), d_geom,
                       reinterpret_cast<int*>(base + kOffImap), reinterpret_cast<double*>(base + kOffFmap),
                       reinterpret_cast<int*>(base + kOffImapOff) + (precision == TCM_FP64 ? 0 : kLmaxMax + 2),
-                      kmax, reinterpret_cast<double*>(base + kOffLowPart), st) != 0)
+                      kmax, reinterpret_cast<double*>(base + kOffSPart), st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: finalisation launch failed");
   if (geom_out && cudaMemcpyAsync(geom_out, d_geom, sizeof(SysGeom), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: copy of the centre and radius failed");
