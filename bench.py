@@ -54,6 +54,10 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-pes-grid", action="store_true", help="skip the surface-scan measurement")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--only", choices=["protein_pes_scan", "uneven_pairs"], default=None,
+                   help="run one of the other workloads alone and print its record (for profiling captures)")
+    p.add_argument("--orientations", type=int, default=10000,
+                   help="orientations of B in the headline workload (10,000; fewer only for profiling captures)")
     return p.parse_args()
 
 
@@ -364,7 +368,7 @@ class Timer:
 def config4_cfg(s):
     atoms = len(s.A) + len(s.R0) * len(s.B)
     return {"workload": "large assembly: A = 1,000,000 charges +-1 (2% excess) in an 80-100 A shell, B = 50,000-atom "
-                        "random-walk ligand, 10,000 orientations of B, |R0| in [max(150, 1.05(a_A+a_B)), 300] A, "
+                        f"random-walk ligand, {len(s.R0):,} orientations of B, |R0| in [max(150, 1.05(a_A+a_B)), 300] A, "
                         "Lmax=24, B's moments recomputed per orientation",
             "n_atoms_A": len(s.A), "n_atoms_B": len(s.B), "orientations": len(s.R0), "lmax": s.L,
             "atom_moments_per_step": atoms, "energies_per_step": len(s.R0), "coords": "float32 (x,y,z,q)",
@@ -390,7 +394,7 @@ def run_ours(args, rank, world, dist):
     timer = Timer(torch, stream)
 
     # ---- headline: large assembly
-    s = synth.large_assembly()
+    s = synth.large_assembly(n_orient=args.orientations)
     k = len(s.R0)
     L = s.L
     cfg = config4_cfg(s)
@@ -768,6 +772,26 @@ def plain_fp64_config4(ctx, tcm, torch, A, B, s, n_orient=8):
             "how": "per orientation: tcm_moments(B, FP64, rotated) + tcm_energy (synchronous); A once per step"}
 
 
+def run_only(args):
+    """One of the other workloads alone (its record as printed in the full line)."""
+    import torch
+
+    from paper_0704_1672_gb300 import autotune, build, synth, tcm
+    build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    smx = sm_max_mhz()
+    stream = torch.cuda.current_stream()
+    prec = tcm.TCM_MIXED if args.precision == "mixed" else tcm.TCM_FP64
+    if args.only == "protein_pes_scan":
+        rec = bench_config2(torch, tcm, synth, autotune, Timer(torch, stream), stream, prec,
+                            n_sm * FP32_LANES_PER_SM * smx * 1e6 / 1e12, n_sm * FP64_PER_SM_CLK * smx * 1e6 / 1e9,
+                            n_sm, smx, steps=args.steps)
+    else:
+        rec = bench_config3(torch, tcm, synth, stream, prec)
+    print(json.dumps({args.only: rec}), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -782,6 +806,8 @@ def main():
         dist = tdist
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.only:
+        run_only(args)
     else:
         run_ours(args, rank, world, dist)
     if dist:

@@ -262,9 +262,9 @@ int tcm_direct_batch(tcm_ctx_t ctx, const tcm_system* A, const tcm_system* B, in
                      const double* rotB, const double* R0, double* E);
 
 /* Largest atom count accepted by tcm_moments_noalloc, and the size in bytes of the fixed
- * device array it works in (about 0.67 MiB). */
+ * device array it works in (about 0.69 MiB). */
 #define TCM_NOALLOC_MAX_ATOMS 262144
-#define TCM_NOALLOC_SCRATCH_BYTES 702976
+#define TCM_NOALLOC_SCRATCH_BYTES 720128
 
 /* The paper has no counterpart to this call; it exists for callers that cannot allocate
  * device memory.  Examples: code that must not let cudaMalloc/cudaFree synchronise the

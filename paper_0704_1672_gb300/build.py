@@ -2,8 +2,9 @@
 
 Every translation unit is compiled by its own nvcc process, in parallel; the
 objects go to paper_0704_1672_gb300/_build/ and the shared library to
-paper_0704_1672_gb300/libtcm.so.  A rebuild happens only when a source or header
-is newer than the library (or ``force=True``).
+paper_0704_1672_gb300/libtcm.so.  Only the units whose object is missing or older
+than the unit or any header are compiled (all of them with ``force=True``); the
+library is relinked when any source or header is newer than it.
 """
 import glob
 import os
@@ -52,20 +53,36 @@ def _compile(src, verbose):
     return obj, r.stderr
 
 
+def _headers():
+    return glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "tcm.h")]
+
+
+def _stale(src, force):
+    """A translation unit needs compiling when its object is missing or older than it or any header."""
+    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+    if force or not os.path.exists(obj):
+        return True
+    t = os.path.getmtime(obj)
+    return any(os.path.getmtime(p) > t for p in [src] + _headers())
+
+
 def build(force=False, verbose=False, jobs=None):
-    """Compile every CUDA translation unit for sm_103a and link libtcm.so; returns its path."""
+    """Compile the CUDA translation units for sm_103a that are out of date (all of them with
+    ``force``), in parallel, and link libtcm.so; returns its path."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
-    jobs = jobs or min(len(srcs), max(2, os.cpu_count() or 2))
+    todo = [s for s in srcs if _stale(s, force)]
+    jobs = jobs or min(max(len(todo), 1), max(2, os.cpu_count() or 2))
     with ThreadPoolExecutor(max_workers=jobs) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose), srcs))
+        results = list(ex.map(lambda s: _compile(s, verbose), todo))
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
+    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -50,8 +50,8 @@ __device__ __forceinline__ void load_xyz(const void* p, int dtype, long long i, 
   }
 }
 
-// Degrees l <= kLowLmax of one job from its system's low-degree sums (system pass 2): the tile rows
-// are added in tile order (double), the Cartesian sums are rotated by the job's rotation R
+// Degrees l <= kLowLmax of one job from its system's low-degree sums (system pass 2, reduced over
+// the system's tiles by its last tile): the Cartesian sums are rotated by the job's rotation R
 // (P' = R P, T' = R T R^T, p = R d) and turned into the packed Q_lm, l <= 2, with
 //   Q_00 = S,  Q_10 = P'_z,  Q_11 = -(P'_x + i P'_y)/sqrt(2),
 //   Q_20 = T'_zz - (T'_xx + T'_yy)/2,  Q_21 = -sqrt(3/2) (T'_xz + i T'_yz),
@@ -59,12 +59,7 @@ __device__ __forceinline__ void load_xyz(const void* p, int dtype, long long i, 
 // the regular solid harmonics r^l sqrt(4 pi/(2l+1)) Y_lm of Eq. (multipole) written out in x, y, z.
 constexpr int kLowComps = (kLowLmax + 1) * (kLowLmax + 1);
 __device__ void low_degrees(const MomJob& job, const double* __restrict__ syspart, double* s_low) {
-  if (threadIdx.x < kLowSums) {
-    const double* p = syspart + (long long)job.low_base * kSysPart + kSysPartLow + threadIdx.x;
-    double t = 0.0;
-    for (int r = 0; r < job.low_tiles; ++r) t += __ldcg(p + (long long)r * kSysPart);
-    s_low[threadIdx.x] = t;
-  }
+  if (threadIdx.x < kLowSums) s_low[threadIdx.x] = __ldcg(syspart + (long long)job.low_base * kSysPart + kSysPartLow + threadIdx.x);
   __syncthreads();
   if (threadIdx.x != 0) return;
   const double* R = job.rot;
@@ -162,7 +157,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const MomJob* __r
 //   S_m = (-1)^l [sum_{k = l+m (mod 2)} D^l_{mk} Re p~_k - i sum_{other k} D^l_{mk} Im p~_k],  Q'_lm = i^m S_m,
 // with v~_m' = v_m' and p~_k = e^{i k beta} p_k, both doubled for indices >= 1: (l+1)^2 real
 // multiply-adds per product and degree, no table of d^l(beta) per energy.
-constexpr int kContractThreads = 256;
+constexpr int kContractThreads = 512;  // most threads of a contraction CTA
 
 // Layout of ztab (doubles): k! and 2 k! for k < 2 kZN, 1/sqrt((l+m)!(l-m)!) at [l][m], and the rows of
 // D^l = d^l(pi/2): D^l_{km}, 0 <= k, m <= l, at kZ_DPI2 + dpi2_off(l) + k dpi2_stride(l) + m.  The
@@ -332,7 +327,7 @@ __device__ void block_sum_n(double (&v)[N], double* sh) {
 // large batches); the gradient kernel, with nine sums per thread, may take more (at the default
 // it was held to 64 and spilled).
 template <bool kGrad>
-__global__ void __launch_bounds__(kContractThreads, kGrad ? 1 : 4) k_contract(const PairDesc* __restrict__ items,
+__global__ void __launch_bounds__(kContractThreads, kGrad ? 1 : 2) k_contract(const PairDesc* __restrict__ items,
                                                                const MomJob* __restrict__ jobs,
                                                                const SysGeom* __restrict__ geoms,
                                                                const double* __restrict__ ztab,
@@ -675,9 +670,14 @@ __global__ void k_direct_final(const double* __restrict__ part, int nblk, double
 
 // Threads per contraction CTA: the largest per-degree loops have (L+1)^2 iterations, so small
 // degrees take smaller CTAs (more of them resident per SM); at least 64, at most 256.
-int contract_threads(int L) {
+// Threads of a contraction CTA: about one per (l1, l2) pair, up to 256; a batch of fewer than a
+// thousand energies at high degree (a few CTAs per SM) takes 512, so that the rotation products
+// and the pair loop run in one round and more warps hide the phases' latency.
+int contract_threads(int L, long long n_items) {
   const int n = (L + 1) * (L + 1);
-  return n <= 64 ? 64 : (n <= 128 ? 128 : kContractThreads);
+  if (n <= 64) return 64;
+  if (n <= 128) return 128;
+  return (n > 256 && n_items < 1024) ? kContractThreads : 256;
 }
 
 int contract_smem_bytes(int L) {
@@ -697,7 +697,7 @@ int launch_rotate_moments(const RotDesc* sets, int n_sets, int Lmax_sets, const 
     if (cudaFuncSetAttribute(k_rotate_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return -1;
   }
-  k_rotate_moments<<<n_sets, contract_threads(Lmax_sets), smem, s>>>(sets, ztab);
+  k_rotate_moments<<<n_sets, contract_threads(Lmax_sets, n_sets), smem, s>>>(sets, ztab);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -714,7 +714,7 @@ int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const Mo
                     const double* ztab, const double* rots, double* E, int32_t* status, double* G, cudaStream_t s) {
   if (n_items <= 0) return 0;
   const int smem = contract_smem_bytes(Lmax_items);
-  const int nt = contract_threads(Lmax_items);
+  const int nt = contract_threads(Lmax_items, n_items);
   if (G) {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)

@@ -10,11 +10,12 @@
 //
 // Each system is cut into warp tiles whose size depends on its own atom count only (so a
 // system's results do not depend on the batch it is in); one warp per tile, all systems' tiles
-// in one launch, so small and large systems alike spread over the GPU.  Per-atom arithmetic is
+// in one launch, so small and large systems alike spread over the GPU.  A lane issues the loads
+// of several atoms before their arithmetic.  Per-atom arithmetic is
 // float for float records: error-free two-sums for the centroid, float-float (two-sum and
-// fma-based two-product) for the low-degree sums, and a float filter for the radius that sends
-// only the atoms within a relative 4e-6 of a lane's running maximum to an exact double
-// recomputation.  Tile partials are doubles; the last tile of a system to finish (a ticket)
+// fma-based two-product) for the low-degree sums, and a float filter for the radius: a second
+// scan of the tile (from cache) recomputes in double only the atoms within a relative 4e-6 of
+// the tile's float maximum.  Tile partials are doubles; the last tile of a system to finish (a ticket)
 // reduces them in tile order, so every result is deterministic.
 #include <cuda_runtime.h>
 
@@ -52,6 +53,13 @@ __device__ __forceinline__ FF ff_sub_split(float x, float hi, float lo) {
   const float bb = s - x;
   const float e = (x - (s - bb)) + (-hi - bb);
   return FF{s, e - lo};
+}
+
+// |x - c|^2 in float from the exact difference d (each coordinate rounded once): within about
+// 3 x 2^-24 of the exact value.  Both scans of the radius use this same expression.
+__device__ __forceinline__ float r2_float(const FF* d) {
+  const float x = d[0].h + d[0].l, y = d[1].h + d[1].l, z = d[2].h + d[2].l;
+  return __fmaf_rn(x, x, __fmaf_rn(y, y, z * z));
 }
 
 __device__ __forceinline__ void ff_warp_sum(float& s, float& e) {
@@ -100,6 +108,24 @@ __device__ __forceinline__ bool last_tile(int* ticket, int n_tiles, int lane) {
   return last;
 }
 
+// Atoms per lane whose loads are issued together before any of their arithmetic (the per-atom
+// work is short, so a lane must keep several loads in flight to cover the memory latency).
+constexpr int kSysBatch = 4;
+
+__device__ __forceinline__ void low_accumulate(float* s, float* e, FF q, const FF* d) {
+  ff_acc(s[0], e[0], q);
+  const FF qd0 = ff_mul(q, d[0]), qd1 = ff_mul(q, d[1]), qd2 = ff_mul(q, d[2]);
+  ff_acc(s[1], e[1], qd0);
+  ff_acc(s[2], e[2], qd1);
+  ff_acc(s[3], e[3], qd2);
+  ff_acc(s[4], e[4], ff_mul(qd0, d[0]));
+  ff_acc(s[5], e[5], ff_mul(qd0, d[1]));
+  ff_acc(s[6], e[6], ff_mul(qd0, d[2]));
+  ff_acc(s[7], e[7], ff_mul(qd1, d[1]));
+  ff_acc(s[8], e[8], ff_mul(qd1, d[2]));
+  ff_acc(s[9], e[9], ff_mul(qd2, d[2]));
+}
+
 __global__ void __launch_bounds__(kSysThreads) k_sys_centroid(const SysJob* __restrict__ jobs,
                                                               const SysTile* __restrict__ tiles, int n_tiles,
                                                               double* __restrict__ part, int* __restrict__ tickets,
@@ -113,12 +139,19 @@ __global__ void __launch_bounds__(kSysThreads) k_sys_centroid(const SysJob* __re
   const long long i1 = min(j.n, i0 + (long long)j.atoms_per_tile);
   double sum[3];
   if (j.dtype == TCM_F32) {
+    const float4* X = reinterpret_cast<const float4*>(j.xyzq);
     float s[3] = {0.f, 0.f, 0.f}, e[3] = {0.f, 0.f, 0.f};
-    for (long long i = i0 + lane; i < i1; i += 32) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(j.xyzq) + i);
-      ff_acc(s[0], e[0], FF{v.x, 0.f});
-      ff_acc(s[1], e[1], FF{v.y, 0.f});
-      ff_acc(s[2], e[2], FF{v.z, 0.f});
+    for (long long i = i0 + lane; i < i1; i += 32 * kSysBatch) {
+      float4 v[kSysBatch];
+#pragma unroll
+      for (int u = 0; u < kSysBatch; ++u)  // padding atoms add exact zeros
+        v[u] = i + 32 * u < i1 ? __ldg(X + i + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < kSysBatch; ++u) {
+        ff_acc(s[0], e[0], FF{v[u].x, 0.f});
+        ff_acc(s[1], e[1], FF{v[u].y, 0.f});
+        ff_acc(s[2], e[2], FF{v[u].z, 0.f});
+      }
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -126,13 +159,22 @@ __global__ void __launch_bounds__(kSysThreads) k_sys_centroid(const SysJob* __re
       sum[k] = (double)s[k] + (double)e[k];
     }
   } else {
+    const double2* X = reinterpret_cast<const double2*>(j.xyzq);
     double s[3] = {0.0, 0.0, 0.0};
-    for (long long i = i0 + lane; i < i1; i += 32) {
-      const double2 a = __ldg(reinterpret_cast<const double2*>(j.xyzq) + 2 * i);
-      const double2 b = __ldg(reinterpret_cast<const double2*>(j.xyzq) + 2 * i + 1);
-      s[0] += a.x;
-      s[1] += a.y;
-      s[2] += b.x;
+    for (long long i = i0 + lane; i < i1; i += 32 * kSysBatch) {
+      double2 a[kSysBatch], b[kSysBatch];
+#pragma unroll
+      for (int u = 0; u < kSysBatch; ++u) {
+        const bool ok = i + 32 * u < i1;
+        a[u] = ok ? __ldg(X + 2 * (i + 32 * u)) : make_double2(0.0, 0.0);
+        b[u] = ok ? __ldg(X + 2 * (i + 32 * u) + 1) : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < kSysBatch; ++u) {
+        s[0] += a[u].x;
+        s[1] += a[u].y;
+        s[2] += b[u].x;
+      }
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) sum[k] = warp_sum_d(s[k]);
@@ -165,72 +207,71 @@ __global__ void __launch_bounds__(kSysThreads) k_sys_radius_low(const SysJob* __
   const SysGeom g = geoms[j.geom];
   const long long i0 = (long long)tl.t * j.atoms_per_tile;
   const long long i1 = min(j.n, i0 + (long long)j.atoms_per_tile);
-  double rmax = 0.0;  // exact max |x - c|^2 of this lane's atoms
+  double rmax = 0.0;  // exact max |x - c|^2 of the tile's atoms
   float s[kLowSums], e[kLowSums];
 #pragma unroll
   for (int k = 0; k < kLowSums; ++k) s[k] = e[k] = 0.f;
   if (j.dtype == TCM_F32) {
+    const float4* X = reinterpret_cast<const float4*>(j.xyzq);
     float chi[3], clo[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       chi[k] = (float)g.c[k];
       clo[k] = (float)(g.c[k] - (double)chi[k]);
     }
-    float thr = 0.f;  // lane's running float maximum, lowered by a relative 4e-6
-    for (long long i = i0 + lane; i < i1; i += 32) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(j.xyzq) + i);
-      FF d[3];
-      d[0] = ff_sub_split(v.x, chi[0], clo[0]);
-      d[1] = ff_sub_split(v.y, chi[1], clo[1]);
-      d[2] = ff_sub_split(v.z, chi[2], clo[2]);
-      // |x - c|^2 in float (within about 4e-7 of the exact value): only atoms near the lane's
-      // running maximum are recomputed exactly
-      const float r2f = __fmaf_rn(d[0].h, d[0].h, __fmaf_rn(d[1].h, d[1].h, d[2].h * d[2].h));
-      if (r2f >= thr) {
-        const double dx = (double)v.x - g.c[0], dy = (double)v.y - g.c[1], dz = (double)v.z - g.c[2];
-        rmax = fmax(rmax, dx * dx + dy * dy + dz * dz);
-        thr = fmaxf(thr, r2f * (1.0f - 4e-6f));
+    float mf = 0.f;  // lane's largest |x - c|^2 in float (within about 4e-7 of the exact value)
+    for (long long i = i0 + lane; i < i1; i += 32 * kSysBatch) {
+      float4 v[kSysBatch];
+#pragma unroll
+      for (int u = 0; u < kSysBatch; ++u)
+        v[u] = i + 32 * u < i1 ? __ldg(X + i + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < kSysBatch; ++u) {
+        const FF d[3] = {ff_sub_split(v[u].x, chi[0], clo[0]), ff_sub_split(v[u].y, chi[1], clo[1]),
+                         ff_sub_split(v[u].z, chi[2], clo[2])};
+        if (i + 32 * u < i1) mf = fmaxf(mf, r2_float(d));
+        if (j.need_low) low_accumulate(s, e, FF{v[u].w, 0.f}, d);  // padding atoms carry q = 0
       }
-      if (j.need_low) {
-        const FF q{v.w, 0.f};
-        ff_acc(s[0], e[0], q);
-        const FF qd0 = ff_mul(q, d[0]), qd1 = ff_mul(q, d[1]), qd2 = ff_mul(q, d[2]);
-        ff_acc(s[1], e[1], qd0);
-        ff_acc(s[2], e[2], qd1);
-        ff_acc(s[3], e[3], qd2);
-        ff_acc(s[4], e[4], ff_mul(qd0, d[0]));
-        ff_acc(s[5], e[5], ff_mul(qd0, d[1]));
-        ff_acc(s[6], e[6], ff_mul(qd0, d[2]));
-        ff_acc(s[7], e[7], ff_mul(qd1, d[1]));
-        ff_acc(s[8], e[8], ff_mul(qd1, d[2]));
-        ff_acc(s[9], e[9], ff_mul(qd2, d[2]));
+    }
+    // the exact radius: only atoms within a relative 4e-6 of the tile's float maximum can hold
+    // the exact maximum; a second scan of the tile (from cache) recomputes just those in double
+    if (j.need_radius) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mf = fmaxf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+      const float thr = mf * (1.0f - 4e-6f);
+      for (long long i = i0 + lane; i < i1; i += 32) {
+        const float4 v = __ldg(X + i);
+        const FF d[3] = {ff_sub_split(v.x, chi[0], clo[0]), ff_sub_split(v.y, chi[1], clo[1]),
+                         ff_sub_split(v.z, chi[2], clo[2])};
+        if (r2_float(d) >= thr) {
+          const double ex = (double)v.x - g.c[0], ey = (double)v.y - g.c[1], ez = (double)v.z - g.c[2];
+          rmax = fmax(rmax, ex * ex + ey * ey + ez * ez);
+        }
       }
     }
   } else {
-    for (long long i = i0 + lane; i < i1; i += 32) {
-      const double2 a = __ldg(reinterpret_cast<const double2*>(j.xyzq) + 2 * i);
-      const double2 b = __ldg(reinterpret_cast<const double2*>(j.xyzq) + 2 * i + 1);
-      const double dd[4] = {a.x - g.c[0], a.y - g.c[1], b.x - g.c[2], b.y};
-      rmax = fmax(rmax, dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-      if (j.need_low) {
-        FF t[4];
+    const double2* X = reinterpret_cast<const double2*>(j.xyzq);
+    for (long long i = i0 + lane; i < i1; i += 32 * kSysBatch) {
+      double2 a[kSysBatch], b[kSysBatch];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float h = (float)dd[k];
-          t[k] = FF{h, (float)(dd[k] - (double)h)};
+      for (int u = 0; u < kSysBatch; ++u) {
+        const bool ok = i + 32 * u < i1;
+        a[u] = ok ? __ldg(X + 2 * (i + 32 * u)) : make_double2(g.c[0], g.c[1]);
+        b[u] = ok ? __ldg(X + 2 * (i + 32 * u) + 1) : make_double2(g.c[2], 0.0);  // padding: d = 0, q = 0
+      }
+#pragma unroll
+      for (int u = 0; u < kSysBatch; ++u) {
+        const double dd[4] = {a[u].x - g.c[0], a[u].y - g.c[1], b[u].x - g.c[2], b[u].y};
+        rmax = fmax(rmax, dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        if (j.need_low) {
+          FF t[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float h = (float)dd[k];
+            t[k] = FF{h, (float)(dd[k] - (double)h)};
+          }
+          low_accumulate(s, e, t[3], t);
         }
-        const FF q = t[3];
-        ff_acc(s[0], e[0], q);
-        const FF qd0 = ff_mul(q, t[0]), qd1 = ff_mul(q, t[1]), qd2 = ff_mul(q, t[2]);
-        ff_acc(s[1], e[1], qd0);
-        ff_acc(s[2], e[2], qd1);
-        ff_acc(s[3], e[3], qd2);
-        ff_acc(s[4], e[4], ff_mul(qd0, t[0]));
-        ff_acc(s[5], e[5], ff_mul(qd0, t[1]));
-        ff_acc(s[6], e[6], ff_mul(qd0, t[2]));
-        ff_acc(s[7], e[7], ff_mul(qd1, t[1]));
-        ff_acc(s[8], e[8], ff_mul(qd1, t[2]));
-        ff_acc(s[9], e[9], ff_mul(qd2, t[2]));
       }
     }
   }
@@ -251,20 +292,32 @@ __global__ void __launch_bounds__(kSysThreads) k_sys_radius_low(const SysJob* __
     }
   }
   if (lane == 0) row[kSysPartR2] = rmax;
-  if (!j.need_radius || !last_tile(&tickets[2 * tl.job + 1], j.n_tiles, lane)) return;
-  double m = 0.0;
-  const double* p0 = part + (long long)j.tile_base * kSysPart + kSysPartR2;
-  for (int r = lane; r < j.n_tiles; r += 32) m = fmax(m, __ldcg(p0 + (long long)r * kSysPart));
-  m = warp_max_d(m);
-  if (lane == 0) geoms[j.geom].a = sqrt(m);
+  if (!last_tile(&tickets[2 * tl.job + 1], j.n_tiles, lane)) return;
+  // the last tile of the system: its radius and its low-degree sums over all tiles (tile order),
+  // written once to the system's sum row, which every moment job of the system reads
+  const double* p0 = part + (long long)j.tile_base * kSysPart;
+  if (j.need_radius) {
+    double m = 0.0;
+    for (int r = lane; r < j.n_tiles; r += 32) m = fmax(m, __ldcg(p0 + (long long)r * kSysPart + kSysPartR2));
+    m = warp_max_d(m);
+    if (lane == 0) geoms[j.geom].a = sqrt(m);
+  }
+  if (j.need_low) {
+    double* sr = part + (long long)j.sum_row * kSysPart;
+    for (int k = 0; k < kLowSums; ++k) {
+      const double t = ordered_sum(p0 + kSysPartLow + k, j.n_tiles, kSysPart, lane);
+      if (lane == 0) sr[kSysPartLow + k] = t;
+    }
+  }
 }
 
 }  // namespace
 
 int sys_tile_atoms(long long n) {
-  // about 64 tiles for a system, between 256 and 2,048 atoms (8 to 64 per lane)
+  // 256-atom tiles (8 per lane) up to 32,768 atoms, 512 up to 65,536, 1,024 above: enough warps
+  // for the GPU even for a single system, few enough partial rows for the largest
   long long t = 256;
-  while (t < 2048 && t * 64 < n) t *= 2;
+  while (t < 1024 && t * 128 < n) t *= 2;
   return (int)t;
 }
 

@@ -400,6 +400,7 @@ void plan_sys(const tcm_system* systems, int n_systems, const std::vector<char>&
     j.n_tiles = (int)std::max<long long>(1, (sy.n + j.atoms_per_tile - 1) / j.atoms_per_tile);
     j.tile_base = S.rows;
     S.rows += j.n_tiles;
+    j.sum_row = -1;
     const int ji = (int)S.jobs.size();
     for (int t = 0; t < j.n_tiles; ++t) {
       if (nc) S.t1.push_back(SysTile{ji, t});
@@ -408,6 +409,8 @@ void plan_sys(const tcm_system* systems, int n_systems, const std::vector<char>&
     S.of_system[s] = ji;
     S.jobs.push_back(j);
   }
+  for (SysJob& j : S.jobs)  // one sum row per system after the tile rows
+    if (j.need_low) j.sum_row = S.rows++;
 }
 
 // Mixed path: every computed moment job takes its degrees l <= 2 from its system's low sums.
@@ -415,8 +418,8 @@ void link_low(const SysPlan& S, Plan& P) {
   for (MomJob& j : P.jobs) {
     const int si = S.of_system[j.geom];
     if (si < 0 || !S.jobs[si].need_low) continue;
-    j.low_base = S.jobs[si].tile_base;
-    j.low_tiles = S.jobs[si].n_tiles;
+    j.low_base = S.jobs[si].sum_row;
+    j.low_tiles = 1;
   }
 }
 

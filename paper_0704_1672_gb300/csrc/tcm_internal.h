@@ -146,8 +146,9 @@ struct MomJob {    // one moment set: a system at one Lmax under one rotation
   int tile_base;   // id of the job's first tile; tile id = base + chunk * tpc + t
   double rot[9];   // row-major, identity when unrotated
   double* out;     // packed moments, (L+1)^2 doubles
-  int low_base;    // mixed precision: first tile row of the system's low-degree sums (SysJob), and
-  int low_tiles;   // their count; 0 = the degrees l <= 2 keep the float kernel's values
+  int low_base;    // mixed precision: the row of the system-pass partials holding the system's
+  int low_tiles;   // low-degree sums (SysJob.sum_row) when low_tiles != 0; 0 = the degrees l <= 2
+                   // keep the float kernel's values
 };
 
 struct MomTile {   // one tile of moment work
@@ -176,6 +177,7 @@ struct SysJob {
   int tile_base;     // row of its first tile in the partials (kSysPart doubles per row)
   int n_tiles;
   int atoms_per_tile;
+  int sum_row;       // row of its low-degree sums over all tiles (written by its last tile)
 };
 
 struct SysTile {
@@ -255,9 +257,8 @@ int sys_tile_atoms(long long n);
 // Step a3: one CTA per job.  imap + imap_off[L] lists, per (chunk, slot) of degree L, the packed
 // component it holds (-1 for none), nch(L) x kmax entries; fmap beside it holds that
 // component's F_lm with the sign of the kernels' H variables.
-// Jobs with low_tiles > 0 take their degrees l <= min(kLowLmax, L) from the low-degree sums of
-// their system (rows [low_base, low_base + low_tiles) of the system-pass partials syspart)
-// rotated by the job's rotation.
+// Jobs with low_tiles != 0 take their degrees l <= min(kLowLmax, L) from the low-degree sums of
+// their system (row low_base of the system-pass partials syspart) rotated by the job's rotation.
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms,
                     const int* imap, const double* fmap, const int* imap_off, int kmax, const double* syspart,
                     cudaStream_t s);

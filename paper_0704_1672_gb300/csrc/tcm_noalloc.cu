@@ -33,8 +33,9 @@ constexpr int kNaTilesPerChunk = (int)(kNaMaxAtoms / kNaTileAtoms);  // 64
 constexpr int kNaMaxChunks = 10;                                     // most chunks of any (precision, Lmax)
 constexpr int kNaPartialDoubles = kNaTilesPerChunk * 800;            // max over plans of chunks * kmax = 800
 constexpr int kNaMaxTiles = kNaTilesPerChunk * kNaMaxChunks;
-// system-pass tiles: sys_tile_atoms gives at most 64 tiles below 131,072 atoms and tiles of 2,048 above
-constexpr int kNaSysTiles = (int)((kNaMaxAtoms + 2047) / 2048) > 64 ? (int)((kNaMaxAtoms + 2047) / 2048) : 64;
+// system-pass rows: sys_tile_atoms gives at most 128 tiles up to 65,536 atoms and 1,024-atom tiles
+// above (256 for the largest request), plus the sum row
+constexpr int kNaSysTiles = (int)((kNaMaxAtoms + 1023) / 1024) + 1;
 constexpr int kNaCompTotal = 5525;  // sum over L = 0..24 of (L+1)^2
 
 // Layout of the scratch array (byte offsets, 256-byte aligned sections).
@@ -166,9 +167,10 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   sj.atoms_per_tile = sys_tile_atoms(s->n);
   sj.n_tiles = (int)std::max<long long>(1, (s->n + sj.atoms_per_tile - 1) / sj.atoms_per_tile);
   sj.tile_base = 0;
-  if (sj.n_tiles > kNaSysTiles) return na_err(TCM_EINVAL, "tcm_moments_noalloc: request exceeds the fixed scratch");
-  job.low_base = 0;
-  job.low_tiles = sj.need_low ? sj.n_tiles : 0;
+  sj.sum_row = sj.n_tiles;  // the row after the tile rows
+  if (sj.n_tiles + 1 > kNaSysTiles) return na_err(TCM_EINVAL, "tcm_moments_noalloc: request exceeds the fixed scratch");
+  job.low_base = sj.sum_row;
+  job.low_tiles = sj.need_low ? 1 : 0;
   const int n1 = sj.need_center ? sj.n_tiles : 0;
   const int n2 = (sj.need_radius || sj.need_low) ? sj.n_tiles : 0;
 

@@ -5,10 +5,11 @@ Two kinds of work partition:
 * independent items (orientations, pairs, requests): ``shard_items`` gives each rank a
   contiguous slice; nothing is exchanged (weak scaling of the benchmark, replicas);
 * the moments of one system too large for one device: every rank takes a contiguous range
-  of atoms (``shard_range``), the global centroid and radius come from one all-reduce of
-  (sum x, sum y, sum z, n) and one max-all-reduce, every rank computes the moments of its
-  atoms about that centre, and one all-reduce of the (Lmax+1)^2 doubles adds them up
-  (Eq. (multipole) is a sum over atoms).
+  of atoms (``shard_range``); the library's step a1 gives each rank's coordinate sums, one
+  all-reduce gives the global centroid, the library's radius about it and one max-all-reduce
+  the global radius; every rank computes the moments of its atoms about that centre with the
+  library, and one all-reduce of the (Lmax+1)^2 doubles adds them up (Eq. (multipole) is a sum
+  over atoms).
 """
 from __future__ import annotations
 
@@ -29,20 +30,30 @@ def shard_items(n_items: int, rank: int, world: int):
     return np.arange(lo, hi)
 
 
-def global_center_radius(xyz_local: torch.Tensor, group=None):
-    """Centroid and radius of a system whose atoms are spread over the ranks (double)."""
-    x = xyz_local.to(torch.float64)
-    s = torch.zeros(4, dtype=torch.float64, device=x.device)
-    if x.numel():
-        s[:3] = x[:, :3].sum(0)
-    s[3] = float(x.shape[0])
-    dist.all_reduce(s, op=dist.ReduceOp.SUM, group=group)
-    c = s[:3] / torch.clamp(s[3], min=1.0)
-    r2 = torch.zeros(1, dtype=torch.float64, device=x.device)
-    if x.numel():
-        r2[0] = ((x[:, :3] - c) ** 2).sum(1).max()
-    dist.all_reduce(r2, op=dist.ReduceOp.MAX, group=group)
-    return c.cpu().numpy(), float(torch.sqrt(r2)[0])
+def shard_center_sums(ctx, xyzq_local: torch.Tensor):
+    """(sum x, sum y, sum z, n) of this rank's atoms, from the library's centroid (step a1 on the
+    device): n times the shard's centroid."""
+    n = int(xyzq_local.shape[0])
+    if n == 0:
+        return np.zeros(4)
+    c, _ = ctx.tcm_prepare(xyzq_local)
+    return np.array([c[0] * n, c[1] * n, c[2] * n, float(n)])
+
+
+def shard_radius(ctx, xyzq_local: torch.Tensor, center) -> float:
+    """Largest distance of this rank's atoms from the given (global) centre (step a1 on the device)."""
+    if int(xyzq_local.shape[0]) == 0:
+        return 0.0
+    _, a = ctx.tcm_prepare(xyzq_local, center=center)
+    return float(a)
+
+
+def shard_moments(ctx, xyzq_local: torch.Tensor, lmax: int, center, radius, precision=None) -> torch.Tensor:
+    """Moments of this rank's atoms about the global centre, scaled by the global radius
+    (tcm_moments): their sum over the ranks is the system's moments."""
+    from . import tcm
+    precision = tcm.TCM_MIXED if precision is None else precision
+    return ctx.tcm_moments(xyzq_local, lmax, precision=precision, center=center, radius=radius).q
 
 
 def allreduce_moments(q: torch.Tensor, group=None) -> torch.Tensor:
@@ -51,21 +62,46 @@ def allreduce_moments(q: torch.Tensor, group=None) -> torch.Tensor:
     return q
 
 
-def sharded_moments(xyzq_local: torch.Tensor, lmax: int, moment_fn=None, group=None):
+def global_center_radius(ctx, xyzq_local: torch.Tensor, group=None, geom=None):
+    """Centroid and radius of a system whose atoms are spread over the ranks: each rank's
+    coordinate sums and, about the resulting centre, its largest distance, from the library
+    (``geom`` = (center_sums_fn, radius_fn) replaces it, e.g. on CPU ranks), combined by one
+    sum-all-reduce and one max-all-reduce."""
+    csum, rad = geom if geom is not None else (lambda x: shard_center_sums(ctx, x),
+                                              lambda x, c: shard_radius(ctx, x, c))
+    s = torch.tensor(csum(xyzq_local), dtype=torch.float64)
+    dev_t = torch.device("cuda") if dist.get_backend(group) == "nccl" else torch.device("cpu")
+    s = s.to(dev_t)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM, group=group)
+    s = s.cpu().numpy()
+    c = s[:3] / max(s[3], 1.0)
+    r = torch.tensor([rad(xyzq_local, c)], dtype=torch.float64, device=dev_t)
+    dist.all_reduce(r, op=dist.ReduceOp.MAX, group=group)
+    return c, float(r.cpu()[0])
+
+
+def sharded_moments(xyzq_local: torch.Tensor, lmax: int, moment_fn=None, geom=None, group=None, precision=None):
     """Moments of a system split over the ranks (this rank holds ``xyzq_local``).
 
-    ``moment_fn(xyzq, lmax, center, radius) -> packed double tensor`` computes the moments of a
-    set of atoms about a given centre; by default the library's tcm_moments on the current
-    device (mixed precision).  Returns (packed moments, centre, radius), identical on all ranks.
+    The global centre and radius come from the library's step a1 on every rank's atoms plus two
+    all-reduces; ``moment_fn(xyzq, lmax, center, radius) -> packed double tensor`` computes the
+    moments of a set of atoms about a given centre, by default the library's tcm_moments on the
+    current device.  ``geom`` and ``moment_fn`` stand in for the library on CPU ranks.  Returns
+    (packed moments, centre, radius), identical on all ranks.
     """
-    c, a = global_center_radius(xyzq_local, group)
-    if moment_fn is None:
+    ctx = None
+    if geom is None or moment_fn is None:
         from . import tcm
         ctx = tcm.Context(lmax_cap=lmax)
-        q = ctx.tcm_moments(xyzq_local, lmax, precision=tcm.TCM_MIXED, center=c, radius=a).q
-        ctx.close()
-    else:
-        q = moment_fn(xyzq_local, lmax, c, a)
+    try:
+        c, a = global_center_radius(ctx, xyzq_local, group, geom)
+        if moment_fn is None:
+            q = shard_moments(ctx, xyzq_local, lmax, c, a, precision)
+        else:
+            q = moment_fn(xyzq_local, lmax, c, a)
+    finally:
+        if ctx is not None:
+            ctx.close()
     q = q.to(torch.float64).contiguous()
     allreduce_moments(q, group)
     return q, c, a

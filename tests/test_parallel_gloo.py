@@ -1,7 +1,8 @@
 """The multi-rank partition logic on CPU ranks (gloo, world size 2): sharded moments of one system
 (atoms split over the ranks, global centre and radius, one all-reduce) equal the single-process
-moments, and item shards cover every item once.  The per-rank moment function is the CPU
-oracle here; only the partition and reduction logic of the package is under test."""
+moments, and item shards cover every item once.  The per-rank geometry and moment functions are
+the CPU oracle here; only the partition and reduction logic of the package is under test (the
+library's per-rank route runs in tests/test_gpu_sharded.py)."""
 import os
 import socket
 
@@ -37,6 +38,20 @@ def _oracle_fn(xyzq, L, c, a):
     return torch.tensor(_packed(Q, L))
 
 
+def _oracle_center_sums(xyzq):
+    import oracle
+    n = len(xyzq)
+    if n == 0:
+        return np.zeros(4)
+    c, _ = oracle.center_radius(xyzq.numpy())
+    return np.array([c[0] * n, c[1] * n, c[2] * n, float(n)])
+
+
+def _radius_about(xyzq, c):
+    x = xyzq.numpy()
+    return float(np.sqrt(((x[:, :3] - c) ** 2).sum(1).max())) if len(x) else 0.0
+
+
 def _worker(rank, world, port, S, L, out):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -44,7 +59,7 @@ def _worker(rank, world, port, S, L, out):
     try:
         lo, hi = parallel.shard_range(len(S), rank, world)
         local = torch.tensor(S[lo:hi])
-        q, c, a = parallel.sharded_moments(local, L, moment_fn=_oracle_fn)
+        q, c, a = parallel.sharded_moments(local, L, moment_fn=_oracle_fn, geom=(_oracle_center_sums, _radius_about))
         out[rank] = (q.numpy(), c, a)
     finally:
         torch.distributed.destroy_process_group()
