@@ -602,7 +602,7 @@ def bench_config2(torch, tcm, synth, autotune, timer, stream, prec, peak_fp32, p
     return out
 
 
-def bench_config3(torch, tcm, synth, stream, prec, calls=3):
+def bench_config3(torch, tcm, synth, stream, prec, calls=3, tune=True):
     """4,096 uneven pairs in one call.  Each timed call is a single call of its shape (graph capture
     on the first call is on): the host planning, the descriptor upload, the capture and the
     kernels are all inside the timed region."""
@@ -616,7 +616,7 @@ def bench_config3(torch, tcm, synth, stream, prec, calls=3):
                     for i in range(len(b.L))))
     ctx = tcm.Context(lmax_cap=24, stream=stream)
     tuned = autotune.tune(ctx, T, b.pair_a, b.pair_b, b.L, b.R0, rotB=b.rotB, precision=prec, reps=2,
-                          max_items_per_l=256, atoms_per_lane=(32, 64, 128))
+                          max_items_per_l=256, atoms_per_lane=(32, 64, 128)) if tune else None
     E = torch.empty(len(b.L), dtype=torch.float64, device="cuda")
     st = torch.empty(len(b.L), dtype=torch.int32, device="cuda")
     rng = np.random.default_rng(99)
@@ -633,9 +633,10 @@ def bench_config3(torch, tcm, synth, stream, prec, calls=3):
         e0.record(stream)
         pb.items["rotB"] = rot.reshape(len(b.L), 9)
         ctx.tcm_energy_batch_packed(pb, prec, E, st)
+        th = time.perf_counter()  # the call has planned, uploaded and queued its work
         e1.record(stream)
         torch.cuda.synchronize()
-        res.append((e0.elapsed_time(e1), (time.perf_counter() - tw) * 1e3))
+        res.append((e0.elapsed_time(e1), (time.perf_counter() - tw) * 1e3, (th - tw) * 1e3))
     ctx.tcm_ctx_set_profiling(True)
     ctx.tcm_ctx_read_profile()
     ctx.tcm_energy_batch_packed(pb, prec, E, st)
@@ -645,14 +646,15 @@ def bench_config3(torch, tcm, synth, stream, prec, calls=3):
     ctx.close()
     dev_ms = [r[0] for r in res]
     wall_ms = [r[1] for r in res]
+    host_ms = [r[2] for r in res]
     return {"workload": b.name, "pairs": len(b.L), "systems": len(b.systems), "atoms": atoms,
             "atom_moment_components": comps, "calls": calls,
-            "call_ms_device": dev_ms, "call_ms_wall": wall_ms,
+            "call_ms_device": dev_ms, "call_ms_wall": wall_ms, "call_ms_host_queueing": host_ms,
             "value": atoms / (np.median(dev_ms) * 1e-3), "unit": UNIT,
             "energies_per_s": len(b.L) / (np.median(dev_ms) * 1e-3),
             "moment_components_per_s": comps / (np.median(dev_ms) * 1e-3),
             "phase_ms_one_call": ph, "launches_one_call": la, "graph_captures": caps, "graph_launches": glaunch,
-            "tiling": {str(L): list(v) for L, v in tuned.best.items()}, "generator_s": t_gen,
+            "tiling": {str(L): list(v) for L, v in tuned.best.items()} if tuned else "default", "generator_s": t_gen,
             "how": "each call is timed alone (CUDA events around one tcm_energy_batch call, with its host planning, "
                    "descriptor upload and, on a shape's first call, the graph capture); calls 2 and 3 use new "
                    "orientations"}
@@ -788,7 +790,7 @@ def run_only(args):
                             n_sm * FP32_LANES_PER_SM * smx * 1e6 / 1e12, n_sm * FP64_PER_SM_CLK * smx * 1e6 / 1e9,
                             n_sm, smx, steps=args.steps)
     else:
-        rec = bench_config3(torch, tcm, synth, stream, prec)
+        rec = bench_config3(torch, tcm, synth, stream, prec, tune=not args.no_autotune)
     print(json.dumps({args.only: rec}), flush=True)
 
 

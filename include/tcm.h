@@ -136,7 +136,9 @@ typedef enum {
   TCM_PHASE_FINALIZE = 2, /* a3: cross-tile reduction in double and normalisation */
   TCM_PHASE_CONTRACT = 3, /* a4 + a5: irregular harmonics at R0 and the two-center contraction */
   TCM_PHASE_DIRECT = 4,   /* a6: exact pairwise sum */
-  TCM_NPHASES = 5
+  TCM_PHASE_HOST = 5,     /* host wall time inside tcm_energy_batch / tcm_gradients_batch (planning,
+                             descriptor staging and upload, launching or graph replay); no kernels */
+  TCM_NPHASES = 6
 } tcm_phase;
 
 /* Tiling of the moment pass for one precision, every degree: each warp of the moment kernels

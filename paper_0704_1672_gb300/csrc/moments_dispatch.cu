@@ -33,7 +33,31 @@ constexpr int size_of(int precision) { return precision == TCM_FP64 ? 8 : 4; }
 
 int moments_kmax(int precision) { return precision == TCM_FP64 ? kKmaxF64 : kKmaxF32; }
 
-int moments_nchunks(int precision, int L) { return plan_nch(L, moments_kmax(precision)); }
+namespace {
+// The chunk plans of both precisions, tabulated once (plan_nch and plan_m0 are loops meant for
+// compile time; the host planning of a batch asks for them per job and per group).
+struct ChunkTables {
+  int nch[2][kLmaxMax + 1];
+  int m0[2][kLmaxMax + 1][kLmaxMax + 2];
+  ChunkTables() {
+    for (int pi = 0; pi < 2; ++pi) {
+      const int kmax = pi == 0 ? kKmaxF64 : kKmaxF32;
+      for (int L = 0; L <= kLmaxMax; ++L) {
+        nch[pi][L] = plan_nch(L, kmax);
+        for (int c = 0; c <= nch[pi][L]; ++c) m0[pi][L][c] = plan_m0(L, kmax, nch[pi][L], c);
+      }
+    }
+  }
+};
+const ChunkTables& chunk_tables() {
+  static const ChunkTables t;
+  return t;
+}
+}  // namespace
+
+int moments_nchunks(int precision, int L) { return chunk_tables().nch[precision == TCM_FP64 ? 0 : 1][L]; }
+
+int moments_chunk_m0(int precision, int L, int chunk) { return chunk_tables().m0[precision == TCM_FP64 ? 0 : 1][L][chunk]; }
 
 int moments_smem_bytes(int precision, int L) {
   const int kmax = moments_kmax(precision);
@@ -117,19 +141,32 @@ int launch_moments(int precision, int L, const MomJob* jobs, const MomTile* tile
 
 namespace {
 __global__ void __launch_bounds__(256) k_expand_tiles(const MomGroup* __restrict__ groups, int n_groups,
-                                                      const MomJob* __restrict__ jobs, MomTile* __restrict__ tiles) {
+                                                      const MomJob* __restrict__ jobs, MomTile* __restrict__ tiles,
+                                                      const SysJob* __restrict__ sjobs, int n_sjobs,
+                                                      SysTile* __restrict__ t1, SysTile* __restrict__ t2) {
   const int g = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (g >= n_groups) return;
-  const MomGroup gr = groups[g];
-  const MomJob& j = jobs[gr.job];
-  const int row = j.tile_base + gr.chunk * j.tiles_per_chunk;
-  for (int t = threadIdx.x & 31; t < gr.n; t += 32) tiles[gr.first + t] = MomTile{gr.job, gr.chunk, t, row + t};
+  const int lane = threadIdx.x & 31;
+  if (g < n_groups) {
+    const MomGroup gr = groups[g];
+    const MomJob& j = jobs[gr.job];
+    const int row = j.tile_base + gr.chunk * j.tiles_per_chunk;
+    for (int t = lane; t < gr.n; t += 32) tiles[gr.first + t] = MomTile{gr.job, gr.chunk, t, row + t};
+  } else if (g - n_groups < n_sjobs) {
+    const int ji = g - n_groups;
+    const SysJob sj = sjobs[ji];
+    for (int t = lane; t < sj.n_tiles; t += 32) {
+      if (sj.first1 >= 0) t1[sj.first1 + t] = SysTile{ji, t};
+      if (sj.first2 >= 0) t2[sj.first2 + t] = SysTile{ji, t};
+    }
+  }
 }
 }  // namespace
 
-int launch_expand_tiles(const MomGroup* groups, int n_groups, const MomJob* jobs, MomTile* tiles, cudaStream_t s) {
-  if (n_groups <= 0) return 0;
-  k_expand_tiles<<<(n_groups + 7) / 8, 256, 0, s>>>(groups, n_groups, jobs, tiles);
+int launch_expand_tiles(const MomGroup* groups, int n_groups, const MomJob* jobs, MomTile* tiles, const SysJob* sjobs,
+                        int n_sjobs, SysTile* t1, SysTile* t2, cudaStream_t s) {
+  const int n = n_groups + n_sjobs;
+  if (n <= 0) return 0;
+  k_expand_tiles<<<(n + 7) / 8, 256, 0, s>>>(groups, n_groups, jobs, tiles, sjobs, n_sjobs, t1, t2);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

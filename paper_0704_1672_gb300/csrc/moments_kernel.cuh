@@ -283,9 +283,9 @@ __device__ __forceinline__ Xform<T> make_xform(const MomJob& job, const SysGeom&
   Xform<T> x;
   const double ia = 1.0 / scale_radius(g.a);  // exact: a power of two
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    x.chi[k] = (T)g.c[k];
-    x.clo[k] = (T)(g.c[k] - (double)x.chi[k]);
+  for (int k = 0; k < 3; ++k) {  // float: the centre's split from the geometry record
+    x.chi[k] = sizeof(T) == 4 ? (T)g.chi[k] : (T)g.c[k];
+    x.clo[k] = sizeof(T) == 4 ? (T)g.clo[k] : (T)0;
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) x.M[k] = (T)(job.rot[k] * ia);

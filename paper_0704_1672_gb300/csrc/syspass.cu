@@ -77,19 +77,30 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// Warp maximum of non-negative doubles through their bit patterns (they order like the integers),
+// so that the comparisons stay off the FP64 pipe.
 __device__ __forceinline__ double warp_max_d(double v) {
+  long long b = __double_as_longlong(v);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
+  for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+  return __longlong_as_double(b);
 }
 
-// Lane l adds rows l, l + 32, ... of n, then the lanes' sums are added in a fixed tree: the same
-// result for the same rows in every run.  Rows are read through L2 (written by other CTAs).
-__device__ __forceinline__ double ordered_sum(const double* p, int n, int stride, int lane) {
-  double t = 0.0;
-  for (int r = lane; r < n; r += 32) t += __ldcg(p + (long long)r * stride);
-  return warp_sum_d(t);
+// Float-float sum of one (hi, lo) pair over n tile rows (stride in floats): lane l adds rows l,
+// l + 32, ..., then the lanes' pairs are added in a fixed tree, so the same rows give the same
+// result in every run.  Float instructions only.  Rows are read through L2 (written by other CTAs).
+__device__ __forceinline__ double ordered_ff_sum(const float* p, int n, int stride, int lane) {
+  float s = 0.f, e = 0.f;
+  for (int r = lane; r < n; r += 32) ff_acc(s, e, FF{__ldcg(p + (long long)r * stride), __ldcg(p + (long long)r * stride + 1)});
+  ff_warp_sum(s, e);
+  return (double)s + (double)e;
 }
+
+// Tile rows hold their sums as (hi, lo) float pairs: no per-tile double arithmetic, which on GB300
+// runs at 1/64 of the float rate.  Float offsets within a row:
+constexpr int kRowFloats = 2 * kSysPart;
+constexpr int kRowCen = 0;                 // centroid sums, 3 pairs
+constexpr int kRowLow = 2 * kSysPartLow;   // low-degree sums, kLowSums pairs
 
 constexpr int kSysWarps = kSysThreads / 32;
 
@@ -137,7 +148,7 @@ __global__ void __launch_bounds__(kSysThreads) k_sys_centroid(const SysJob* __re
   const SysJob j = jobs[tl.job];
   const long long i0 = (long long)tl.t * j.atoms_per_tile;
   const long long i1 = min(j.n, i0 + (long long)j.atoms_per_tile);
-  double sum[3];
+  FF pair[3];
   if (j.dtype == TCM_F32) {
     const float4* X = reinterpret_cast<const float4*>(j.xyzq);
     float s[3] = {0.f, 0.f, 0.f}, e[3] = {0.f, 0.f, 0.f};
@@ -156,7 +167,7 @@ __global__ void __launch_bounds__(kSysThreads) k_sys_centroid(const SysJob* __re
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       ff_warp_sum(s[k], e[k]);
-      sum[k] = (double)s[k] + (double)e[k];
+      pair[k] = FF{s[k], e[k]};
     }
   } else {
     const double2* X = reinterpret_cast<const double2*>(j.xyzq);
@@ -177,24 +188,30 @@ __global__ void __launch_bounds__(kSysThreads) k_sys_centroid(const SysJob* __re
       }
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) sum[k] = warp_sum_d(s[k]);
+    for (int k = 0; k < 3; ++k) {  // double records: the tile's double sum as a float pair
+      const double t = warp_sum_d(s[k]);
+      const float h = (float)t;
+      pair[k] = FF{h, (float)(t - (double)h)};
+    }
   }
-  double* row = part + (long long)(j.tile_base + tl.t) * kSysPart;
-  if (lane < 3) row[lane] = lane == 0 ? sum[0] : (lane == 1 ? sum[1] : sum[2]);
+  float* row = reinterpret_cast<float*>(part + (long long)(j.tile_base + tl.t) * kSysPart);
+  if (lane < 6) row[kRowCen + lane] = (lane & 1) ? pair[lane >> 1].l : pair[lane >> 1].h;
   if (!last_tile(&tickets[2 * tl.job], j.n_tiles, lane)) return;
-  const double* p0 = part + (long long)j.tile_base * kSysPart;
+  const float* p0 = reinterpret_cast<const float*>(part + (long long)j.tile_base * kSysPart);
   const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
-  const double cx = ordered_sum(p0, j.n_tiles, kSysPart, lane) * inv;
-  const double cy = ordered_sum(p0 + 1, j.n_tiles, kSysPart, lane) * inv;
-  const double cz = ordered_sum(p0 + 2, j.n_tiles, kSysPart, lane) * inv;
-  if (lane == 0) {
-    geoms[j.geom].c[0] = cx;
-    geoms[j.geom].c[1] = cy;
-    geoms[j.geom].c[2] = cz;
+  const double cx = ordered_ff_sum(p0 + kRowCen, j.n_tiles, kRowFloats, lane) * inv;
+  const double cy = ordered_ff_sum(p0 + kRowCen + 2, j.n_tiles, kRowFloats, lane) * inv;
+  const double cz = ordered_ff_sum(p0 + kRowCen + 4, j.n_tiles, kRowFloats, lane) * inv;
+  if (lane < 3) {  // the centre and its split into float parts
+    const double c = lane == 0 ? cx : (lane == 1 ? cy : cz);
+    const float hi = (float)c;
+    geoms[j.geom].c[lane] = c;
+    geoms[j.geom].chi[lane] = hi;
+    geoms[j.geom].clo[lane] = (float)(c - (double)hi);
   }
 }
 
-__global__ void __launch_bounds__(kSysThreads) k_sys_radius_low(const SysJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kSysThreads, 3) k_sys_radius_low(const SysJob* __restrict__ jobs,
                                                                 const SysTile* __restrict__ tiles, int n_tiles,
                                                                 double* __restrict__ part, int* __restrict__ tickets,
                                                                 SysGeom* __restrict__ geoms) {
@@ -213,12 +230,8 @@ __global__ void __launch_bounds__(kSysThreads) k_sys_radius_low(const SysJob* __
   for (int k = 0; k < kLowSums; ++k) s[k] = e[k] = 0.f;
   if (j.dtype == TCM_F32) {
     const float4* X = reinterpret_cast<const float4*>(j.xyzq);
-    float chi[3], clo[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      chi[k] = (float)g.c[k];
-      clo[k] = (float)(g.c[k] - (double)chi[k]);
-    }
+    const float* chi = g.chi;
+    const float* clo = g.clo;
     float mf = 0.f;  // lane's largest |x - c|^2 in float (within about 4e-7 of the exact value)
     for (long long i = i0 + lane; i < i1; i += 32 * kSysBatch) {
       float4 v[kSysBatch];
@@ -239,13 +252,24 @@ __global__ void __launch_bounds__(kSysThreads) k_sys_radius_low(const SysJob* __
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mf = fmaxf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
       const float thr = mf * (1.0f - 4e-6f);
-      for (long long i = i0 + lane; i < i1; i += 32) {
-        const float4 v = __ldg(X + i);
-        const FF d[3] = {ff_sub_split(v.x, chi[0], clo[0]), ff_sub_split(v.y, chi[1], clo[1]),
-                         ff_sub_split(v.z, chi[2], clo[2])};
-        if (r2_float(d) >= thr) {
-          const double ex = (double)v.x - g.c[0], ey = (double)v.y - g.c[1], ez = (double)v.z - g.c[2];
-          rmax = fmax(rmax, ex * ex + ey * ey + ez * ez);
+      for (long long i0w = i0; i0w < i1; i0w += 32) {  // warp-uniform trip count
+        const long long i = i0w + lane;
+        bool cand = false;
+        if (i < i1) {
+          const float4 v = __ldg(X + i);
+          const FF d[3] = {ff_sub_split(v.x, chi[0], clo[0]), ff_sub_split(v.y, chi[1], clo[1]),
+                           ff_sub_split(v.z, chi[2], clo[2])};
+          cand = r2_float(d) >= thr;
+        }
+        // the candidates one at a time, in a loop whose trip count is the warp's candidate count:
+        // a predicated double block would occupy GB300's 1/64-rate FP64 pipe for every atom
+        unsigned m = __ballot_sync(0xffffffffu, cand);
+        while (m) {
+          const int src = __ffs(m) - 1;
+          m &= m - 1;
+          const float4 w = __ldcg(X + i0w + src);
+          const double ex = (double)w.x - g.c[0], ey = (double)w.y - g.c[1], ez = (double)w.z - g.c[2];
+          rmax = fmax(rmax, ex * ex + ey * ey + ez * ez);  // the same value in every lane
         }
       }
     }
@@ -280,15 +304,11 @@ __global__ void __launch_bounds__(kSysThreads) k_sys_radius_low(const SysJob* __
   if (j.need_low) {
 #pragma unroll
     for (int k = 0; k < kLowSums; ++k) ff_warp_sum(s[k], e[k]);
-    if (lane < kLowSums) {
-      float sv = 0.f, ev = 0.f;
+    if (lane < 2 * kLowSums) {  // lane 2k writes the hi part of sum k, lane 2k + 1 its lo part
+      float v = 0.f;
 #pragma unroll
-      for (int k = 0; k < kLowSums; ++k)
-        if (lane == k) {
-          sv = s[k];
-          ev = e[k];
-        }
-      row[kSysPartLow + lane] = (double)sv + (double)ev;
+      for (int k = 0; k < kLowSums; ++k) v = (lane == 2 * k) ? s[k] : ((lane == 2 * k + 1) ? e[k] : v);
+      reinterpret_cast<float*>(row)[kRowLow + lane] = v;
     }
   }
   if (lane == 0) row[kSysPartR2] = rmax;
@@ -304,8 +324,9 @@ __global__ void __launch_bounds__(kSysThreads) k_sys_radius_low(const SysJob* __
   }
   if (j.need_low) {
     double* sr = part + (long long)j.sum_row * kSysPart;
+    const float* f0 = reinterpret_cast<const float*>(p0);
     for (int k = 0; k < kLowSums; ++k) {
-      const double t = ordered_sum(p0 + kSysPartLow + k, j.n_tiles, kSysPart, lane);
+      const double t = ordered_ff_sum(f0 + kRowLow + 2 * k, j.n_tiles, kRowFloats, lane);
       if (lane == 0) sr[kSysPartLow + k] = t;
     }
   }

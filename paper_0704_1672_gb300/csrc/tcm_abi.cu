@@ -3,11 +3,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <unordered_map>
 #include <new>
 #include <tuple>
 #include <vector>
@@ -98,7 +100,7 @@ struct tcm_ctx {
   int* d_imap = nullptr;      // (chunk, slot) -> packed component, both precisions
   int* d_imap_off = nullptr;  // [precision][L] offsets into d_imap
   // scratch
-  DevBuf desc, partials, gpart, systk, counters, moms, escr, dpart, tiles;
+  DevBuf desc, partials, gpart, systk, systiles, counters, moms, escr, dpart, tiles;
   Stage stage[kStages];
   int stage_next = 0;
   void* pinned_small = nullptr;  // 256 B for small device->host reads
@@ -115,6 +117,7 @@ struct tcm_ctx {
   std::vector<Mark> marks;
   std::vector<cudaEvent_t> ev_pool;
   int64_t launches[TCM_NPHASES] = {};
+  double host_ms = 0.0;  // TCM_PHASE_HOST: wall time inside the batched calls while profiling
   // CUDA-graph replay of the batched launch sequence
   bool rotate_cached = false;  // rotated B sides from the moment cache by Wigner rotation
   int graphs = 1;  // 0: launch directly; 1: capture a shape seen twice in a row; 2: capture every new shape
@@ -228,10 +231,6 @@ bool geom_known(const tcm_system& s) { return s.has_center && s.radius >= 0.0; }
 
 // Moment-job planning -------------------------------------------------------------
 
-struct JobKey {
-  int sys, L, rot_item;  // rot_item = -1 when unrotated
-  bool operator<(const JobKey& o) const { return std::tie(sys, L, rot_item) < std::tie(o.sys, o.L, o.rot_item); }
-};
 
 struct Plan {
   std::vector<MomJob> jobs;
@@ -256,9 +255,7 @@ void plan_job(tcm_ctx* c, int precision, MomJob& j, int& next_id) {
 }
 
 double chunk_cost(int precision, int L, int chunk) {
-  const int kmax = moments_kmax(precision);
-  const int nch = plan_nch(L, kmax);
-  const int m0 = plan_m0(L, kmax, nch, chunk), m1 = plan_m0(L, kmax, nch, chunk + 1);
+  const int m0 = moments_chunk_m0(precision, L, chunk), m1 = moments_chunk_m0(precision, L, chunk + 1);
   return 1.25 * chunk_off(L, m0, m1) + 4.0 * m0 + 30.0;
 }
 
@@ -316,15 +313,6 @@ int ensure_moment_buffers(tcm_ctx* c, int precision, const Plan& P) {
 // degrees.
 constexpr int kAnyCounter = kLmaxMax + 1;
 
-// The tile list of the plan, written on the device from its groups (first launch of a call: it
-// depends on nothing queued before it).
-int run_expand(tcm_ctx* c, const Plan& P, const MomJob* d_jobs, const MomGroup* d_groups, cudaStream_t st) {
-  if (P.groups.empty()) return TCM_OK;
-  PhaseScope ps(c, TCM_PHASE_GEOM, 1);
-  TRY_LAUNCH(launch_expand_tiles(d_groups, (int)P.groups.size(), d_jobs, static_cast<MomTile*>(c->tiles.p), st));
-  return TCM_OK;
-}
-
 int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, const SysGeom* d_geoms,
                 cudaStream_t st) {
   const int kmax = moments_kmax(precision);
@@ -372,7 +360,7 @@ int moment_launches(int precision, const Plan& P) {
 // system with a computed moment job.
 struct SysPlan {
   std::vector<SysJob> jobs;
-  std::vector<SysTile> t1, t2;  // tiles of pass 1 (centroid) and pass 2 (radius, low-degree sums)
+  int n1 = 0, n2 = 0;            // tiles of pass 1 (centroid) and pass 2 (radius, low-degree sums)
   std::vector<int> of_system;   // system -> index of its SysJob, or -1
   int rows = 0;
 };
@@ -402,10 +390,10 @@ void plan_sys(const tcm_system* systems, int n_systems, const std::vector<char>&
     S.rows += j.n_tiles;
     j.sum_row = -1;
     const int ji = (int)S.jobs.size();
-    for (int t = 0; t < j.n_tiles; ++t) {
-      if (nc) S.t1.push_back(SysTile{ji, t});
-      if (nr || nl) S.t2.push_back(SysTile{ji, t});
-    }
+    j.first1 = nc ? S.n1 : -1;
+    j.first2 = (nr || nl) ? S.n2 : -1;
+    if (nc) S.n1 += j.n_tiles;
+    if (nr || nl) S.n2 += j.n_tiles;
     S.of_system[s] = ji;
     S.jobs.push_back(j);
   }
@@ -430,21 +418,38 @@ int ensure_sys_buffers(tcm_ctx* c, const SysPlan& S) {
   void* before = c->systk.p;
   TRY(dev_ensure(c, c->systk, std::max<size_t>(2 * S.jobs.size(), 64) * sizeof(int)));
   if (c->systk.p != before) TRY_CUDA(cudaMemsetAsync(c->systk.p, 0, c->systk.cap, c->stream));
+  TRY(dev_ensure(c, c->systiles, (size_t)std::max(S.n1 + S.n2, 1) * sizeof(SysTile)));
   return TCM_OK;
 }
 
-int run_sys(tcm_ctx* c, const SysPlan& S, const SysJob* d_sj, const SysTile* d_t1, const SysTile* d_t2, SysGeom* d_geo,
-            cudaStream_t st) {
+int run_sys(tcm_ctx* c, const SysPlan& S, const SysJob* d_sj, SysGeom* d_geo, cudaStream_t st) {
   if (S.jobs.empty()) return TCM_OK;
-  PhaseScope ps(c, TCM_PHASE_GEOM, sys_launches((int)S.t1.size(), (int)S.t2.size()));
-  TRY_LAUNCH(launch_sys(d_sj, d_t1, (int)S.t1.size(), d_t2, (int)S.t2.size(), static_cast<double*>(c->gpart.p),
+  PhaseScope ps(c, TCM_PHASE_GEOM, sys_launches(S.n1, S.n2));
+  SysTile* t1 = static_cast<SysTile*>(c->systiles.p);
+  TRY_LAUNCH(launch_sys(d_sj, t1, S.n1, t1 + S.n1, S.n2, static_cast<double*>(c->gpart.p),
                         static_cast<int*>(c->systk.p), d_geo, st));
+  return TCM_OK;
+}
+
+// The tile lists of the call (moment pass and system pass), written on the device from the
+// groups and system jobs: the first launch of a call (it depends on nothing queued before it).
+int run_expand(tcm_ctx* c, const std::vector<MomGroup>& groups, const MomJob* d_jobs, const MomGroup* d_groups,
+               const SysPlan& S, const SysJob* d_sj, cudaStream_t st) {
+  if (groups.empty() && S.jobs.empty()) return TCM_OK;
+  PhaseScope ps(c, TCM_PHASE_GEOM, 1);
+  SysTile* t1 = static_cast<SysTile*>(c->systiles.p);
+  TRY_LAUNCH(launch_expand_tiles(d_groups, (int)groups.size(), d_jobs, static_cast<MomTile*>(c->tiles.p), d_sj,
+                                 (int)S.jobs.size(), t1, t1 + S.n1, st));
   return TCM_OK;
 }
 
 SysGeom host_geom(const tcm_system& s) {
   SysGeom g{};
-  for (int d = 0; d < 3; ++d) g.c[d] = s.has_center ? s.center[d] : 0.0;
+  for (int d = 0; d < 3; ++d) {
+    g.c[d] = s.has_center ? s.center[d] : 0.0;
+    g.chi[d] = (float)g.c[d];
+    g.clo[d] = (float)(g.c[d] - (double)g.chi[d]);
+  }
   g.a = s.radius >= 0.0 ? s.radius : 0.0;
   return g;
 }
@@ -479,7 +484,8 @@ void free_ctx(tcm_ctx* c) {
   cudaFree(c->d_ztab);
   cudaFree(c->d_imap);
   cudaFree(c->d_imap_off);
-  for (DevBuf* b : {&c->desc, &c->partials, &c->gpart, &c->systk, &c->counters, &c->moms, &c->escr, &c->dpart, &c->tiles})
+  for (DevBuf* b : {&c->desc, &c->partials, &c->gpart, &c->systk, &c->systiles, &c->counters, &c->moms, &c->escr,
+                     &c->dpart, &c->tiles})
     cudaFree(b->p);
   for (auto& st : c->stage) {
     if (st.host) cudaFreeHost(st.host);
@@ -619,6 +625,8 @@ int tcm_ctx_read_profile(tcm_ctx_t c, double* ms, int64_t* launches) {
   TRY(check_ctx(c));
   TRY_CUDA(cudaStreamSynchronize(c->stream));
   double acc[TCM_NPHASES] = {};
+  acc[TCM_PHASE_HOST] = c->host_ms;
+  c->host_ms = 0.0;
   for (auto& m : c->marks) {
     float t = 0.0f;
     if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess) acc[m.phase] += t;
@@ -643,13 +651,14 @@ int tcm_prepare(tcm_ctx_t c, tcm_system* s) {
   plan_sys(s, 1, used, {}, S);
   std::vector<SysGeom> geoms{host_geom(*s)};
   Packer pk;
-  const size_t o_geo = pk.add(geoms), o_sj = pk.add(S.jobs), o_t1 = pk.add(S.t1), o_t2 = pk.add(S.t2);
+  const size_t o_geo = pk.add(geoms), o_sj = pk.add(S.jobs);
   TRY(ensure_sys_buffers(c, S));
   char* base = nullptr;
   TRY(upload(c, pk, &base));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
-  TRY(run_sys(c, S, reinterpret_cast<SysJob*>(base + o_sj), reinterpret_cast<SysTile*>(base + o_t1),
-              reinterpret_cast<SysTile*>(base + o_t2), d_geo, c->stream));
+  const SysJob* d_sj = reinterpret_cast<SysJob*>(base + o_sj);
+  TRY(run_expand(c, {}, nullptr, nullptr, S, d_sj, c->stream));
+  TRY(run_sys(c, S, d_sj, d_geo, c->stream));
   TRY_CUDA(cudaMemcpyAsync(c->pinned_small, d_geo, sizeof(SysGeom), cudaMemcpyDeviceToHost, c->stream));
   TRY_CUDA(cudaStreamSynchronize(c->stream));
   const SysGeom* g = static_cast<const SysGeom*>(c->pinned_small);
@@ -690,16 +699,16 @@ int tcm_moments(tcm_ctx_t c, const tcm_system* s, const double* rot, int lmax, i
   link_low(S, P);
   std::vector<SysGeom> geoms{host_geom(*s)};
   Packer pk;
-  const size_t o_geo = pk.add(geoms), o_job = pk.add(P.jobs), o_tile = pk.add(P.groups), o_sj = pk.add(S.jobs),
-               o_t1 = pk.add(S.t1), o_t2 = pk.add(S.t2);
+  const size_t o_geo = pk.add(geoms), o_job = pk.add(P.jobs), o_tile = pk.add(P.groups), o_sj = pk.add(S.jobs);
   TRY(ensure_moment_buffers(c, precision, P));
   TRY(ensure_sys_buffers(c, S));
   char* base = nullptr;
   TRY(upload(c, pk, &base));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
-  TRY(run_expand(c, P, reinterpret_cast<MomJob*>(base + o_job), reinterpret_cast<MomGroup*>(base + o_tile), c->stream));
-  TRY(run_sys(c, S, reinterpret_cast<SysJob*>(base + o_sj), reinterpret_cast<SysTile*>(base + o_t1),
-              reinterpret_cast<SysTile*>(base + o_t2), d_geo, c->stream));
+  const SysJob* d_sj = reinterpret_cast<SysJob*>(base + o_sj);
+  TRY(run_expand(c, P.groups, reinterpret_cast<MomJob*>(base + o_job), reinterpret_cast<MomGroup*>(base + o_tile), S,
+                 d_sj, c->stream));
+  TRY(run_sys(c, S, d_sj, d_geo, c->stream));
   TRY(run_moments(c, precision, P, reinterpret_cast<MomJob*>(base + o_job), d_geo, c->stream));
   out->lmax = lmax;
   if (!geom_known(*s)) {
@@ -798,15 +807,26 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
                  int precision, double* E, int32_t* status, double* G);
 }
 
+namespace {
+// The batched call, with its host wall time added to TCM_PHASE_HOST while profiling is on.
+int timed_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t n_items, const tcm_pair_item* items,
+                int precision, double* E, int32_t* status, double* G) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int rc = energy_batch(c, n_systems, systems, n_items, items, precision, E, status, G);
+  if (c && c->prof) c->host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return rc;
+}
+}  // namespace
+
 int tcm_energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t n_items, const tcm_pair_item* items,
                      int precision, double* E, int32_t* status) {
-  return energy_batch(c, n_systems, systems, n_items, items, precision, E, status, nullptr);
+  return timed_batch(c, n_systems, systems, n_items, items, precision, E, status, nullptr);
 }
 
 int tcm_gradients_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t n_items,
                         const tcm_pair_item* items, int precision, double* E, double* G, int32_t* status) {
   if (n_items > 0 && !G) return set_err(TCM_EINVAL, "tcm_gradients_batch: null gradient output");
-  return energy_batch(c, n_systems, systems, n_items, items, precision, E, status, G);
+  return timed_batch(c, n_systems, systems, n_items, items, precision, E, status, G);
 }
 
 namespace {
@@ -842,7 +862,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   }
   // moment jobs (A sides and unrotated B sides shared)
   Plan P;
-  std::map<JobKey, int> job_of;
+  std::unordered_map<long long, int> job_of;  // unrotated jobs by (system, Lmax)
   std::vector<PairDesc> pd(n_items);
   int next_id = 0;
   size_t moff = 0;
@@ -861,7 +881,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
       cached_of[sys] = (int)cached.size() - 1;
       return -2 - ((int)cached.size() - 1);
     }
-    JobKey key{sys, L, rot_item};
+    const long long key = (long long)sys * (kLmaxMax + 1) + L;
     if (rot_item < 0) {  // rotated jobs are unique to their item: no lookup
       auto itr = job_of.find(key);
       if (itr != job_of.end()) return itr->second;
@@ -942,7 +962,7 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   for (int s = 0; s < n_systems; ++s) geoms[s] = host_geom(systems[s]);
   Packer pk;
   const size_t o_geo = pk.add(geoms), o_job = pk.add(all_jobs), o_tile = pk.add(P.groups), o_sj = pk.add(S.jobs),
-               o_t1 = pk.add(S.t1), o_t2 = pk.add(S.t2), o_it = pk.add(pd), o_rot = pk.add(rots);
+               o_it = pk.add(pd), o_rot = pk.add(rots);
   // every buffer the launches touch is sized before anything is queued (no reallocation
   // may happen while a graph is being captured)
   TRY(ensure_sys_buffers(c, S));
@@ -952,9 +972,9 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
   const MomJob* d_jobs = reinterpret_cast<MomJob*>(base + o_job);
   auto enqueue = [&](cudaStream_t st) -> int {
-    TRY(run_expand(c, P, d_jobs, reinterpret_cast<MomGroup*>(base + o_tile), st));
-    TRY(run_sys(c, S, reinterpret_cast<SysJob*>(base + o_sj), reinterpret_cast<SysTile*>(base + o_t1),
-                reinterpret_cast<SysTile*>(base + o_t2), d_geo, st));
+    const SysJob* d_sj = reinterpret_cast<SysJob*>(base + o_sj);
+    TRY(run_expand(c, P.groups, d_jobs, reinterpret_cast<MomGroup*>(base + o_tile), S, d_sj, st));
+    TRY(run_sys(c, S, d_sj, d_geo, st));
     TRY(run_moments(c, precision, P, d_jobs, d_geo, st));
     PhaseScope ps(c, TCM_PHASE_CONTRACT, 1);
     TRY_LAUNCH(launch_contract(reinterpret_cast<PairDesc*>(base + o_it), (int)n_items, Lmax_items, d_jobs, d_geo,
@@ -966,9 +986,9 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   // Replay a captured graph of the launch sequence when this call has the same shape and
   // buffers as the captured one (only the uploaded descriptor contents differ).
   std::vector<long long> key = {precision, G != nullptr, (long long)(uintptr_t)G, (long long)S.jobs.size(),
-                                (long long)S.t1.size(), (long long)S.t2.size(), (long long)P.jobs.size(), P.n_tile_ids,
+                                (long long)S.n1, (long long)S.n2, (long long)P.jobs.size(), P.n_tile_ids,
                                 (long long)n_items, Lmax_items, (long long)o_geo, (long long)o_job, (long long)o_tile,
-                                (long long)o_sj, (long long)o_t1, (long long)o_t2, (long long)o_it, (long long)o_rot,
+                                (long long)o_sj, (long long)o_it, (long long)o_rot, (long long)(uintptr_t)c->systiles.p,
                                 (long long)rots.empty(), (long long)(uintptr_t)base, (long long)(uintptr_t)c->gpart.p,
                                 (long long)(uintptr_t)c->systk.p, (long long)(uintptr_t)c->partials.p,
                                 (long long)(uintptr_t)c->counters.p, (long long)(uintptr_t)E, (long long)(uintptr_t)status,
@@ -986,7 +1006,8 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
       c->gexec = nullptr;
     }
     TRY_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const int64_t saved[TCM_NPHASES] = {c->launches[0], c->launches[1], c->launches[2], c->launches[3], c->launches[4]};
+    int64_t saved[TCM_NPHASES];
+    std::copy(c->launches, c->launches + TCM_NPHASES, saved);
     const int rc = enqueue(c->cap_stream);
     for (int k = 0; k < TCM_NPHASES; ++k) c->launches[k] = saved[k];
     cudaGraph_t g = nullptr;
@@ -1007,8 +1028,8 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   }
   TRY_CUDA(cudaGraphLaunch(c->gexec, c->stream));
   ++c->graph_launches;
-  c->launches[TCM_PHASE_GEOM] += (S.jobs.empty() ? 0 : sys_launches((int)S.t1.size(), (int)S.t2.size())) +
-                                  (P.groups.empty() ? 0 : 1);
+  c->launches[TCM_PHASE_GEOM] += (S.jobs.empty() ? 0 : sys_launches(S.n1, S.n2)) +
+                                  ((P.groups.empty() && S.jobs.empty()) ? 0 : 1);
   c->launches[TCM_PHASE_MOMENTS] += moment_launches(precision, P);
   c->launches[TCM_PHASE_FINALIZE] += 1;
   c->launches[TCM_PHASE_CONTRACT] += 1;
@@ -1037,16 +1058,16 @@ int direct_items(tcm_ctx_t c, const tcm_system* A, const tcm_system* B, int64_t 
     for (int d = 0; d < 3; ++d) xf[12 * k + 9 + d] = R0[3 * k + d];
   }
   Packer pk;
-  const size_t o_geo = pk.add(geoms), o_xf = pk.add(xf), o_sj = pk.add(S.jobs), o_t1 = pk.add(S.t1),
-               o_t2 = pk.add(S.t2);
+  const size_t o_geo = pk.add(geoms), o_xf = pk.add(xf), o_sj = pk.add(S.jobs);
   const int nblk = direct_blocks(A->n);
   TRY(ensure_sys_buffers(c, S));
   TRY(dev_ensure(c, c->dpart, (size_t)std::max<int64_t>(nblk * n, 1) * sizeof(double)));
   char* base = nullptr;
   TRY(upload(c, pk, &base));
   SysGeom* d_geo = reinterpret_cast<SysGeom*>(base + o_geo);
-  TRY(run_sys(c, S, reinterpret_cast<SysJob*>(base + o_sj), reinterpret_cast<SysTile*>(base + o_t1),
-              reinterpret_cast<SysTile*>(base + o_t2), d_geo, c->stream));
+  const SysJob* d_sj = reinterpret_cast<SysJob*>(base + o_sj);
+  TRY(run_expand(c, {}, nullptr, nullptr, S, d_sj, c->stream));
+  TRY(run_sys(c, S, d_sj, d_geo, c->stream));
   const int nlaunch = (int)((n + 65534) / 65535) * (nblk > 0 ? 2 : 1);
   PhaseScope ps(c, TCM_PHASE_DIRECT, nlaunch);
   TRY_LAUNCH(launch_direct(A->xyzq, A->n, A->dtype, B->xyzq, B->n, B->dtype, d_geo,

@@ -133,6 +133,8 @@ __host__ __device__ inline double scale_radius(double a) {
 struct SysGeom {   // centre and radius of one system (device)
   double c[3];
   double a;
+  float chi[3], clo[3];  // the centre split into float parts c = chi + clo (set with c)
+  float pad_[2];
 };
 
 struct MomJob {    // one moment set: a system at one Lmax under one rotation
@@ -178,6 +180,8 @@ struct SysJob {
   int n_tiles;
   int atoms_per_tile;
   int sum_row;       // row of its low-degree sums over all tiles (written by its last tile)
+  int first1;        // position of its first tile in the pass-1 tile list (-1: no pass 1)
+  int first2;        // position of its first tile in the pass-2 tile list (-1: no pass 2)
 };
 
 struct SysTile {
@@ -232,9 +236,12 @@ cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
 // counter[32] must be zero on entry; the launch leaves them zero.
 int launch_moments(int precision, int L, const MomJob* jobs, const MomTile* tiles, int n_tiles,
                    int* counter, const SysGeom* geoms, double* partials, int grid, cudaStream_t s);
-// The tile list of a moment pass from its groups: tiles[g.first + t] = (g.job, g.chunk, t, row),
-// t < g.n, row = jobs[g.job].tile_base + g.chunk * tiles_per_chunk + t.  One warp per group.
-int launch_expand_tiles(const MomGroup* groups, int n_groups, const MomJob* jobs, MomTile* tiles, cudaStream_t s);
+// The tile lists of a call, written on the device: the moment pass's from its groups,
+// tiles[g.first + t] = (g.job, g.chunk, t, row), t < g.n, row = jobs[g.job].tile_base +
+// g.chunk * tiles_per_chunk + t; and the system pass's, t1[sj.first1 + t] = t2[sj.first2 + t] =
+// (job, t), t < sj.n_tiles.  One warp per group or system job.
+int launch_expand_tiles(const MomGroup* groups, int n_groups, const MomJob* jobs, MomTile* tiles, const SysJob* sjobs,
+                        int n_sjobs, SysTile* t1, SysTile* t2, cudaStream_t s);
 // Mixed precision: one persistent launch over tiles of any degrees (each tile runs the code of
 // its job's degree); the tiles are taken in array order.
 int launch_moments_any(const MomJob* jobs, const MomTile* tiles, int n_tiles, int* counter, const SysGeom* geoms,
@@ -242,6 +249,7 @@ int launch_moments_any(const MomJob* jobs, const MomTile* tiles, int n_tiles, in
 int moments_smem_bytes(int precision, int L);
 int moments_kmax(int precision);
 int moments_nchunks(int precision, int L);
+int moments_chunk_m0(int precision, int L, int chunk);  // first column of a chunk (chunk = nch: L + 1)
 // Host: the inverse component maps of both precisions and their factors F_lm (imap_off has
 // 2 (kLmaxMax + 2) entries, FP64 first, each block ending with its total).
 void finalize_tables(std::vector<int>& imap_off, std::vector<int>& imap, std::vector<double>& fmap);

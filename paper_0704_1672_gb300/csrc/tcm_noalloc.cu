@@ -151,7 +151,11 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   for (int k = 0; k < 9; ++k) job.rot[k] = rot ? rot[k] : ((k % 4 == 0) ? 1.0 : 0.0);
   job.out = q_out;
   SysGeom geom{};
-  for (int d = 0; d < 3; ++d) geom.c[d] = s->has_center ? s->center[d] : 0.0;
+  for (int d = 0; d < 3; ++d) {
+    geom.c[d] = s->has_center ? s->center[d] : 0.0;
+    geom.chi[d] = (float)geom.c[d];
+    geom.clo[d] = (float)(geom.c[d] - (double)geom.chi[d]);
+  }
   geom.a = s->radius >= 0.0 ? s->radius : 0.0;
   // the pass over the atoms before the moment pass, as tcm_moments plans it: the centroid when
   // no centre is given, the radius when no radius is given, and the low-degree sums of the
@@ -167,6 +171,8 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   sj.atoms_per_tile = sys_tile_atoms(s->n);
   sj.n_tiles = (int)std::max<long long>(1, (s->n + sj.atoms_per_tile - 1) / sj.atoms_per_tile);
   sj.tile_base = 0;
+  sj.first1 = sj.need_center ? 0 : -1;  // the tile lists are written by k_noalloc_prepare
+  sj.first2 = 0;
   sj.sum_row = sj.n_tiles;  // the row after the tile rows
   if (sj.n_tiles + 1 > kNaSysTiles) return na_err(TCM_EINVAL, "tcm_moments_noalloc: request exceeds the fixed scratch");
   job.low_base = sj.sum_row;
@@ -196,7 +202,7 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
                       reinterpret_cast<int*>(base + kOffImapOff) + (precision == TCM_FP64 ? 0 : kLmaxMax + 2),
                       kmax, reinterpret_cast<double*>(base + kOffSPart), st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: finalisation launch failed");
-  if (geom_out && cudaMemcpyAsync(geom_out, d_geom, sizeof(SysGeom), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+  if (geom_out && cudaMemcpyAsync(geom_out, d_geom, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: copy of the centre and radius failed");
   return TCM_OK;
 }

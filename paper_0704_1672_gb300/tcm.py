@@ -21,7 +21,7 @@ TCM_OK, TCM_EINVAL, TCM_ENOTCONV, TCM_ENOMEM, TCM_ECUDA, TCM_ETIMEOUT = range(6)
 TCM_F32, TCM_F64 = 0, 1
 TCM_FP64, TCM_MIXED = 0, 1
 LMAX_MAX = 24
-PHASES = ("geom", "moments", "finalize", "contract", "direct")
+PHASES = ("geom", "moments", "finalize", "contract", "direct", "host")
 NPHASES = len(PHASES)
 _NAMES = {0: "TCM_OK", 1: "TCM_EINVAL", 2: "TCM_ENOTCONV", 3: "TCM_ENOMEM", 4: "TCM_ECUDA", 5: "TCM_ETIMEOUT"}
 
