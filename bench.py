@@ -529,7 +529,8 @@ def run_ours(args, rank, world, dist):
 
 # ----------------------------------------------------------------------------- other workloads
 
-def bench_config2(torch, tcm, synth, autotune, timer, stream, prec, peak_fp32, peak_fp64, n_sm, smx, steps=200):
+def bench_config2(torch, tcm, synth, autotune, timer, stream, prec, peak_fp32, peak_fp64, n_sm, smx, steps=200,
+                  tune=True):
     """Protein-like PES scan: 2 x 20,000 atoms, 256 orientations of B, Lmax = 20."""
     s = synth.protein_pes_scan()
     k = len(s.R0)
@@ -540,7 +541,7 @@ def bench_config2(torch, tcm, synth, autotune, timer, stream, prec, peak_fp32, p
     ctx = tcm.Context(lmax_cap=L, stream=stream)
     systems = [(A, None, None), (B, None, None)]
     ia, ib, il = np.zeros(k, int), np.ones(k, int), np.full(k, L)
-    tuned = autotune.tune(ctx, systems, ia, ib, il, s.R0, rotB=s.rotB, precision=prec, reps=3)
+    tuned = autotune.tune(ctx, systems, ia, ib, il, s.R0, rotB=s.rotB, precision=prec, reps=3) if tune else None
     pb = tcm.pack_batch(systems, ia, ib, il, s.R0, rotB=s.rotB)
     E = torch.empty(k, dtype=torch.float64, device="cuda")
     st = torch.empty(k, dtype=torch.int32, device="cuda")
@@ -573,7 +574,7 @@ def bench_config2(torch, tcm, synth, autotune, timer, stream, prec, peak_fp32, p
            "contract_roofline": {"bound": "fp64", "achieved": con, "peak": peak_fp64, "unit": "G FP64 op/s",
                                  "frac": con / peak_fp64, "launch_ms": con_launch_ms,
                                  "algorithmic_fp64_per_energy": contract_fp64_ops(L)},
-           "tiling": {"atoms_per_lane": tuned.best[L][0], "ctas_per_sm": tuned.best[L][1]}}
+           "tiling": {"atoms_per_lane": tuned.best[L][0], "ctas_per_sm": tuned.best[L][1]} if tuned else "default"}
     # B's moments rotated from a cache (Wigner rotation in the contraction kernel) instead of
     # recomputed from its atoms: moments of A and B once, outside the timed steps
     mA = ctx.tcm_moments(A, L, precision=prec)
@@ -788,7 +789,7 @@ def run_only(args):
     if args.only == "protein_pes_scan":
         rec = bench_config2(torch, tcm, synth, autotune, Timer(torch, stream), stream, prec,
                             n_sm * FP32_LANES_PER_SM * smx * 1e6 / 1e12, n_sm * FP64_PER_SM_CLK * smx * 1e6 / 1e9,
-                            n_sm, smx, steps=args.steps)
+                            n_sm, smx, steps=args.steps, tune=not args.no_autotune)
     else:
         rec = bench_config3(torch, tcm, synth, stream, prec, tune=not args.no_autotune)
     print(json.dumps({args.only: rec}), flush=True)

@@ -264,29 +264,39 @@ double chunk_cost(int precision, int L, int chunk) {
 // one order over all degrees (one launch).  The tiles themselves are written on the device
 // (k_expand_tiles), so the host work is O(groups log groups).
 void build_tiles(int precision, Plan& P) {
+  // one 64-bit key per group: [degree (FP64 only)] [largest cost first] [group index], so a plain
+  // sort of integers gives the order deterministically (ties in their planning order)
   struct Group {
-    double cost;
-    int L, job, chunk;
+    int job, chunk;
   };
-  std::vector<Group> v;
+  std::vector<Group> g;
+  std::vector<unsigned long long> key;
+  g.reserve(P.jobs.size() * 2);
+  key.reserve(P.jobs.size() * 2);
+  const bool by_degree = precision == TCM_FP64;
   for (int ji = 0; ji < (int)P.jobs.size(); ++ji) {
     const MomJob& j = P.jobs[ji];
     const int nch = moments_nchunks(precision, j.L);
-    for (int ch = 0; ch < nch; ++ch) v.push_back({chunk_cost(precision, j.L, ch) * (double)j.atoms_per_tile, j.L, ji, ch});
+    for (int ch = 0; ch < nch; ++ch) {
+      const double cost = chunk_cost(precision, j.L, ch) * (double)j.atoms_per_tile;
+      const unsigned long long cq = (unsigned long long)std::min(cost, 134217727.0);  // 27 bits
+      key.push_back(((by_degree ? (unsigned long long)j.L : 0ull) << 59) | ((134217727ull - cq) << 32) |
+                    (unsigned long long)g.size());
+      g.push_back(Group{ji, ch});
+    }
   }
-  const bool by_degree = precision == TCM_FP64;
-  std::stable_sort(v.begin(), v.end(), [by_degree](const Group& a, const Group& b) {
-    if (by_degree && a.L != b.L) return a.L < b.L;
-    return a.cost > b.cost;
-  });
+  std::sort(key.begin(), key.end());
   P.groups.clear();
-  P.groups.reserve(v.size());
-  int first = 0, gi = 0;
+  P.groups.reserve(g.size());
+  int first = 0;
+  size_t gi = 0;
   for (int L = 0; L <= kLmaxMax; ++L) {
     P.tile_begin[L] = first;
-    for (; gi < (int)v.size() && (!by_degree || v[gi].L == L); ++gi) {
-      const int n = P.jobs[v[gi].job].tiles_per_chunk;
-      P.groups.push_back(MomGroup{v[gi].job, v[gi].chunk, n, first});
+    for (; gi < key.size(); ++gi) {
+      const Group& gr = g[key[gi] & 0xffffffffull];
+      if (by_degree && P.jobs[gr.job].L != L) break;
+      const int n = P.jobs[gr.job].tiles_per_chunk;
+      P.groups.push_back(MomGroup{gr.job, gr.chunk, n, first});
       first += n;
     }
   }
@@ -863,6 +873,8 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
   // moment jobs (A sides and unrotated B sides shared)
   Plan P;
   std::unordered_map<long long, int> job_of;  // unrotated jobs by (system, Lmax)
+  job_of.reserve((size_t)std::min<int64_t>(n_items, 1 << 20) * 2);
+  P.jobs.reserve((size_t)std::min<int64_t>(n_items, 1 << 20) * 2);
   std::vector<PairDesc> pd(n_items);
   int next_id = 0;
   size_t moff = 0;
