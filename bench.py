@@ -406,13 +406,16 @@ def run_ours(args, rank, world, dist):
     ia, ib, il = np.zeros(k, int), np.ones(k, int), np.full(k, L)
     tiling = None
     if not args.no_autotune:
-        # the moment pass's warp tiles and grid chosen by the library's autotuner on a sample of
-        # this batch's own items, before any timed step
+        # the moment pass's warp tiles, grid and L-chunking chosen by the library's autotuner on a
+        # sample of this batch's own items, before any timed step
         tuned = autotune.tune(ctx, systems, ia, ib, il, s.R0, rotB=s.rotB, precision=prec, reps=2,
                               max_items_per_l=512, atoms_per_lane=(32, 64, 96, 128, 256))
         tiling = {"lmax": L, "atoms_per_lane": tuned.best[L][0], "ctas_per_sm": tuned.best[L][1],
+                  "kmax": tuned.best[L][2], "chunks": ctx.tcm_ctx_get_chunking_l(L)[1],
                   "tuned_on": "512 of the 10,000 orientations",
-                  "moment_phase_ms_by_candidate": {f"{a}x{c}": round(ms, 5) for (a, c), ms in tuned.timings[L].items()}}
+                  "moment_phase_ms_by_candidate": {"x".join(str(x) for x in c): round(ms, 5)
+                                                   for c, ms in tuned.timings[L].items()},
+                  "candidate_key": "atoms_per_lane x ctas_per_sm x kmax"}
     pb = tcm.pack_batch(systems, ia, ib, il, s.R0, rotB=s.rotB)
     E = torch.empty(k, dtype=torch.float64, device="cuda")
     st = torch.empty(k, dtype=torch.int32, device="cuda")
@@ -574,7 +577,8 @@ def bench_config2(torch, tcm, synth, autotune, timer, stream, prec, peak_fp32, p
            "contract_roofline": {"bound": "fp64", "achieved": con, "peak": peak_fp64, "unit": "G FP64 op/s",
                                  "frac": con / peak_fp64, "launch_ms": con_launch_ms,
                                  "algorithmic_fp64_per_energy": contract_fp64_ops(L)},
-           "tiling": {"atoms_per_lane": tuned.best[L][0], "ctas_per_sm": tuned.best[L][1]} if tuned else "default"}
+           "tiling": {"atoms_per_lane": tuned.best[L][0], "ctas_per_sm": tuned.best[L][1], "kmax": tuned.best[L][2],
+                      "chunks": ctx.tcm_ctx_get_chunking_l(L)[1]} if tuned else "default"}
     # B's moments rotated from a cache (Wigner rotation in the contraction kernel) instead of
     # recomputed from its atoms: moments of A and B once, outside the timed steps
     mA = ctx.tcm_moments(A, L, precision=prec)
@@ -655,7 +659,8 @@ def bench_config3(torch, tcm, synth, stream, prec, calls=3, tune=True):
             "energies_per_s": len(b.L) / (np.median(dev_ms) * 1e-3),
             "moment_components_per_s": comps / (np.median(dev_ms) * 1e-3),
             "phase_ms_one_call": ph, "launches_one_call": la, "graph_captures": caps, "graph_launches": glaunch,
-            "tiling": {str(L): list(v) for L, v in tuned.best.items()} if tuned else "default", "generator_s": t_gen,
+            "tiling": ({str(L): list(v) for L, v in tuned.best.items()} if tuned else "default"),
+            "tiling_key": "L: [atoms_per_lane, ctas_per_sm, kmax]", "generator_s": t_gen,
             "how": "each call is timed alone (CUDA events around one tcm_energy_batch call, with its host planning, "
                    "descriptor upload and, on a shape's first call, the graph capture); calls 2 and 3 use new "
                    "orientations"}

@@ -148,17 +148,31 @@ typedef enum {
 int tcm_ctx_set_tiling(tcm_ctx_t ctx, int precision, int atoms_per_lane);
 
 /* The moment-pass tiling of one degree lmax in [0, TCM_LMAX_MAX] at one precision: atoms per
- * lane of a warp tile (as above) and the resident CTAs per SM, in [1, 2], that the persistent
- * grid of that degree's launch is sized for (grid = min(work, ctas_per_sm x SMs) CTAs of four
- * warps).  Defaults: 32 (FP64) or 64 (mixed) atoms per lane, 2 CTAs per SM.  Set by the
- * autotuner; results stay within the stated tolerances for any setting (only the summation
- * order of the atom sums changes).  tcm_ctx_get_tiling_l reads the current setting. */
+ * lane of a warp tile (as above) and the resident CTAs per SM that the persistent grid of
+ * that degree's launch is sized for (grid = min(work, ctas_per_sm x SMs) CTAs of four warps):
+ * [1, 2] for TCM_FP64, [1, 3] for TCM_MIXED, where a launch's grid is held to what its
+ * kernel is compiled for (2 CTAs per SM at the 160-accumulator chunk budget, 3 at 96; see
+ * tcm_ctx_set_chunking_l).  Defaults: 32 (FP64) or 64 (mixed) atoms per lane, 2 CTAs per SM.
+ * Set by the autotuner; results stay within the stated tolerances for any setting (only the
+ * summation order of the atom sums changes).  tcm_ctx_get_tiling_l reads the current
+ * setting. */
 int tcm_ctx_set_tiling_l(tcm_ctx_t ctx, int precision, int lmax, int atoms_per_lane, int ctas_per_sm);
 int tcm_ctx_get_tiling_l(tcm_ctx_t ctx, int precision, int lmax, int* atoms_per_lane, int* ctas_per_sm);
 
+/* The L-chunking of the mixed path's moment pass for one degree lmax in [0, TCM_LMAX_MAX]:
+ * each lane keeps at most kmax float accumulators of Eq. (multipole) in registers, so the
+ * (lmax+1)^2 components are split into column chunks of at most kmax, each a tile that
+ * re-reads its atoms.  kmax = 160 (default; kernel compiled for 2 CTAs per SM) or 96 (more
+ * chunks, fewer registers, 3 CTAs per SM).  A batch whose degrees use both budgets runs one
+ * moment launch per budget.  Set by the autotuner; like the tiling it changes only the
+ * summation order.  tcm_ctx_get_chunking_l reads kmax and the resulting number of chunks
+ * (either pointer may be NULL).  TCM_EINVAL for another kmax or lmax. */
+int tcm_ctx_set_chunking_l(tcm_ctx_t ctx, int lmax, int kmax);
+int tcm_ctx_get_chunking_l(tcm_ctx_t ctx, int lmax, int* kmax, int* n_chunks);
+
 /* CUDA-graph replay of tcm_energy_batch.  A call's launch sequence (tile list, centres and
- * radii, low-degree sums, the moment pass -- one launch over all degrees in TCM_MIXED, one per
- * degree in TCM_FP64 --, finalisation, contraction) is captured into a graph and replayed by
+ * radii, low-degree sums, the moment pass -- one launch over all degrees per chunk budget
+ * present in TCM_MIXED, one per degree in TCM_FP64 --, finalisation, contraction) is captured into a graph and replayed by
  * later calls with the same launch shapes and buffers (item count, job and tile counts,
  * output pointers); the descriptors are uploaded per call, so the orientations, pairs and
  * systems may change.  mode 0: launch kernel by kernel; mode 1 (default): capture a shape

@@ -1,15 +1,19 @@
 """Autotuner of the moment pass (steps a2/a3): per degree L and precision it chooses the warp-tile
-size (atoms per lane) and the persistent grid's CTAs per SM by timing the caller's own batch.
+size (atoms per lane), the persistent grid's CTAs per SM and, for the mixed path, the
+L-chunking (the float kernel's accumulator budget kmax: 160 or 96 per lane, which sets how many
+column chunks the (L+1)^2 components take and how many CTAs fit on an SM) by timing the
+caller's own batch.
 
 For every degree present in the batch, the items of that degree (at most ``max_items_per_l`` of
-them) form a sub-batch; each candidate setting is applied with ``tcm_ctx_set_tiling_l``, the
-sub-batch is run once untimed and ``reps`` times timed, and the median time of the moment phase
-(the library's CUDA-event phase profile: the moment kernels of that degree, nothing else) is
-kept.  The fastest candidate is applied to the context and returned.  Results can be saved to a
-JSON file keyed by device name, library build and precision, and loaded into a later context.
+them) form a sub-batch; each candidate setting (atoms per lane, CTAs per SM, kmax) is applied
+with ``tcm_ctx_set_tiling_l`` and ``tcm_ctx_set_chunking_l``, the sub-batch is run once untimed
+and ``reps`` times timed, and the median time of the moment phase (the library's CUDA-event
+phase profile: the moment kernels of that degree, nothing else) is kept.  The fastest candidate
+is applied to the context and returned.  Results can be saved to a JSON file keyed by device
+name, library build and precision, and loaded into a later context.
 
-The tiling changes only the order in which atom contributions are summed, so every candidate
-gives results within the stated tolerances; the choice is made on time alone.
+The tiling and the chunking change only the order in which atom contributions are summed, so
+every candidate gives results within the stated tolerances; the choice is made on time alone.
 """
 from __future__ import annotations
 
@@ -21,24 +25,58 @@ from dataclasses import dataclass, field
 import numpy as np
 
 DEFAULT_ATOMS_PER_LANE = (16, 32, 48, 64, 96, 128, 256)
-DEFAULT_CTAS_PER_SM = (1, 2)
+DEFAULT_CTAS_PER_SM = (1, 2, 3)
+DEFAULT_KMAX = (160, 96)  # the mixed path's chunk budgets (tcm_ctx_set_chunking_l)
+FP64_KMAX = 80            # the double kernels' budget (fixed)
+
+
+def ctas_limit(precision, kmax):
+    """CTAs per SM the moment kernel of that precision and budget is compiled for."""
+    from . import tcm
+    if precision == tcm.TCM_FP64:
+        return 2
+    return 3 if kmax <= 96 else 2
+
+
+def candidates(precision, atoms_per_lane=DEFAULT_ATOMS_PER_LANE, ctas_per_sm=DEFAULT_CTAS_PER_SM,
+               kmax=DEFAULT_KMAX):
+    """Every (atoms_per_lane, ctas_per_sm, kmax) the tuner times, in timing order."""
+    from . import tcm
+    kms = (FP64_KMAX,) if precision == tcm.TCM_FP64 else tuple(kmax)
+    return [(a, c, k) for k in kms for a in atoms_per_lane for c in ctas_per_sm if c <= ctas_limit(precision, k)]
+
+
+def get_setting(ctx, precision, L):
+    from . import tcm
+    apl, cps = ctx.tcm_ctx_get_tiling_l(precision, L)
+    km = FP64_KMAX if precision == tcm.TCM_FP64 else ctx.tcm_ctx_get_chunking_l(L)[0]
+    return (apl, cps, km)
+
+
+def set_setting(ctx, precision, L, setting):
+    from . import tcm
+    apl, cps, km = setting
+    ctx.tcm_ctx_set_tiling_l(precision, L, apl, cps)
+    if precision != tcm.TCM_FP64:
+        ctx.tcm_ctx_set_chunking_l(L, km)
 
 
 @dataclass
 class TuneResult:
     precision: int
-    best: dict = field(default_factory=dict)     # L -> (atoms_per_lane, ctas_per_sm)
-    timings: dict = field(default_factory=dict)  # L -> {(atoms_per_lane, ctas_per_sm): median ms}
+    best: dict = field(default_factory=dict)     # L -> (atoms_per_lane, ctas_per_sm, kmax)
+    timings: dict = field(default_factory=dict)  # L -> {(atoms_per_lane, ctas_per_sm, kmax): median ms}
 
     def to_json(self):
         return {"precision": int(self.precision),
                 "best": {str(L): list(v) for L, v in self.best.items()},
-                "timings": {str(L): {f"{a}x{c}": ms for (a, c), ms in t.items()} for L, t in self.timings.items()}}
+                "timings": {str(L): {"x".join(str(x) for x in c): ms for c, ms in t.items()}
+                            for L, t in self.timings.items()}}
 
     @classmethod
     def from_json(cls, d):
         r = cls(int(d["precision"]))
-        r.best = {int(L): (int(v[0]), int(v[1])) for L, v in d["best"].items()}
+        r.best = {int(L): tuple(int(x) for x in v) for L, v in d["best"].items()}
         r.timings = {int(L): {tuple(int(x) for x in k.split("x")): float(ms) for k, ms in t.items()}
                      for L, t in d.get("timings", {}).items()}
         return r
@@ -80,7 +118,8 @@ def moment_phase_ms(ctx, run, reps):
 
 
 def tune(ctx, systems, a, b, lmax, R0, rotB=None, precision=None, atoms_per_lane=DEFAULT_ATOMS_PER_LANE,
-         ctas_per_sm=DEFAULT_CTAS_PER_SM, reps=3, max_items_per_l=512, measure=None) -> TuneResult:
+         ctas_per_sm=DEFAULT_CTAS_PER_SM, kmax=DEFAULT_KMAX, reps=3, max_items_per_l=512,
+         measure=None) -> TuneResult:
     """Tune the moment pass on this batch (arguments as for ``Context.tcm_energy_batch``).
 
     ``measure(L, run) -> ms`` replaces the CUDA-event measurement (used by the host-side tests).
@@ -99,22 +138,21 @@ def tune(ctx, systems, a, b, lmax, R0, rotB=None, precision=None, atoms_per_lane
         def run(pb=pb):
             ctx.tcm_energy_batch_packed(pb, precision)
 
-        default = ctx.tcm_ctx_get_tiling_l(precision, L)
+        default = get_setting(ctx, precision, L)
         t = {}
-        for apl in atoms_per_lane:
-            for cps in ctas_per_sm:
-                ctx.tcm_ctx_set_tiling_l(precision, L, apl, cps)
-                t[(apl, cps)] = measure(L, run) if measure else moment_phase_ms(ctx, run, reps)
+        for cand in candidates(precision, atoms_per_lane, ctas_per_sm, kmax):
+            set_setting(ctx, precision, L, cand)
+            t[cand] = measure(L, run) if measure else moment_phase_ms(ctx, run, reps)
         best = choose(t) or default
-        ctx.tcm_ctx_set_tiling_l(precision, L, *best)
+        set_setting(ctx, precision, L, best)
         res.best[L] = best
         res.timings[L] = t
     return res
 
 
 def apply(ctx, result: TuneResult):
-    for L, (apl, cps) in result.best.items():
-        ctx.tcm_ctx_set_tiling_l(result.precision, L, apl, cps)
+    for L, setting in result.best.items():
+        set_setting(ctx, result.precision, L, setting)
 
 
 def library_key(lib_path=None, device_name=None):

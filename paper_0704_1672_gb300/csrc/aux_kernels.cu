@@ -100,15 +100,18 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const MomJob* __r
                                                                const SysGeom* __restrict__ geoms,
                                                                const int* __restrict__ imap,
                                                                const double* __restrict__ fmap,
-                                                               const int* __restrict__ imap_off, int kmax,
+                                                               const int* __restrict__ imap_off,
                                                                const double* __restrict__ syspart) {
   __shared__ double s_low[kLowSums];
-  pdl_wait();  // the moment kernels' partial rows are complete
+  pdl_trigger();  // the contraction may be scheduled; it waits for this grid before reading
+  pdl_wait();     // the moment kernels' partial rows are complete
   const MomJob& job = jobs[blockIdx.x];
   const int L = job.L;
   const int tpc = job.tiles_per_chunk;
-  const int o = imap_off[L];
-  const int nq = imap_off[L + 1] - o;  // nch x kmax
+  const int kmax = plan_kmax(job.plan), row = plan_row(job.plan);
+  const int* off = imap_off + job.plan * (kLmaxMax + 2);
+  const int o = off[L];
+  const int nq = off[L + 1] - o;  // nch x kmax
   const double a = geoms[job.geom].a;
   int e = 0;  // a' = scale_radius(a) = 2^e
   if (a > 0.0) frexp(a, &e);
@@ -116,10 +119,10 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const MomJob* __r
     const int p = imap[o + q];
     const double f = fmap[o + q];
     const int ch = q / kmax, slot = q - ch * kmax;
-    const double* base = partials + (long long)(job.tile_base + ch * tpc) * kmax + slot;
+    const double* base = partials + (long long)(job.tile_base + ch * tpc) * row + slot;
     double s = 0.0;
 #pragma unroll 8
-    for (int t = 0; t < tpc; ++t) s += __ldcg(base + (long long)t * kmax);  // loads issued ahead of the adds
+    for (int t = 0; t < tpc; ++t) s += __ldcg(base + (long long)t * row);  // loads issued ahead of the adds
     if (p < 0) continue;
     int l = (int)sqrtf((float)p);
     while (l * l > p) --l;
@@ -294,24 +297,6 @@ __device__ __forceinline__ double2 rot_second(const double* Ds, const double2* p
   return q;
 }
 
-// Sum of N values over the block; thread 0 gets the totals in v.  sh holds N * 32 doubles.
-template <int N>
-__device__ void block_sum_n(double (&v)[N], double* sh) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const double t = warp_sum(v[k]);
-    if (lane == 0) sh[k * 32 + w] = t;
-  }
-  __syncthreads();
-  if (w == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = warp_sum(lane < nw ? sh[k * 32 + lane] : 0.0);
-  }
-  __syncthreads();
-}
-
 // Eq. (Formula) for one (pair, orientation) per CTA, in the frame where R0hat = z.  With kGrad
 // it also writes, per item, the force on B (-grad_R0 E) and the torques on A and on B about
 // their centres, from the same frame moments:
@@ -335,7 +320,9 @@ __global__ void __launch_bounds__(kContractThreads, kGrad ? 1 : 2) k_contract(co
                                                                double* __restrict__ E, int32_t* __restrict__ status,
                                                                double* __restrict__ G) {
   extern __shared__ double2 sm2[];
-  __shared__ double sh[(kGrad ? 9 : 1) * 32];
+  constexpr int kVWarps = kContractThreads / 32;
+  __shared__ double she[kContractThreads];           // the virtual lanes' energy sums
+  __shared__ double shv[(kGrad ? 8 : 1) * kVWarps];  // the virtual warps' gradient sums
   __shared__ int g_conv;
   const PairDesc d = items[blockIdx.x];  // descriptors and tables precede the kernels before
   const int L = d.L;
@@ -354,28 +341,13 @@ __global__ void __launch_bounds__(kContractThreads, kGrad ? 1 : 2) k_contract(co
   double* c2t = rp + 2 * L + 2;                       // 2 n! R^-(n+1), n <= 2L
   double* hb0 = c2t + 2 * L + 1;                      // Qhat'^B_l0 / 2
   double* Ds = hb0 + L + 1;                           // rows of D^l, l <= L
+  // Before griddepcontrol.wait: everything that depends only on the descriptors and tables the
+  // host uploaded ahead of the kernels (the d^l(pi/2) rows, the phase and power tables of the
+  // frame, the moment sets' addresses), so it overlaps the tail of the kernel before.
   load_dpi2(Ds, ztab, L);
-  pdl_wait();  // the moments (and centres and radii) of the launches before are complete
+  const int bmode = d.b_mode;
   const double* pa = jobs[d.jobA].out;
   const double* pb = jobs[d.jobB].out;
-  const int bmode = d.b_mode;
-  // the frame's angles and R come with the descriptor; the radii from the kernels before
-  if (threadIdx.x == 0) g_conv = d.fr[1] > geoms[d.geomA].a + geoms[d.geomB].a;  // Eq. (mainCond)
-  for (int k = threadIdx.x; k < nq; k += blockDim.x) {
-    const int l = tri_l(k);
-    const int m = k - l * (l + 1) / 2;
-    qa[k] = m == 0 ? make_double2(pa[l * l], 0.0) : make_double2(pa[l * l + 2 * m - 1], pa[l * l + 2 * m]);
-    qb[k] = m == 0 ? make_double2(pb[l * l], 0.0) : make_double2(pb[l * l + 2 * m - 1], pb[l * l + 2 * m]);
-  }
-  __syncthreads();
-  if (!g_conv) {  // the expansion does not converge: NaN and a status instead of an energy
-    if (threadIdx.x == 0) {
-      E[blockIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
-      if (status) status[blockIdx.x] = TCM_ENOTCONV;
-    }
-    if (kGrad && threadIdx.x < 9) G[9LL * blockIdx.x + threadIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
-    return;
-  }
   {  // the phase tables and R^-(k+1) (k <= 2L + 1 <= 49), one warp per table (warp-uniform tasks)
     const int lane = threadIdx.x & 31;
     const int ntask = bmode == kBRotate ? 7 : 4;
@@ -402,23 +374,36 @@ __global__ void __launch_bounds__(kContractThreads, kGrad ? 1 : 2) k_contract(co
     }
   }
   __syncthreads();
+  for (int n = threadIdx.x; n <= 2 * L; n += blockDim.x) c2t[n] = ztab[kZ_FACT2 + n] * rp[n];
+  pdl_wait();  // the moments (and centres and radii) of the launches before are complete
+  // the radii come from the kernels before
+  if (threadIdx.x == 0) g_conv = d.fr[1] > geoms[d.geomA].a + geoms[d.geomB].a;  // Eq. (mainCond)
   // v~ = input phases times the moments of the sides rotated here; mode kBInFrame scales B to Qhat
   for (int k = threadIdx.x; k < nq; k += blockDim.x) {
     const int l = tri_l(k);
     const int m = k - l * (l + 1) / 2;
-    qa[k] = cmul(ph[m], qa[k]);
+    const double2 a = m == 0 ? make_double2(pa[l * l], 0.0) : make_double2(pa[l * l + 2 * m - 1], pa[l * l + 2 * m]);
+    const double2 b = m == 0 ? make_double2(pb[l * l], 0.0) : make_double2(pb[l * l + 2 * m - 1], pb[l * l + 2 * m]);
+    qa[k] = cmul(ph[m], a);
     if (bmode == kBLab) {
-      qb[k] = cmul(ph[m], qb[k]);
+      qb[k] = cmul(ph[m], b);
     } else if (bmode == kBRotate) {
-      qb[k] = cmul(pha[m], qb[k]);
+      qb[k] = cmul(pha[m], b);
     } else {
       const double f = ztab[kZ_ISF + l * kZN + m];
-      qb[k] = make_double2(qb[k].x * f, qb[k].y * f);
+      qb[k] = make_double2(b.x * f, b.y * f);
       if (m == 0) hb0[l] = 0.5 * qb[k].x;
     }
   }
-  for (int n = threadIdx.x; n <= 2 * L; n += blockDim.x) c2t[n] = ztab[kZ_FACT2 + n] * rp[n];
   __syncthreads();
+  if (!g_conv) {  // the expansion does not converge: NaN and a status instead of an energy
+    if (threadIdx.x == 0) {
+      E[blockIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
+      if (status) status[blockIdx.x] = TCM_ENOTCONV;
+    }
+    if (kGrad && threadIdx.x < 9) G[9LL * blockIdx.x + threadIdx.x] = __longlong_as_double(0x7ff8000000000000LL);
+    return;
+  }
   const int nrot = bmode == kBInFrame ? 1 : 2;
   for (int it = threadIdx.x; it < nrot * nq; it += blockDim.x) {
     const int side = it >= nq;
@@ -446,84 +431,112 @@ __global__ void __launch_bounds__(kContractThreads, kGrad ? 1 : 2) k_contract(co
   // s = min(l1, l2), s = L first: the (L - s)^2 pairs before shell s are those of the larger
   // shells, and shell s lists (s, s), (s, s+1), (s+1, s), (s, s+2), ...  Neighbouring lanes then
   // run the m loops (s terms) to nearly the same length.
-  double acc = 0.0;
-  double gx = 0.0, gy = 0.0, gz = 0.0, tbx = 0.0, tby = 0.0, tbz = 0.0, tax = 0.0, tay = 0.0;
-  for (int p = threadIdx.x; p < (L + 1) * (L + 1); p += blockDim.x) {
-    int u = (int)sqrtf((float)p);  // u = L - s = floor(sqrt(p))
-    while (u * u > p) --u;
-    while ((u + 1) * (u + 1) <= p) ++u;
-    const int sh_s = L - u, j = p - u * u;
-    const int l1 = (j & 1) ? sh_s : sh_s + (j >> 1);
-    const int l2 = (j & 1) ? sh_s + ((j + 1) >> 1) : sh_s;
-    const double2* a = ra + l1 * (l1 + 1) / 2;
-    const double2* b = rb + l2 * (l2 + 1) / 2;
-    const int mm = l1 < l2 ? l1 : l2;
-    // even and odd m: with the m = 0 term at half weight, s / 2 = a_0 b_0 / 2 + sum_{m>=1} (-1)^m
-    // Re(a_m conj b_m) = se - so, and the factor 2 sits in the table c2t
-    double se = a[0].x * hb0[l2], so = 0.0;
-    int m = 1;
-    for (; m + 1 <= mm; m += 2) {
-      so = fma(a[m].x, b[m].x, so);
-      so = fma(a[m].y, b[m].y, so);
-      se = fma(a[m + 1].x, b[m + 1].x, se);
-      se = fma(a[m + 1].y, b[m + 1].y, se);
+  //
+  // The energy's summation order does not depend on the CTA size (which the launch picks from
+  // the batch): pair p belongs to virtual lane p mod kContractThreads, each virtual lane adds its
+  // pairs in increasing p, lane c of one warp adds virtual lanes c, c + 32, ... in order, and a
+  // fixed shuffle tree adds the 32 lanes.  A CTA of nt threads runs virtual lanes t, t + nt, ...
+  // one after the other, so an item's energy is the same in any batch.  (The sequential sums keep
+  // the FP64 instructions of the reduction to about a tenth of a shuffle tree per warp.)  The
+  // gradient sums take a shuffle tree per virtual warp of 32 lanes, then one over those.
+  const int n_pairs = (L + 1) * (L + 1);
+  for (int v = threadIdx.x; v < kContractThreads; v += blockDim.x) {  // block-uniform trip count
+    double acc = 0.0;
+    double gx = 0.0, gy = 0.0, gz = 0.0, tbx = 0.0, tby = 0.0, tbz = 0.0, tax = 0.0, tay = 0.0;
+    for (int p = v; p < n_pairs; p += kContractThreads) {
+      int u = (int)sqrtf((float)p);  // u = L - s = floor(sqrt(p))
+      while (u * u > p) --u;
+      while ((u + 1) * (u + 1) <= p) ++u;
+      const int sh_s = L - u, j = p - u * u;
+      const int l1 = (j & 1) ? sh_s : sh_s + (j >> 1);
+      const int l2 = (j & 1) ? sh_s + ((j + 1) >> 1) : sh_s;
+      const double2* a = ra + l1 * (l1 + 1) / 2;
+      const double2* b = rb + l2 * (l2 + 1) / 2;
+      const int mm = l1 < l2 ? l1 : l2;
+      // even and odd m: with the m = 0 term at half weight, s / 2 = a_0 b_0 / 2 + sum_{m>=1} (-1)^m
+      // Re(a_m conj b_m) = se - so, and the factor 2 sits in the table c2t
+      double se = a[0].x * hb0[l2], so = 0.0;
+      int m = 1;
+      for (; m + 1 <= mm; m += 2) {
+        so = fma(a[m].x, b[m].x, so);
+        so = fma(a[m].y, b[m].y, so);
+        se = fma(a[m + 1].x, b[m + 1].x, se);
+        se = fma(a[m + 1].y, b[m + 1].y, se);
+      }
+      if (m <= mm) {
+        so = fma(a[m].x, b[m].x, so);
+        so = fma(a[m].y, b[m].y, so);
+      }
+      const double h = se - so;
+      acc = fma(flip(c2t[l1 + l2], l2), h, acc);
+      if (kGrad) {
+        const double s = h + h;
+        const double c = flip(ztab[kZ_FACT + l1 + l2] * rp[l1 + l2], l2);
+        // S+ and P: pairs (m1, m2) = (m, 1 - m), m >= 1, and (-m, m + 1), m >= 0
+        double spr = 0.0, spi = 0.0, pr = 0.0, pi = 0.0, z = 0.0;
+        const int m1a = l1 < l2 + 1 ? l1 : l2 + 1;
+        for (int m = 1; m <= m1a; ++m) {  // (-1)^(m-1) a_m conj(b_(m-1)), weight l2 + 1 - m
+          const double2 x = a[m], y = b[m - 1];
+          const double re = flip(fma(x.x, y.x, x.y * y.y), m - 1);
+          const double im = flip(fma(x.y, y.x, -(x.x * y.y)), m - 1);
+          const double w = (double)(l2 + 1 - m);
+          spr += re;
+          spi += im;
+          pr = fma(w, re, pr);
+          pi = fma(w, im, pi);
+        }
+        const int m1b = l1 < l2 - 1 ? l1 : l2 - 1;
+        for (int m = 0; m <= m1b; ++m) {  // (-1)^m conj(a_m) b_(m+1), weight l2 + 1 + m
+          const double2 x = a[m], y = b[m + 1];
+          const double re = flip(fma(x.x, y.x, x.y * y.y), m);
+          const double im = flip(fma(x.x, y.y, -(x.y * y.x)), m);
+          const double w = (double)(l2 + 1 + m);
+          spr += re;
+          spi += im;
+          pr = fma(w, re, pr);
+          pi = fma(w, im, pi);
+        }
+        for (int m = 1; m <= mm; ++m) z += flip((double)(2 * m) * fma(a[m].y, b[m].x, -(a[m].x * b[m].y)), m);
+        const double c1 = flip(ztab[kZ_FACT + l1 + l2 + 1] * rp[l1 + l2 + 1], l2);
+        const double L1 = (double)(l1 + l2 + 1);
+        gx = fma(-c1, spr, gx);
+        gy = fma(-c1, spi, gy);
+        gz = fma(-c1, s, gz);
+        tbx = fma(c, pi, tbx);
+        tby = fma(-c, pr, tby);
+        tbz = fma(-c, z, tbz);
+        tax = fma(c, fma(L1, spi, -pi), tax);
+        tay = fma(-c, fma(L1, spr, -pr), tay);
+      }
     }
-    if (m <= mm) {
-      so = fma(a[m].x, b[m].x, so);
-      so = fma(a[m].y, b[m].y, so);
-    }
-    const double h = se - so;
-    acc = fma(flip(c2t[l1 + l2], l2), h, acc);
+    she[v] = acc;
     if (kGrad) {
-      const double s = h + h;
-      const double c = flip(ztab[kZ_FACT + l1 + l2] * rp[l1 + l2], l2);
-      // S+ and P: pairs (m1, m2) = (m, 1 - m), m >= 1, and (-m, m + 1), m >= 0
-      double spr = 0.0, spi = 0.0, pr = 0.0, pi = 0.0, z = 0.0;
-      const int m1a = l1 < l2 + 1 ? l1 : l2 + 1;
-      for (int m = 1; m <= m1a; ++m) {  // (-1)^(m-1) a_m conj(b_(m-1)), weight l2 + 1 - m
-        const double2 x = a[m], y = b[m - 1];
-        const double re = flip(fma(x.x, y.x, x.y * y.y), m - 1);
-        const double im = flip(fma(x.y, y.x, -(x.x * y.y)), m - 1);
-        const double w = (double)(l2 + 1 - m);
-        spr += re;
-        spi += im;
-        pr = fma(w, re, pr);
-        pi = fma(w, im, pi);
+      double w[8] = {gx, gy, gz, tbx, tby, tbz, tax, tay};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        w[k] = warp_sum(w[k]);
+        if ((threadIdx.x & 31) == 0) shv[k * kVWarps + (v >> 5)] = w[k];
       }
-      const int m1b = l1 < l2 - 1 ? l1 : l2 - 1;
-      for (int m = 0; m <= m1b; ++m) {  // (-1)^m conj(a_m) b_(m+1), weight l2 + 1 + m
-        const double2 x = a[m], y = b[m + 1];
-        const double re = flip(fma(x.x, y.x, x.y * y.y), m);
-        const double im = flip(fma(x.x, y.y, -(x.y * y.x)), m);
-        const double w = (double)(l2 + 1 + m);
-        spr += re;
-        spi += im;
-        pr = fma(w, re, pr);
-        pi = fma(w, im, pi);
-      }
-      for (int m = 1; m <= mm; ++m) z += flip((double)(2 * m) * fma(a[m].y, b[m].x, -(a[m].x * b[m].y)), m);
-      const double c1 = flip(ztab[kZ_FACT + l1 + l2 + 1] * rp[l1 + l2 + 1], l2);
-      const double L1 = (double)(l1 + l2 + 1);
-      gx = fma(-c1, spr, gx);
-      gy = fma(-c1, spi, gy);
-      gz = fma(-c1, s, gz);
-      tbx = fma(c, pi, tbx);
-      tby = fma(-c, pr, tby);
-      tbz = fma(-c, z, tbz);
-      tax = fma(c, fma(L1, spi, -pi), tax);
-      tay = fma(-c, fma(L1, spr, -pr), tay);
     }
   }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  double e_sum = she[lane];
+#pragma unroll
+  for (int c = 1; c < kVWarps; ++c) e_sum += she[c * 32 + lane];
+  e_sum = warp_sum(e_sum);  // valid in lane 0
   if (!kGrad) {
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) {
-      E[blockIdx.x] = acc;
+    if (lane == 0) {
+      E[blockIdx.x] = e_sum;
       if (status) status[blockIdx.x] = TCM_OK;
     }
   } else {
-    double v[9] = {acc, gx, gy, gz, tbx, tby, tbz, tax, tay};
-    block_sum_n<9>(v, sh);
-    if (threadIdx.x == 0) {
+    double w[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) w[k] = warp_sum(lane < kVWarps ? shv[k * kVWarps + lane] : 0.0);
+    if (lane == 0) {
+      const double v[9] = {e_sum, w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7]};
       E[blockIdx.x] = v[0];
       if (status) status[blockIdx.x] = TCM_OK;
       const double cb = d.fr[2], sb = d.fr[3], ca = d.fr[4], sa = d.fr[5];
@@ -702,10 +715,10 @@ int launch_rotate_moments(const RotDesc* sets, int n_sets, int Lmax_sets, const 
 }
 
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms, const int* imap,
-                    const double* fmap, const int* imap_off, int kmax, const double* syspart, cudaStream_t s) {
+                    const double* fmap, const int* imap_off, const double* syspart, cudaStream_t s) {
   if (n_jobs <= 0) return 0;
   return launch_pdl(k_finalize, dim3(n_jobs), dim3(kFinalizeThreads), 0, s, jobs, partials, geoms, imap, fmap,
-                    imap_off, kmax, syspart) == cudaSuccess
+                    imap_off, syspart) == cudaSuccess
              ? 0
              : -1;
 }

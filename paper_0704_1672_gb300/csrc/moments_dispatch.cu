@@ -11,7 +11,7 @@
 namespace tcm {
 
 // Defined (and explicitly instantiated) in moments_kernel.cuh / moments_*.cu.
-template <typename T, int L>
+template <typename T, int L, int KM>
 int launch_moments_t(const MomJob* jobs, const MomTile* tiles, int n_tiles, int* counter, const SysGeom* geoms,
                      double* partials, int grid, cudaStream_t s);
 
@@ -21,27 +21,22 @@ using LaunchFn = int (*)(const MomJob*, const MomTile*, int, int*, const SysGeom
 
 template <typename T, int... Ls>
 constexpr auto make_table(std::integer_sequence<int, Ls...>) {
-  return std::array<LaunchFn, sizeof...(Ls)>{{&launch_moments_t<T, Ls>...}};
+  return std::array<LaunchFn, sizeof...(Ls)>{{&launch_moments_t<T, Ls, kKmaxF64>...}};
 }
 
 const auto kF64 = make_table<double>(std::make_integer_sequence<int, kLmaxMax + 1>{});
 
-constexpr int stride_of(int precision) { return precision == TCM_FP64 ? 34 : 36; }
-constexpr int size_of(int precision) { return precision == TCM_FP64 ? 8 : 4; }
-
 }  // namespace
 
-int moments_kmax(int precision) { return precision == TCM_FP64 ? kKmaxF64 : kKmaxF32; }
-
 namespace {
-// The chunk plans of both precisions, tabulated once (plan_nch and plan_m0 are loops meant for
-// compile time; the host planning of a batch asks for them per job and per group).
+// The chunk plans, tabulated once (plan_nch and plan_m0 are loops meant for compile time; the
+// host planning of a batch asks for them per job and per group).
 struct ChunkTables {
-  int nch[2][kLmaxMax + 1];
-  int m0[2][kLmaxMax + 1][kLmaxMax + 2];
+  int nch[kNumPlans][kLmaxMax + 1];
+  int m0[kNumPlans][kLmaxMax + 1][kLmaxMax + 2];
   ChunkTables() {
-    for (int pi = 0; pi < 2; ++pi) {
-      const int kmax = pi == 0 ? kKmaxF64 : kKmaxF32;
+    for (int pi = 0; pi < kNumPlans; ++pi) {
+      const int kmax = plan_kmax(pi);
       for (int L = 0; L <= kLmaxMax; ++L) {
         nch[pi][L] = plan_nch(L, kmax);
         for (int c = 0; c <= nch[pi][L]; ++c) m0[pi][L][c] = plan_m0(L, kmax, nch[pi][L], c);
@@ -55,21 +50,9 @@ const ChunkTables& chunk_tables() {
 }
 }  // namespace
 
-int moments_nchunks(int precision, int L) { return chunk_tables().nch[precision == TCM_FP64 ? 0 : 1][L]; }
+int moments_nchunks(int plan, int L) { return chunk_tables().nch[plan][L]; }
 
-int moments_chunk_m0(int precision, int L, int chunk) { return chunk_tables().m0[precision == TCM_FP64 ? 0 : 1][L][chunk]; }
-
-int moments_smem_bytes(int precision, int L) {
-  const int kmax = moments_kmax(precision);
-  if (precision != TCM_FP64) return (kThreads / 32) * kmax * stride_of(precision) * size_of(precision);  // any degree
-  const int nch = plan_nch(L, kmax);
-  int mx = 0;
-  for (int c = 0; c < nch; ++c) {
-    const int n = chunk_off(L, plan_m0(L, kmax, nch, c), plan_m0(L, kmax, nch, c + 1));
-    mx = n > mx ? n : mx;
-  }
-  return (kThreads / 32) * mx * stride_of(precision) * size_of(precision);
-}
+int moments_chunk_m0(int plan, int L, int chunk) { return chunk_tables().m0[plan][L][chunk]; }
 
 void finalize_tables(std::vector<int>& imap_off, std::vector<int>& imap, std::vector<double>& fmap) {
   const int N = kLmaxMax + 1;
@@ -97,10 +80,10 @@ void finalize_tables(std::vector<int>& imap_off, std::vector<int>& imap, std::ve
       ftab[l * N + m] = (double)(sgn * std::sqrt(fact[l - m] / fact[l + m]) * s);
     }
   }
-  imap_off.assign(2 * (N + 1), 0);
+  imap_off.assign(kNumPlans * (N + 1), 0);
   imap.clear();
-  for (int pi = 0; pi < 2; ++pi) {
-    const int kmax = moments_kmax(pi == 0 ? TCM_FP64 : TCM_MIXED);
+  for (int pi = 0; pi < kNumPlans; ++pi) {
+    const int kmax = plan_kmax(pi);
     for (int L = 0; L < N; ++L) {
       const int nch = plan_nch(L, kmax);
       const size_t base = imap.size();
@@ -131,12 +114,15 @@ void finalize_tables(std::vector<int>& imap_off, std::vector<int>& imap, std::ve
   }
 }
 
-int launch_moments(int precision, int L, const MomJob* jobs, const MomTile* tiles, int n_tiles, int* counter,
+int launch_moments(int plan, int L, const MomJob* jobs, const MomTile* tiles, int n_tiles, int* counter,
                    const SysGeom* geoms, double* partials, int grid, cudaStream_t s) {
-  if (L < 0 || L > kLmaxMax || n_tiles <= 0) return n_tiles == 0 ? 0 : -1;
-  if (precision != TCM_FP64)  // the float kernel takes tiles of any degree
-    return launch_moments_t<float, -1>(jobs, tiles, n_tiles, counter, geoms, partials, grid, s);
-  return kF64[L](jobs, tiles, n_tiles, counter, geoms, partials, grid, s);
+  if (n_tiles <= 0) return n_tiles == 0 ? 0 : -1;
+  switch (plan) {  // the float kernels take tiles of any degree
+    case 1: return launch_moments_t<float, -1, kKmaxF32>(jobs, tiles, n_tiles, counter, geoms, partials, grid, s);
+    case 2: return launch_moments_t<float, -1, kKmaxF32Small>(jobs, tiles, n_tiles, counter, geoms, partials, grid, s);
+    case 0: return L < 0 || L > kLmaxMax ? -1 : kF64[L](jobs, tiles, n_tiles, counter, geoms, partials, grid, s);
+    default: return -1;
+  }
 }
 
 namespace {
@@ -168,12 +154,6 @@ int launch_expand_tiles(const MomGroup* groups, int n_groups, const MomJob* jobs
   if (n <= 0) return 0;
   k_expand_tiles<<<(n + 7) / 8, 256, 0, s>>>(groups, n_groups, jobs, tiles, sjobs, n_sjobs, t1, t2);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
-}
-
-int launch_moments_any(const MomJob* jobs, const MomTile* tiles, int n_tiles, int* counter, const SysGeom* geoms,
-                       double* partials, int grid, cudaStream_t s) {
-  if (n_tiles <= 0) return 0;
-  return launch_moments_t<float, -1>(jobs, tiles, n_tiles, counter, geoms, partials, grid, s);
 }
 
 }  // namespace tcm

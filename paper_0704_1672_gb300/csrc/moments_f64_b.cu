@@ -3,10 +3,10 @@
 #include "moments_kernel.cuh"
 
 namespace tcm {
-template int launch_moments_t<double, 14>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
-template int launch_moments_t<double, 15>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
-template int launch_moments_t<double, 16>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
-template int launch_moments_t<double, 17>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
-template int launch_moments_t<double, 18>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
-template int launch_moments_t<double, 19>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 14, kKmaxF64>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 15, kKmaxF64>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 16, kKmaxF64>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 17, kKmaxF64>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 18, kKmaxF64>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 19, kKmaxF64>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
 }  // namespace tcm

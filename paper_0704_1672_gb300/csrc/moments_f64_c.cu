@@ -3,7 +3,7 @@
 #include "moments_kernel.cuh"
 
 namespace tcm {
-template int launch_moments_t<double, 20>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
-template int launch_moments_t<double, 21>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
-template int launch_moments_t<double, 22>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 20, kKmaxF64>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 21, kKmaxF64>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 22, kKmaxF64>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
 }  // namespace tcm

@@ -3,6 +3,6 @@
 #include "moments_kernel.cuh"
 
 namespace tcm {
-template int launch_moments_t<double, 23>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
-template int launch_moments_t<double, 24>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 23, kKmaxF64>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
+template int launch_moments_t<double, 24, kKmaxF64>(const MomJob*, const MomTile*, int, int*, const SysGeom*, double*, int, cudaStream_t);
 }  // namespace tcm

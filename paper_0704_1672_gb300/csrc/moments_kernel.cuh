@@ -23,12 +23,14 @@ template <typename T>
 struct MomTraits;
 template <>
 struct MomTraits<float> {
-  static constexpr int kmax = kKmaxF32;
+  static constexpr int kmax = kKmaxF32;  // the largest budget (plan 1)
+  static constexpr int row = kKmaxF32;   // partial-row stride of every float plan
   static constexpr int stride = 36;  // row stride (floats) of the transpose buffer: 16-B rows, no LDS.128 conflicts
 };
 template <>
 struct MomTraits<double> {
   static constexpr int kmax = kKmaxF64;
+  static constexpr int row = kKmaxF64;
   static constexpr int stride = 34;  // doubles
 };
 
@@ -37,9 +39,9 @@ __device__ __forceinline__ double fmaT(double a, double b, double c) { return __
 __device__ __forceinline__ float rsqrtT(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrtT(double x) { return rsqrt(x); }
 
-template <typename T, int L>
+template <typename T, int L, int KM = MomTraits<T>::kmax>
 struct Plan {
-  static constexpr int kmax = MomTraits<T>::kmax;
+  static constexpr int kmax = KM;
   static constexpr int nch = plan_nch(L, kmax);
   __host__ __device__ static constexpr int m0(int c) { return plan_m0(L, kmax, nch, c); }
   __host__ __device__ static constexpr int nacc(int c) { return chunk_off(L, m0(c), m0(c + 1)); }
@@ -484,32 +486,32 @@ __device__ __forceinline__ void run_chunk(const MomTile& tile, const MomJob* __r
     atom_loop<T, L, M0, M1>(s, reinterpret_cast<const float4*>(xyzq), i0, i1, xf, g.c);
   else
     atom_loop<T, L, M0, M1>(s, reinterpret_cast<const Rec64*>(xyzq), i0, i1, xf, g.c);
-  warp_reduce_store<T, L, M0, M1>(s, wb, partials + (long long)tile.id * Plan<T, L>::kmax);
+  warp_reduce_store<T, L, M0, M1>(s, wb, partials + (long long)tile.id * MomTraits<T>::row);
 }
 
-template <typename T, int L, int C>
+template <typename T, int L, int C, int KM>
 __device__ __forceinline__ void run_tile(const MomTile& tile, const MomJob* __restrict__ jobs,
                                          const SysGeom* __restrict__ geoms, double* __restrict__ partials, T* wb,
                                          Xform<T>* xf_w) {
-  using P = Plan<T, L>;
+  using P = Plan<T, L, KM>;
   if constexpr (C < P::nch) {
     if (tile.chunk == C)
       run_chunk<T, L, P::m0(C), P::m0(C + 1)>(tile, jobs, geoms, partials, wb, xf_w);
     else
-      run_tile<T, L, C + 1>(tile, jobs, geoms, partials, wb, xf_w);
+      run_tile<T, L, C + 1, KM>(tile, jobs, geoms, partials, wb, xf_w);
   }
 }
 
 // Code of the tile's own degree: a chain of compile-time degrees, one compare per degree.
-template <typename T, int L>
+template <typename T, int L, int KM>
 __device__ __forceinline__ void run_tile_any(int Lt, const MomTile& tile, const MomJob* __restrict__ jobs,
                                              const SysGeom* __restrict__ geoms, double* __restrict__ partials, T* wb,
                                              Xform<T>* xf_w) {
   if constexpr (L <= kLmaxMax) {
     if (Lt == L)
-      run_tile<T, L, 0>(tile, jobs, geoms, partials, wb, xf_w);
+      run_tile<T, L, 0, KM>(tile, jobs, geoms, partials, wb, xf_w);
     else
-      run_tile_any<T, L + 1>(Lt, tile, jobs, geoms, partials, wb, xf_w);
+      run_tile_any<T, L + 1, KM>(Lt, tile, jobs, geoms, partials, wb, xf_w);
   }
 }
 
@@ -517,15 +519,15 @@ __device__ __forceinline__ void run_tile_any(int Lt, const MomTile& tile, const 
 // left, so warps never wait for each other.  counter[0] is the work counter and counter[32]
 // the exit ticket, both zero on entry and left zero on exit.  LK >= 0: every tile has degree
 // LK; LK < 0: the tiles may have any degree (one launch for a whole uneven batch), each runs
-// the code of its job's degree.
-template <typename T, int LK>
-__global__ void __launch_bounds__(kThreads, TCM_MOMENT_CTAS_PER_SM)
+// the code of its job's degree.  KM: the accumulator budget of the chunk plan.
+template <typename T, int LK, int KM>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? moment_ctas(KM) : TCM_MOMENT_CTAS_PER_SM)
     k_moments(const MomJob* __restrict__ jobs, const MomTile* __restrict__ tiles, int n_tiles,
               int* __restrict__ counter, const SysGeom* __restrict__ geoms, double* __restrict__ partials) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Xform<T> s_xf[kThreads / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int kRow = LK >= 0 ? Plan<T, (LK >= 0 ? LK : 0)>::max_nacc() : MomTraits<T>::kmax;
+  constexpr int kRow = LK >= 0 ? Plan<T, (LK >= 0 ? LK : 0), KM>::max_nacc() : KM;
   T* wb = reinterpret_cast<T*>(smem) + warp * (kRow * MomTraits<T>::stride);
   pdl_wait();  // the centres and radii of the launch before are complete
   for (;;) {
@@ -535,9 +537,9 @@ __global__ void __launch_bounds__(kThreads, TCM_MOMENT_CTAS_PER_SM)
     if (ti >= n_tiles) break;
     const MomTile tile = tiles[ti];
     if constexpr (LK >= 0)
-      run_tile<T, LK, 0>(tile, jobs, geoms, partials, wb, &s_xf[warp]);
+      run_tile<T, LK, 0, KM>(tile, jobs, geoms, partials, wb, &s_xf[warp]);
     else
-      run_tile_any<T, 0>(jobs[tile.job].L, tile, jobs, geoms, partials, wb, &s_xf[warp]);
+      run_tile_any<T, 0, KM>(jobs[tile.job].L, tile, jobs, geoms, partials, wb, &s_xf[warp]);
   }
   // the last warp out leaves the work counter and its own ticket at zero for the next launch
   if (lane == 0 && atomicAdd(counter + 32, 1) == (int)(gridDim.x * (kThreads / 32)) - 1) {
@@ -546,16 +548,16 @@ __global__ void __launch_bounds__(kThreads, TCM_MOMENT_CTAS_PER_SM)
   }
 }
 
-template <typename T, int LK>
+template <typename T, int LK, int KM>
 int launch_moments_t(const MomJob* jobs, const MomTile* tiles, int n_tiles, int* counter,
                      const SysGeom* geoms, double* partials, int grid, cudaStream_t s) {
-  constexpr int smem = (kThreads / 32) * (LK >= 0 ? Plan<T, (LK >= 0 ? LK : 0)>::max_nacc() : MomTraits<T>::kmax) *
+  constexpr int smem = (kThreads / 32) * (LK >= 0 ? Plan<T, (LK >= 0 ? LK : 0), KM>::max_nacc() : KM) *
                        MomTraits<T>::stride * (int)sizeof(T);
   if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(k_moments<T, LK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_moments<T, LK, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return -1;
   }
-  return launch_pdl(k_moments<T, LK>, dim3(grid), dim3(kThreads), smem, s, jobs, tiles, n_tiles, counter, geoms,
+  return launch_pdl(k_moments<T, LK, KM>, dim3(grid), dim3(kThreads), smem, s, jobs, tiles, n_tiles, counter, geoms,
                     partials) == cudaSuccess
              ? 0
              : -1;

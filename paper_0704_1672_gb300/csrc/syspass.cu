@@ -86,14 +86,43 @@ __device__ __forceinline__ double warp_max_d(double v) {
   return __longlong_as_double(b);
 }
 
-// Float-float sum of one (hi, lo) pair over n tile rows (stride in floats): lane l adds rows l,
-// l + 32, ..., then the lanes' pairs are added in a fixed tree, so the same rows give the same
-// result in every run.  Float instructions only.  Rows are read through L2 (written by other CTAs).
-__device__ __forceinline__ double ordered_ff_sum(const float* p, int n, int stride, int lane) {
-  float s = 0.f, e = 0.f;
-  for (int r = lane; r < n; r += 32) ff_acc(s, e, FF{__ldcg(p + (long long)r * stride), __ldcg(p + (long long)r * stride + 1)});
-  ff_warp_sum(s, e);
-  return (double)s + (double)e;
+// Float-float sums of N consecutive (hi, lo) pairs over n tile rows (stride in floats, p and the
+// stride 16-byte aligned): lane l adds rows l, l + 32, ... (all N pairs of a row loaded
+// together), then the lanes' pairs are added in a fixed tree, so the same rows give the same
+// results in every run.  Float instructions only.  Rows are read through L2 (written by other
+// CTAs).  With kR2, also the maximum of the double at float offset r2_off of each row.
+template <int N, bool kR2>
+__device__ __forceinline__ void ordered_ff_sums(const float* p, int n, int stride, int lane, double* out,
+                                                int r2_off = 0, double* r2max = nullptr) {
+  float s[N], e[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) s[k] = e[k] = 0.f;
+  long long b2 = 0;
+  for (int r = lane; r < n; r += 32) {
+    const float* row = p + (long long)r * stride;
+    float4 v[N / 2];
+    float2 v1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) v[k] = __ldcg(reinterpret_cast<const float4*>(row) + k);
+    if (N % 2) v1 = __ldcg(reinterpret_cast<const float2*>(row) + N - 1);
+    if (kR2) b2 = max(b2, __ldcg(reinterpret_cast<const long long*>(row + r2_off)));
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      ff_acc(s[2 * k], e[2 * k], FF{v[k].x, v[k].y});
+      ff_acc(s[2 * k + 1], e[2 * k + 1], FF{v[k].z, v[k].w});
+    }
+    if (N % 2) ff_acc(s[N - 1], e[N - 1], FF{v1.x, v1.y});
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    ff_warp_sum(s[k], e[k]);
+    out[k] = (double)s[k] + (double)e[k];
+  }
+  if (kR2) {  // non-negative doubles order like their bit patterns
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b2 = max(b2, __shfl_xor_sync(0xffffffffu, b2, o));
+    *r2max = __longlong_as_double(b2);
+  }
 }
 
 // Tile rows hold their sums as (hi, lo) float pairs: no per-tile double arithmetic, which on GB300
@@ -199,11 +228,10 @@ __global__ void __launch_bounds__(kSysThreads) k_sys_centroid(const SysJob* __re
   if (!last_tile(&tickets[2 * tl.job], j.n_tiles, lane)) return;
   const float* p0 = reinterpret_cast<const float*>(part + (long long)j.tile_base * kSysPart);
   const double inv = j.n > 0 ? 1.0 / (double)j.n : 0.0;
-  const double cx = ordered_ff_sum(p0 + kRowCen, j.n_tiles, kRowFloats, lane) * inv;
-  const double cy = ordered_ff_sum(p0 + kRowCen + 2, j.n_tiles, kRowFloats, lane) * inv;
-  const double cz = ordered_ff_sum(p0 + kRowCen + 4, j.n_tiles, kRowFloats, lane) * inv;
+  double cs[3];
+  ordered_ff_sums<3, false>(p0 + kRowCen, j.n_tiles, kRowFloats, lane, cs);
   if (lane < 3) {  // the centre and its split into float parts
-    const double c = lane == 0 ? cx : (lane == 1 ? cy : cz);
+    const double c = (lane == 0 ? cs[0] : (lane == 1 ? cs[1] : cs[2])) * inv;
     const float hi = (float)c;
     geoms[j.geom].c[lane] = c;
     geoms[j.geom].chi[lane] = hi;
@@ -316,19 +344,21 @@ __global__ void __launch_bounds__(kSysThreads, 3) k_sys_radius_low(const SysJob*
   // the last tile of the system: its radius and its low-degree sums over all tiles (tile order),
   // written once to the system's sum row, which every moment job of the system reads
   const double* p0 = part + (long long)j.tile_base * kSysPart;
-  if (j.need_radius) {
+  if (j.need_low) {  // one pass over the tile rows: the ten sums and the radius together
+    double* sr = part + (long long)j.sum_row * kSysPart;
+    double low[kLowSums], m = 0.0;
+    ordered_ff_sums<kLowSums, true>(reinterpret_cast<const float*>(p0) + kRowLow, j.n_tiles, kRowFloats, lane, low,
+                                    2 * (kSysPartR2 - kSysPartLow), &m);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < kLowSums; ++k) sr[kSysPartLow + k] = low[k];
+      if (j.need_radius) geoms[j.geom].a = sqrt(m);
+    }
+  } else if (j.need_radius) {
     double m = 0.0;
     for (int r = lane; r < j.n_tiles; r += 32) m = fmax(m, __ldcg(p0 + (long long)r * kSysPart + kSysPartR2));
     m = warp_max_d(m);
     if (lane == 0) geoms[j.geom].a = sqrt(m);
-  }
-  if (j.need_low) {
-    double* sr = part + (long long)j.sum_row * kSysPart;
-    const float* f0 = reinterpret_cast<const float*>(p0);
-    for (int k = 0; k < kLowSums; ++k) {
-      const double t = ordered_ff_sum(f0 + kRowLow + 2 * k, j.n_tiles, kRowFloats, lane);
-      if (lane == 0) sr[kSysPartLow + k] = t;
-    }
   }
 }
 

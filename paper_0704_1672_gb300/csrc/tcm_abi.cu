@@ -108,6 +108,8 @@ struct tcm_ctx {
   // resident CTAs per SM the persistent grid is sized for
   int atoms_per_thread[2][kLmaxMax + 1];
   int ctas_per_sm[2][kLmaxMax + 1];
+  int plan_l[kLmaxMax + 1];  // mixed path: the float kernel's chunk plan per degree (1 or 2)
+  int64_t cfg_gen = 0;       // bumped by every tiling or chunking change (part of the graph key)
   // phase profiling
   bool prof = false;
   struct Mark {
@@ -237,14 +239,16 @@ struct Plan {
   std::vector<MomGroup> groups;    // (job, chunk) groups, largest tiles first; expanded on the device
   int n_tiles = 0;
   // FP64 (one launch per degree): the tiles of L are [tile_begin[L], tile_begin[L+1]); mixed
-  // (one launch over all degrees): every tile is in [0, n_tiles)
+  // (one launch per chunk plan over all degrees): the tiles of plan p are
+  // [tile_begin[p - 1], tile_begin[p])
   int tile_begin[kLmaxMax + 2] = {};
   int n_tile_ids = 0;
   size_t moms_doubles = 0;
 };
 
 void plan_job(tcm_ctx* c, int precision, MomJob& j, int& next_id) {
-  const int nch = moments_nchunks(precision, j.L);
+  j.plan = precision == TCM_FP64 ? 0 : c->plan_l[j.L];
+  const int nch = moments_nchunks(j.plan, j.L);
   const long long per_tile = 32LL * c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1][j.L];  // one warp
   long long tpc = (j.n + per_tile - 1) / per_tile;
   if (tpc < 1) tpc = 1;
@@ -254,18 +258,19 @@ void plan_job(tcm_ctx* c, int precision, MomJob& j, int& next_id) {
   next_id += nch * (int)tpc;
 }
 
-double chunk_cost(int precision, int L, int chunk) {
-  const int m0 = moments_chunk_m0(precision, L, chunk), m1 = moments_chunk_m0(precision, L, chunk + 1);
+double chunk_cost(int plan, int L, int chunk) {
+  const int m0 = moments_chunk_m0(plan, L, chunk), m1 = moments_chunk_m0(plan, L, chunk + 1);
   return 1.25 * chunk_off(L, m0, m1) + 4.0 * m0 + 30.0;
 }
 
 // The (job, chunk) groups in decreasing order of their tiles' cost (largest first, so the
 // persistent warps finish together).  FP64: grouped by degree (one launch per degree); mixed:
-// one order over all degrees (one launch).  The tiles themselves are written on the device
+// grouped by chunk plan (one launch per plan present, usually one), one order over all degrees.  The tiles themselves are written on the device
 // (k_expand_tiles), so the host work is O(groups log groups).
 void build_tiles(int precision, Plan& P) {
-  // one 64-bit key per group: [degree (FP64 only)] [largest cost first] [group index], so a plain
-  // sort of integers gives the order deterministically (ties in their planning order)
+  // one 64-bit key per group: [degree (FP64) or chunk plan (mixed)] [largest cost first] [group
+  // index], so a plain sort of integers gives the order deterministically (ties in their
+  // planning order)
   struct Group {
     int job, chunk;
   };
@@ -276,11 +281,11 @@ void build_tiles(int precision, Plan& P) {
   const bool by_degree = precision == TCM_FP64;
   for (int ji = 0; ji < (int)P.jobs.size(); ++ji) {
     const MomJob& j = P.jobs[ji];
-    const int nch = moments_nchunks(precision, j.L);
+    const int nch = moments_nchunks(j.plan, j.L);
     for (int ch = 0; ch < nch; ++ch) {
-      const double cost = chunk_cost(precision, j.L, ch) * (double)j.atoms_per_tile;
+      const double cost = chunk_cost(j.plan, j.L, ch) * (double)j.atoms_per_tile;
       const unsigned long long cq = (unsigned long long)std::min(cost, 134217727.0);  // 27 bits
-      key.push_back(((by_degree ? (unsigned long long)j.L : 0ull) << 59) | ((134217727ull - cq) << 32) |
+      key.push_back(((unsigned long long)(by_degree ? j.L : j.plan - 1) << 59) | ((134217727ull - cq) << 32) |
                     (unsigned long long)g.size());
       g.push_back(Group{ji, ch});
     }
@@ -294,7 +299,7 @@ void build_tiles(int precision, Plan& P) {
     P.tile_begin[L] = first;
     for (; gi < key.size(); ++gi) {
       const Group& gr = g[key[gi] & 0xffffffffull];
-      if (by_degree && P.jobs[gr.job].L != L) break;
+      if ((by_degree ? P.jobs[gr.job].L : P.jobs[gr.job].plan - 1) != L) break;
       const int n = P.jobs[gr.job].tiles_per_chunk;
       P.groups.push_back(MomGroup{gr.job, gr.chunk, n, first});
       first += n;
@@ -304,11 +309,21 @@ void build_tiles(int precision, Plan& P) {
   P.n_tiles = first;
 }
 
+// Moment-phase launches of a plan (for the launch counts of a replayed graph): FP64 one per
+// degree present, mixed one per chunk plan present.
+int moment_launches(int precision, const Plan& P) {
+  const int nb = precision == TCM_FP64 ? kLmaxMax + 1 : kNumPlans - 1;
+  int n = 0;
+  for (int k = 0; k < nb; ++k) n += P.tile_begin[k + 1] > P.tile_begin[k];
+  return n;
+}
+
 // Queue the moment pass (step a2/a3) for every job of the plan.
 // The moment kernels' work counters and exit tickets (counters[L], counters[32 + L]) are zero
 // on entry and left zero by every launch, so they are cleared once, when allocated.
 int ensure_moment_buffers(tcm_ctx* c, int precision, const Plan& P) {
-  TRY(dev_ensure(c, c->partials, (size_t)std::max(P.n_tile_ids, 1) * moments_kmax(precision) * sizeof(double)));
+  TRY(dev_ensure(c, c->partials, (size_t)std::max(P.n_tile_ids, 1) * plan_row(precision == TCM_FP64 ? 0 : 1) *
+                                     sizeof(double)));
   TRY(dev_ensure(c, c->tiles, (size_t)std::max(P.n_tiles, 1) * sizeof(MomTile)));
   void* before = c->counters.p;
   TRY(dev_ensure(c, c->counters, 64 * sizeof(int)));
@@ -319,13 +334,12 @@ int ensure_moment_buffers(tcm_ctx* c, int precision, const Plan& P) {
 }
 
 // Counter slots of the moment kernels (zero on entry, left zero): [L] and [32 + L] for the
-// per-degree FP64 launches, [kAnyCounter] and [32 + kAnyCounter] for the mixed launch over all
-// degrees.
-constexpr int kAnyCounter = kLmaxMax + 1;
+// per-degree FP64 launches, [kAnyCounter + p] and [32 + kAnyCounter + p] for the mixed launch of
+// chunk plan p over all degrees.
+constexpr int kAnyCounter = kLmaxMax;  // + plan (1 or 2)
 
 int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, const SysGeom* d_geoms,
                 cudaStream_t st) {
-  const int kmax = moments_kmax(precision);
   TRY(ensure_moment_buffers(c, precision, P));
   int* counters = static_cast<int*>(c->counters.p);
   double* parts = static_cast<double*>(c->partials.p);
@@ -339,30 +353,28 @@ int run_moments(tcm_ctx* c, int precision, const Plan& P, const MomJob* d_jobs, 
       if (e == b) continue;
       const int cps = c->ctas_per_sm[0][L];
       const int grid = std::min((e - b + kThreads / 32 - 1) / (kThreads / 32), cps * c->num_sms);  // warp tiles
-      TRY_LAUNCH(launch_moments(precision, L, d_jobs, tiles + b, e - b, counters + L, d_geoms, parts, grid, st));
+      TRY_LAUNCH(launch_moments(0, L, d_jobs, tiles + b, e - b, counters + L, d_geoms, parts, grid, st));
     }
   } else if (P.n_tiles > 0) {
-    int cps = 1;  // the grid of the single launch: the largest CTAs per SM of the degrees present
-    for (const MomJob& j : P.jobs) cps = std::max(cps, c->ctas_per_sm[1][j.L]);
-    PhaseScope ps(c, TCM_PHASE_MOMENTS, 1);
-    const int grid = std::min((P.n_tiles + kThreads / 32 - 1) / (kThreads / 32), cps * c->num_sms);
-    TRY_LAUNCH(launch_moments_any(d_jobs, tiles, P.n_tiles, counters + kAnyCounter, d_geoms, parts, grid, st));
+    PhaseScope ps(c, TCM_PHASE_MOMENTS, moment_launches(precision, P));
+    for (int p = 1; p < kNumPlans; ++p) {
+      const int b = P.tile_begin[p - 1], e = P.tile_begin[p];
+      if (e == b) continue;
+      int cps = 1;  // the grid: the largest CTAs per SM of the plan's degrees, within its kernel's limit
+      for (const MomJob& j : P.jobs)
+        if (j.plan == p) cps = std::max(cps, c->ctas_per_sm[1][j.L]);
+      cps = std::min(cps, moment_ctas(plan_kmax(p)));
+      const int grid = std::min((e - b + kThreads / 32 - 1) / (kThreads / 32), cps * c->num_sms);
+      TRY_LAUNCH(launch_moments(p, -1, d_jobs, tiles + b, e - b, counters + kAnyCounter + p, d_geoms, parts, grid,
+                                st));
+    }
   }
   {
     PhaseScope ps(c, TCM_PHASE_FINALIZE, 1);
-    TRY_LAUNCH(launch_finalize(d_jobs, (int)P.jobs.size(), parts, d_geoms, c->d_imap, c->d_fmap,
-                               c->d_imap_off + (precision == TCM_FP64 ? 0 : kLmaxMax + 2), kmax,
+    TRY_LAUNCH(launch_finalize(d_jobs, (int)P.jobs.size(), parts, d_geoms, c->d_imap, c->d_fmap, c->d_imap_off,
                                static_cast<double*>(c->gpart.p), st));
   }
   return TCM_OK;
-}
-
-// Moment-phase launches of a plan (for the launch counts of a replayed graph).
-int moment_launches(int precision, const Plan& P) {
-  if (precision != TCM_FP64) return P.n_tiles > 0 ? 1 : 0;
-  int n = 0;
-  for (int L = 0; L <= kLmaxMax; ++L) n += P.tile_begin[L + 1] > P.tile_begin[L];
-  return n;
 }
 
 // The pass over the systems' atoms before the moment pass (syspass.cu): step a1 for the systems
@@ -537,6 +549,7 @@ int tcm_ctx_create(tcm_ctx_t* out, int lmax_cap, void* cuda_stream) {
     c->atoms_per_thread[0][L] = 32;  // FP64: 32 atoms per lane (1,024 per warp tile)
     c->atoms_per_thread[1][L] = 64;  // mixed: 64 atoms per lane (2,048 per warp tile)
     c->ctas_per_sm[0][L] = c->ctas_per_sm[1][L] = TCM_MOMENT_CTAS_PER_SM;
+    c->plan_l[L] = 1;
   }
   int rc = TCM_OK;
   do {
@@ -586,6 +599,7 @@ int tcm_ctx_set_tiling(tcm_ctx_t c, int precision, int atoms_per_lane) {
   if (atoms_per_lane < 1 || atoms_per_lane > 4096)
     return set_err(TCM_EINVAL, "tcm_ctx_set_tiling: atoms_per_lane outside [1, 4096]");
   for (int L = 0; L <= kLmaxMax; ++L) c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1][L] = atoms_per_lane;
+  ++c->cfg_gen;
   return TCM_OK;
 }
 
@@ -595,10 +609,12 @@ int tcm_ctx_set_tiling_l(tcm_ctx_t c, int precision, int lmax, int atoms_per_lan
   if (lmax < 0 || lmax > kLmaxMax) return set_err(TCM_EINVAL, "tcm_ctx_set_tiling_l: lmax outside [0, %d]", kLmaxMax);
   if (atoms_per_lane < 1 || atoms_per_lane > 4096)
     return set_err(TCM_EINVAL, "tcm_ctx_set_tiling_l: atoms_per_lane outside [1, 4096]");
-  if (ctas_per_sm < 1 || ctas_per_sm > TCM_MOMENT_CTAS_PER_SM)
-    return set_err(TCM_EINVAL, "tcm_ctx_set_tiling_l: ctas_per_sm outside [1, %d]", TCM_MOMENT_CTAS_PER_SM);
+  const int cmax = precision == TCM_FP64 ? TCM_MOMENT_CTAS_PER_SM : moment_ctas(kKmaxF32Small);
+  if (ctas_per_sm < 1 || ctas_per_sm > cmax)
+    return set_err(TCM_EINVAL, "tcm_ctx_set_tiling_l: ctas_per_sm outside [1, %d]", cmax);
   c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1][lmax] = atoms_per_lane;
   c->ctas_per_sm[precision == TCM_FP64 ? 0 : 1][lmax] = ctas_per_sm;
+  ++c->cfg_gen;
   return TCM_OK;
 }
 
@@ -608,6 +624,24 @@ int tcm_ctx_get_tiling_l(tcm_ctx_t c, int precision, int lmax, int* atoms_per_la
   if (lmax < 0 || lmax > kLmaxMax) return set_err(TCM_EINVAL, "tcm_ctx_get_tiling_l: lmax outside [0, %d]", kLmaxMax);
   if (atoms_per_lane) *atoms_per_lane = c->atoms_per_thread[precision == TCM_FP64 ? 0 : 1][lmax];
   if (ctas_per_sm) *ctas_per_sm = c->ctas_per_sm[precision == TCM_FP64 ? 0 : 1][lmax];
+  return TCM_OK;
+}
+
+int tcm_ctx_set_chunking_l(tcm_ctx_t c, int lmax, int kmax) {
+  TRY(check_ctx(c));
+  if (lmax < 0 || lmax > kLmaxMax) return set_err(TCM_EINVAL, "tcm_ctx_set_chunking_l: lmax outside [0, %d]", kLmaxMax);
+  if (kmax != plan_kmax(1) && kmax != plan_kmax(2))
+    return set_err(TCM_EINVAL, "tcm_ctx_set_chunking_l: kmax %d is not %d or %d", kmax, plan_kmax(1), plan_kmax(2));
+  c->plan_l[lmax] = kmax == plan_kmax(1) ? 1 : 2;
+  ++c->cfg_gen;
+  return TCM_OK;
+}
+
+int tcm_ctx_get_chunking_l(tcm_ctx_t c, int lmax, int* kmax, int* n_chunks) {
+  TRY(check_ctx(c));
+  if (lmax < 0 || lmax > kLmaxMax) return set_err(TCM_EINVAL, "tcm_ctx_get_chunking_l: lmax outside [0, %d]", kLmaxMax);
+  if (kmax) *kmax = plan_kmax(c->plan_l[lmax]);
+  if (n_chunks) *n_chunks = moments_nchunks(c->plan_l[lmax], lmax);
   return TCM_OK;
 }
 
@@ -1004,7 +1038,8 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
                                 (long long)rots.empty(), (long long)(uintptr_t)base, (long long)(uintptr_t)c->gpart.p,
                                 (long long)(uintptr_t)c->systk.p, (long long)(uintptr_t)c->partials.p,
                                 (long long)(uintptr_t)c->counters.p, (long long)(uintptr_t)E, (long long)(uintptr_t)status,
-                                (long long)P.groups.size(), (long long)P.n_tiles, (long long)(uintptr_t)c->tiles.p};
+                                (long long)P.groups.size(), (long long)P.n_tiles, (long long)(uintptr_t)c->tiles.p,
+                                (long long)c->cfg_gen};
   for (int L = 0; L <= kLmaxMax + 1; ++L) key.push_back(P.tile_begin[L]);
   if (!c->gexec || key != c->gkey) {
     // by default capture only a shape seen twice in a row: a stream of changing shapes

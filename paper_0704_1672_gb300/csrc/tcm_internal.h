@@ -43,6 +43,21 @@ constexpr int kThreads = 128;  // threads per moment CTA (4 warps)
 constexpr int kKmaxF32 = TCM_KMAX_F32;
 constexpr int kKmaxF64 = TCM_KMAX_F64;
 
+// Chunk plans ("plans" below): the split of the (L+1)^2 accumulators of degree L into column
+// chunks of at most kmax.  Plan 0 is the double kernels' (kmax = kKmaxF64); the float kernel is
+// built for two budgets, plan 1 (kKmaxF32 accumulators per lane, 2 CTAs per SM) and plan 2
+// (kKmaxF32Small, fewer accumulators and registers, 3 CTAs per SM), chosen per degree
+// (tcm_ctx_set_chunking_l, the autotuner).  Partial rows keep the largest budget's stride in
+// every plan.
+constexpr int kKmaxF32Small = 96;
+constexpr int kNumPlans = 3;
+__host__ __device__ constexpr int plan_kmax(int plan) {
+  return plan == 0 ? kKmaxF64 : (plan == 1 ? kKmaxF32 : kKmaxF32Small);
+}
+__host__ __device__ constexpr int plan_row(int plan) { return plan == 0 ? kKmaxF64 : kKmaxF32; }
+// CTAs per SM a float moment kernel of budget kmax is compiled for (its register limit).
+__host__ __device__ constexpr int moment_ctas(int kmax) { return kmax <= kKmaxF32Small ? 3 : TCM_MOMENT_CTAS_PER_SM; }
+
 // ---------------------------------------------------------------------------------
 // Column-chunk plan (host and device, compile time).
 __host__ __device__ constexpr int col_acc(int L, int m) { return m == 0 ? (L + 1) : 2 * (L - m + 1); }
@@ -151,6 +166,8 @@ struct MomJob {    // one moment set: a system at one Lmax under one rotation
   int low_base;    // mixed precision: the row of the system-pass partials holding the system's
   int low_tiles;   // low-degree sums (SysJob.sum_row) when low_tiles != 0; 0 = the degrees l <= 2
                    // keep the float kernel's values
+  int plan;        // chunk plan of its moment tiles (0: double kernels; 1, 2: float budgets)
+  int pad_;
 };
 
 struct MomTile {   // one tile of moment work
@@ -205,10 +222,12 @@ constexpr int kSysPart = kSysPartLow + kLowSums;
 
 // Programmatic dependent launch: a kernel launched with programmatic stream serialization
 // is set up while its predecessor drains; pdl_wait() blocks until the predecessor grid has
-// completed and its memory is visible (a no-op for an ordinary launch).  No kernel issues
-// griddepcontrol.launch_dependents: dependent CTAs made resident before the moment kernel's
-// tail had drained slowed the replayed step down (0.372 ms against 0.325 ms).
+// completed and its memory is visible (a no-op for an ordinary launch).  Only the finalisation
+// issues griddepcontrol.launch_dependents (pdl_trigger), so that the contraction's CTAs set up
+// their tables while the last finalisation CTAs run; dependent CTAs made resident before the
+// moment kernel's tail had drained slowed the replayed step down (0.372 ms against 0.325 ms).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Launch with programmatic stream serialization (programmatic dependent launch): the kernel
 // may be scheduled while the previous kernel on the stream drains, and must call
@@ -231,10 +250,11 @@ cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
 // ---------------------------------------------------------------------------------
 // Launchers (defined in the .cu files).
 
-// Moment kernels: one persistent launch over `n_tiles` tiles of Lmax L.
-// precision: TCM_MIXED (float kernels) or TCM_FP64 (double kernels).  counter[0] and
-// counter[32] must be zero on entry; the launch leaves them zero.
-int launch_moments(int precision, int L, const MomJob* jobs, const MomTile* tiles, int n_tiles,
+// Moment kernels: one persistent launch over `n_tiles` tiles.  plan 0 (double kernels): every
+// tile has degree L; plans 1 and 2 (float kernels): tiles of any degree whose jobs have that
+// plan (each tile runs the code of its job's degree); the tiles are taken in array order.
+// counter[0] and counter[32] must be zero on entry; the launch leaves them zero.
+int launch_moments(int plan, int L, const MomJob* jobs, const MomTile* tiles, int n_tiles,
                    int* counter, const SysGeom* geoms, double* partials, int grid, cudaStream_t s);
 // The tile lists of a call, written on the device: the moment pass's from its groups,
 // tiles[g.first + t] = (g.job, g.chunk, t, row), t < g.n, row = jobs[g.job].tile_base +
@@ -242,16 +262,10 @@ int launch_moments(int precision, int L, const MomJob* jobs, const MomTile* tile
 // (job, t), t < sj.n_tiles.  One warp per group or system job.
 int launch_expand_tiles(const MomGroup* groups, int n_groups, const MomJob* jobs, MomTile* tiles, const SysJob* sjobs,
                         int n_sjobs, SysTile* t1, SysTile* t2, cudaStream_t s);
-// Mixed precision: one persistent launch over tiles of any degrees (each tile runs the code of
-// its job's degree); the tiles are taken in array order.
-int launch_moments_any(const MomJob* jobs, const MomTile* tiles, int n_tiles, int* counter, const SysGeom* geoms,
-                       double* partials, int grid, cudaStream_t s);
-int moments_smem_bytes(int precision, int L);
-int moments_kmax(int precision);
-int moments_nchunks(int precision, int L);
-int moments_chunk_m0(int precision, int L, int chunk);  // first column of a chunk (chunk = nch: L + 1)
-// Host: the inverse component maps of both precisions and their factors F_lm (imap_off has
-// 2 (kLmaxMax + 2) entries, FP64 first, each block ending with its total).
+int moments_nchunks(int plan, int L);
+int moments_chunk_m0(int plan, int L, int chunk);  // first column of a chunk (chunk = nch: L + 1)
+// Host: the inverse component maps of every plan and their factors F_lm (imap_off has
+// kNumPlans (kLmaxMax + 2) entries, plan by plan, each block ending with its total).
 void finalize_tables(std::vector<int>& imap_off, std::vector<int>& imap, std::vector<double>& fmap);
 
 // Step a1 and the low-degree sums: pass 1 over the n1 tiles of the systems that need a centroid,
@@ -262,13 +276,14 @@ int launch_sys(const SysJob* jobs, const SysTile* t1, int n1, const SysTile* t2,
                SysGeom* geoms, cudaStream_t s);
 int sys_launches(int n1, int n2);
 int sys_tile_atoms(long long n);
-// Step a3: one CTA per job.  imap + imap_off[L] lists, per (chunk, slot) of degree L, the packed
-// component it holds (-1 for none), nch(L) x kmax entries; fmap beside it holds that
-// component's F_lm with the sign of the kernels' H variables.
+// Step a3: one CTA per job.  imap + imap_off[plan (kLmaxMax + 2) + L] lists, per (chunk, slot) of
+// degree L under the job's plan, the packed component it holds (-1 for none), nch x
+// plan_kmax(plan) entries; fmap beside it holds that component's F_lm with the sign of the
+// kernels' H variables.  Partial rows are plan_row(plan) doubles apart.
 // Jobs with low_tiles != 0 take their degrees l <= min(kLowLmax, L) from the low-degree sums of
 // their system (row low_base of the system-pass partials syspart) rotated by the job's rotation.
 int launch_finalize(const MomJob* jobs, int n_jobs, const double* partials, const SysGeom* geoms,
-                    const int* imap, const double* fmap, const int* imap_off, int kmax, const double* syspart,
+                    const int* imap, const double* fmap, const int* imap_off, const double* syspart,
                     cudaStream_t s);
 
 

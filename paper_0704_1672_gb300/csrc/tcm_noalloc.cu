@@ -49,7 +49,7 @@ constexpr size_t kOffSTiles1 = align256(kOffSJob + sizeof(SysJob));
 constexpr size_t kOffSTiles2 = align256(kOffSTiles1 + sizeof(SysTile) * kNaSysTiles);
 constexpr size_t kOffSPart = align256(kOffSTiles2 + sizeof(SysTile) * kNaSysTiles);
 constexpr size_t kOffCounters = align256(kOffSPart + sizeof(double) * kSysPart * kNaSysTiles);
-constexpr int kNaImapInts = 4 * kNaCompTotal;  // room for both precisions' (chunk, slot) maps
+constexpr int kNaImapInts = 4 * kNaCompTotal;  // room for the (chunk, slot) maps of plans 0 and 1
 constexpr size_t kOffImapOff = align256(kOffCounters + sizeof(int) * 64);
 constexpr size_t kOffImap = align256(kOffImapOff + sizeof(int) * 2 * (kLmaxMax + 2));
 constexpr size_t kOffFmap = align256(kOffImap + sizeof(int) * kNaImapInts);
@@ -81,10 +81,15 @@ int setup_device(int dev, char** out) {
   std::vector<double> fmap;
   std::vector<int> imap_off, imap;
   finalize_tables(imap_off, imap, fmap);
-  if ((int)imap.size() > kNaImapInts) return na_err(TCM_ECUDA, "tcm_moments_noalloc: internal table size mismatch");
-  if (cudaMemcpy(base + kOffFmap, fmap.data(), fmap.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(base + kOffImapOff, imap_off.data(), imap_off.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(base + kOffImap, imap.data(), imap.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+  // only the chunk plans this entry point runs: 0 (double kernels) and 1 (the float kernel's
+  // default budget), the first two blocks of the tables
+  const size_t n_off = 2 * (kLmaxMax + 2);
+  const size_t n_map = (size_t)imap_off[n_off - 1];
+  if (imap_off.size() < n_off || n_map > (size_t)kNaImapInts)
+    return na_err(TCM_ECUDA, "tcm_moments_noalloc: internal table size mismatch");
+  if (cudaMemcpy(base + kOffFmap, fmap.data(), n_map * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(base + kOffImapOff, imap_off.data(), n_off * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(base + kOffImap, imap.data(), n_map * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: copying the tables into the scratch failed");
   // A copy from pageable host memory may return before the data reach the device; the
   // kernels of this call may run on another (non-blocking) stream, so wait for the tables.
@@ -134,8 +139,9 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   if (rc != TCM_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
-  const int kmax = moments_kmax(precision);
-  const int nch = moments_nchunks(precision, lmax);
+  const int plan = precision == TCM_FP64 ? 0 : 1;
+  const int kmax = plan_kmax(plan);
+  const int nch = moments_nchunks(plan, lmax);
   const int tpc = (int)std::max<long long>(1, (s->n + kNaTileAtoms - 1) / kNaTileAtoms);
   if (nch > kNaMaxChunks || nch * kmax > 800 || tpc > kNaTilesPerChunk)
     return na_err(TCM_EINVAL, "tcm_moments_noalloc: request exceeds the fixed scratch");
@@ -148,6 +154,7 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   job.tiles_per_chunk = tpc;
   job.atoms_per_tile = (int)((s->n + tpc - 1) / tpc);
   job.tile_base = 0;
+  job.plan = plan;
   for (int k = 0; k < 9; ++k) job.rot[k] = rot ? rot[k] : ((k % 4 == 0) ? 1.0 : 0.0);
   job.out = q_out;
   SysGeom geom{};
@@ -193,14 +200,14 @@ extern "C" int tcm_moments_noalloc(const tcm_system* s, const double* rot, int l
   if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: cudaDeviceGetAttribute failed");
   const int n_tiles = nch * tpc;
-  if (launch_moments(precision, lmax, d_job, reinterpret_cast<MomTile*>(base + kOffTiles), n_tiles,
+  if (launch_moments(plan, lmax, d_job, reinterpret_cast<MomTile*>(base + kOffTiles), n_tiles,
                      reinterpret_cast<int*>(base + kOffCounters), d_geom, reinterpret_cast<double*>(base + kOffPartials),
                      std::min((n_tiles + kThreads / 32 - 1) / (kThreads / 32), 2 * num_sms), st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: moment launch failed");
   if (launch_finalize(d_job, 1, reinterpret_cast<double*>(base + kOffPartials), d_geom,
                       reinterpret_cast<int*>(base + kOffImap), reinterpret_cast<double*>(base + kOffFmap),
-                      reinterpret_cast<int*>(base + kOffImapOff) + (precision == TCM_FP64 ? 0 : kLmaxMax + 2),
-                      kmax, reinterpret_cast<double*>(base + kOffSPart), st) != 0)
+                      reinterpret_cast<int*>(base + kOffImapOff), reinterpret_cast<double*>(base + kOffSPart),
+                      st) != 0)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: finalisation launch failed");
   if (geom_out && cudaMemcpyAsync(geom_out, d_geom, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return na_err(TCM_ECUDA, "tcm_moments_noalloc: copy of the centre and radius failed");

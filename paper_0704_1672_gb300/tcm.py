@@ -79,6 +79,8 @@ def lib():
         L.tcm_ctx_set_tiling.argtypes = [P, i32, i32]
         L.tcm_ctx_set_tiling_l.argtypes = [P, i32, i32, i32, i32]
         L.tcm_ctx_get_tiling_l.argtypes = [P, i32, i32, P, P]
+        L.tcm_ctx_set_chunking_l.argtypes = [P, i32, i32]
+        L.tcm_ctx_get_chunking_l.argtypes = [P, i32, P, P]
         L.tcm_ctx_set_graphs.argtypes = [P, i32]
         L.tcm_ctx_set_rotate_cached.argtypes = [P, i32]
         L.tcm_gradients_batch.argtypes = [P, i32, P, ctypes.c_int64, P, i32, P, P, P]
@@ -89,7 +91,7 @@ def lib():
         for name in ("tcm_ctx_create", "tcm_ctx_set_stream", "tcm_prepare", "tcm_moments", "tcm_energy",
                      "tcm_energy_batch", "tcm_direct", "tcm_ctx_set_profiling", "tcm_ctx_read_profile",
                      "tcm_moments_noalloc", "tcm_ctx_set_tiling", "tcm_ctx_set_graphs", "tcm_ctx_graph_stats",
-                     "tcm_ctx_set_tiling_l", "tcm_ctx_get_tiling_l",
+                     "tcm_ctx_set_tiling_l", "tcm_ctx_get_tiling_l", "tcm_ctx_set_chunking_l", "tcm_ctx_get_chunking_l",
                      "tcm_ctx_set_rotate_cached", "tcm_rotate_moments", "tcm_gradients_batch",
                      "tcm_direct_batch"):
             getattr(L, name).restype = i32
@@ -194,6 +196,15 @@ class Context:
         apl, cps = ctypes.c_int(), ctypes.c_int()
         _check(lib().tcm_ctx_get_tiling_l(self._h, int(precision), int(lmax), ctypes.byref(apl), ctypes.byref(cps)))
         return apl.value, cps.value
+
+    def tcm_ctx_set_chunking_l(self, lmax, kmax):
+        _check(lib().tcm_ctx_set_chunking_l(self._h, int(lmax), int(kmax)))
+
+    def tcm_ctx_get_chunking_l(self, lmax):
+        """(kmax, number of column chunks) of the mixed path's moment pass at degree lmax."""
+        km, nch = ctypes.c_int(), ctypes.c_int()
+        _check(lib().tcm_ctx_get_chunking_l(self._h, int(lmax), ctypes.byref(km), ctypes.byref(nch)))
+        return km.value, nch.value
 
     def tcm_ctx_set_rotate_cached(self, enable: bool):
         _check(lib().tcm_ctx_set_rotate_cached(self._h, 1 if enable else 0))

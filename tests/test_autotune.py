@@ -11,21 +11,41 @@ from paper_0704_1672_gb300 import autotune, synth, tcm
 class FakeCtx:
     def __init__(self):
         self.tiling = {}
+        self.chunking = {}
         self.calls = 0
 
     def tcm_ctx_get_tiling_l(self, precision, L):
         return self.tiling.get((precision, L), (64, 2))
 
     def tcm_ctx_set_tiling_l(self, precision, L, apl, cps):
+        assert 1 <= cps <= (2 if precision == tcm.TCM_FP64 else 3)
         self.tiling[(precision, L)] = (apl, cps)
+
+    def tcm_ctx_get_chunking_l(self, L):
+        k = self.chunking.get(L, 160)
+        return k, -(-(L + 1) ** 2 // k)
+
+    def tcm_ctx_set_chunking_l(self, L, kmax):
+        assert kmax in (160, 96)
+        self.chunking[L] = kmax
+
+    def setting(self, precision, L):
+        apl, cps = self.tcm_ctx_get_tiling_l(precision, L)
+        return (apl, cps, self.chunking.get(L, 160) if precision != tcm.TCM_FP64 else 80)
 
     def tcm_energy_batch_packed(self, pb, precision, E=None, status=None):
         self.calls += 1
 
 
-def cost(L, apl, cps):
-    # a made-up landscape with its minimum at apl = 2**(3 + L // 8), cps = 1 for odd L
-    return abs(np.log2(apl) - (3 + L // 8)) + (0.5 if (cps == 1) != (L % 2 == 1) else 0.0) + 0.01 * L
+def cost(L, apl, cps, kmax):
+    # a made-up landscape with its minimum at apl = 2**(3 + L // 8), cps = 1 for odd L, and the
+    # small chunk budget (kmax 96, with 3 CTAs per SM) for L < 16
+    c = abs(np.log2(apl) - (3 + L // 8)) + (0.5 if (cps == 1) != (L % 2 == 1) else 0.0) + 0.01 * L
+    if L < 16:
+        c += 0.0 if (kmax == 96 and cps == 3) else 1.0
+    else:
+        c += 0.0 if kmax == 160 else 0.7
+    return c
 
 
 def systems(n):
@@ -49,32 +69,43 @@ def test_tune_picks_the_fastest_per_degree_and_applies_it():
 
     def measure(Ldeg, run):
         run()
-        apl, cps = ctx.tcm_ctx_get_tiling_l(tcm.TCM_MIXED, Ldeg)
-        return cost(Ldeg, apl, cps)
+        return cost(Ldeg, *ctx.setting(tcm.TCM_MIXED, Ldeg))
 
     res = autotune.tune(ctx, systems(3), rng.integers(0, 3, k), rng.integers(0, 3, k), L, R0,
                         rotB=synth.random_rotations(rng, k), precision=tcm.TCM_MIXED, measure=measure)
+    # the candidates: every atoms-per-lane value with CTAs per SM up to what each budget's kernel
+    # is compiled for (2 at kmax 160, 3 at kmax 96)
+    grid = {(a, c, km): cost(0, a, c, km) for km in (160, 96) for a in autotune.DEFAULT_ATOMS_PER_LANE
+            for c in (1, 2, 3) if c <= (2 if km == 160 else 3)}
+    assert len(autotune.candidates(tcm.TCM_MIXED)) == len(grid) == 5 * len(autotune.DEFAULT_ATOMS_PER_LANE)
     for Ldeg in (8, 13, 16, 24):
-        grid = {(a, c): cost(Ldeg, a, c) for a in autotune.DEFAULT_ATOMS_PER_LANE for c in autotune.DEFAULT_CTAS_PER_SM}
+        grid = {cand: cost(Ldeg, *cand) for cand in autotune.candidates(tcm.TCM_MIXED)}
         want = min(grid, key=grid.get)
         assert res.best[Ldeg] == want
-        assert ctx.tiling[(tcm.TCM_MIXED, Ldeg)] == want
+        assert ctx.setting(tcm.TCM_MIXED, Ldeg) == want
         assert res.timings[Ldeg] == pytest.approx(grid)
-    assert ctx.calls == 4 * len(autotune.DEFAULT_ATOMS_PER_LANE) * len(autotune.DEFAULT_CTAS_PER_SM)
+    assert res.best[8][2] == 96 and res.best[24][2] == 160
+    assert ctx.calls == 4 * len(autotune.candidates(tcm.TCM_MIXED))
+
+
+def test_fp64_candidates_keep_the_double_budget():
+    c = autotune.candidates(tcm.TCM_FP64, (32, 64), (1, 2, 3))
+    assert c == [(32, 1, 80), (32, 2, 80), (64, 1, 80), (64, 2, 80)]
 
 
 def test_cache_round_trip(tmp_path):
     ctx = FakeCtx()
-    r = autotune.TuneResult(tcm.TCM_MIXED, best={8: (32, 1), 24: (128, 2)},
-                            timings={8: {(32, 1): 0.1, (64, 2): 0.2}, 24: {(128, 2): 0.3}})
+    r = autotune.TuneResult(tcm.TCM_MIXED, best={8: (32, 3, 96), 24: (128, 2, 160)},
+                            timings={8: {(32, 3, 96): 0.1, (64, 2, 160): 0.2}, 24: {(128, 2, 160): 0.3}})
     path = str(tmp_path / "tiling.json")
     autotune.save(path, r, "GB300|abc")
-    autotune.save(path, autotune.TuneResult(tcm.TCM_FP64, best={8: (16, 2)}), "GB300|abc")
+    autotune.save(path, autotune.TuneResult(tcm.TCM_FP64, best={8: (16, 2, 80)}), "GB300|abc")
     assert autotune.load(ctx, path, tcm.TCM_MIXED, "other|key") is None
     got = autotune.load(ctx, path, tcm.TCM_MIXED, "GB300|abc")
     assert got.best == r.best and got.timings == r.timings
-    assert ctx.tiling == {(tcm.TCM_MIXED, 8): (32, 1), (tcm.TCM_MIXED, 24): (128, 2)}
-    assert autotune.load(ctx, path, tcm.TCM_FP64, "GB300|abc").best == {8: (16, 2)}
+    assert ctx.tiling == {(tcm.TCM_MIXED, 8): (32, 3), (tcm.TCM_MIXED, 24): (128, 2)}
+    assert ctx.chunking == {8: 96, 24: 160}
+    assert autotune.load(ctx, path, tcm.TCM_FP64, "GB300|abc").best == {8: (16, 2, 80)}
 
 
 @pytest.mark.gpu
@@ -106,7 +137,7 @@ def test_tuned_uneven_batch_matches_oracle():
         res = autotune.tune(ctx, T, a, b, L, R0, rotB=rot, reps=2)
         assert sorted(res.best) == [8, 12, 16, 24]
         for Ldeg, best in res.best.items():
-            assert ctx.tcm_ctx_get_tiling_l(tcm.TCM_MIXED, Ldeg) == best
+            assert autotune.get_setting(ctx, tcm.TCM_MIXED, Ldeg) == best
             assert res.timings[Ldeg][best] == min(res.timings[Ldeg].values())
         print({Ldeg: (best, round(res.timings[Ldeg][best], 4)) for Ldeg, best in res.best.items()})
         E, st = ctx.tcm_energy_batch(T, a, b, L, R0, rotB=rot)

@@ -116,3 +116,33 @@ def test_gradient_modes_agree_fp64(tcm, systems, L):
                     assert np.linalg.norm(x - ref) / scale < TOL_FP64 * 10, (L, i, part, x, ref)
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_energy_does_not_depend_on_the_batch(tcm, systems, precision):
+    """The contraction kernel's CTA size follows the batch (its largest degree and its item count),
+    so the same item must give the same bits alone, beside a degree-24 item, and in a batch of
+    more than a thousand items; energies and gradients alike."""
+    A, B = systems
+    prec = tcm.TCM_FP64 if precision == "fp64" else tcm.TCM_MIXED
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    T = [(torch.tensor(A, dtype=dt, device="cuda"), None, None), (torch.tensor(B, dtype=dt, device="cuda"), None, None)]
+    rng = np.random.default_rng(5)
+    n = 1100
+    R0 = synth.unit_vectors(rng, n) * rng.uniform(12.0, 20.0, n)[:, None]
+    rot = synth.random_rotations(rng, n)
+    L = np.where(np.arange(n) % 2 == 0, 20, 8)
+    L[1] = 24
+    ia, ib = np.zeros(n, int), np.ones(n, int)
+    with tcm.Context(lmax_cap=24) as ctx:
+        E_all, _ = ctx.tcm_energy_batch(T, ia, ib, L, R0, rotB=rot, precision=prec)
+        Eg_all, G_all, _ = ctx.tcm_gradients_batch(T, ia, ib, L, R0, rotB=rot, precision=prec)
+        for k in (0, 2, 3):  # L = 20, 20, 8
+            for sel in ([k], [k, 1]):  # alone; beside the degree-24 item
+                E1, _ = ctx.tcm_energy_batch(T, ia[sel], ib[sel], L[sel], R0[sel], rotB=rot[sel], precision=prec)
+                Eg1, G1, _ = ctx.tcm_gradients_batch(T, ia[sel], ib[sel], L[sel], R0[sel], rotB=rot[sel],
+                                                     precision=prec)
+                torch.cuda.synchronize()
+                assert float(E1[0]) == float(E_all[k]), (k, sel, float(E1[0]) - float(E_all[k]))
+                assert float(Eg1[0]) == float(E_all[k]) == float(Eg_all[k])
+                assert torch.equal(G1[0], G_all[k]), (k, sel)

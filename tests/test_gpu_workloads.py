@@ -94,8 +94,9 @@ def test_uneven_batch_full_size(ctx, tcm):
                                      precision=tcm.TCM_MIXED)
         torch.cuda.synchronize()
         assert float(E1[0]) == E[k]
-    for L in res.best:  # later tests in this module run with the default tiling
+    for L in res.best:  # later tests in this module run with the default tiling and chunking
         ctx.tcm_ctx_set_tiling_l(tcm.TCM_MIXED, L, 64, 2)
+        ctx.tcm_ctx_set_chunking_l(L, 160)
 
 
 def test_large_assembly_full_size(ctx, tcm):
