@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--only", choices=["protein_pes_scan", "uneven_pairs"], default=None,
                    help="run one of the other workloads alone and print its record (for profiling captures)")
+    p.add_argument("--tiling", default=None, metavar="APL,CTAS,KMAX",
+                   help="apply this moment-pass tiling instead of running the autotuner (for profiling captures "
+                        "of the tuned launch configuration)")
     p.add_argument("--orientations", type=int, default=10000,
                    help="orientations of B in the headline workload (10,000; fewer only for profiling captures)")
     return p.parse_args()
@@ -405,7 +408,9 @@ def run_ours(args, rank, world, dist):
     systems = [(A, None, None), (B, None, None)]
     ia, ib, il = np.zeros(k, int), np.ones(k, int), np.full(k, L)
     tiling = None
-    if not args.no_autotune:
+    if args.tiling:
+        tiling = fixed_tiling(ctx, tcm, prec, L, args.tiling)
+    elif not args.no_autotune:
         # the moment pass's warp tiles, grid and L-chunking chosen by the library's autotuner on a
         # sample of this batch's own items, before any timed step
         tuned = autotune.tune(ctx, systems, ia, ib, il, s.R0, rotB=s.rotB, precision=prec, reps=2,
@@ -532,8 +537,17 @@ def run_ours(args, rank, world, dist):
 
 # ----------------------------------------------------------------------------- other workloads
 
+def fixed_tiling(ctx, tcm, prec, L, spec):
+    """Apply an 'APL,CTAS,KMAX' tiling to degree L; returns the record the JSON line carries."""
+    apl, cps, km = (int(x) for x in spec.split(","))
+    ctx.tcm_ctx_set_tiling_l(prec, L, apl, cps)
+    if prec != tcm.TCM_FP64:
+        ctx.tcm_ctx_set_chunking_l(L, km)
+    return {"lmax": L, "atoms_per_lane": apl, "ctas_per_sm": cps, "kmax": km, "how": "given (--tiling), not tuned"}
+
+
 def bench_config2(torch, tcm, synth, autotune, timer, stream, prec, peak_fp32, peak_fp64, n_sm, smx, steps=200,
-                  tune=True):
+                  tune=True, tiling=None):
     """Protein-like PES scan: 2 x 20,000 atoms, 256 orientations of B, Lmax = 20."""
     s = synth.protein_pes_scan()
     k = len(s.R0)
@@ -544,7 +558,9 @@ def bench_config2(torch, tcm, synth, autotune, timer, stream, prec, peak_fp32, p
     ctx = tcm.Context(lmax_cap=L, stream=stream)
     systems = [(A, None, None), (B, None, None)]
     ia, ib, il = np.zeros(k, int), np.ones(k, int), np.full(k, L)
-    tuned = autotune.tune(ctx, systems, ia, ib, il, s.R0, rotB=s.rotB, precision=prec, reps=3) if tune else None
+    tuned = autotune.tune(ctx, systems, ia, ib, il, s.R0, rotB=s.rotB, precision=prec, reps=3) \
+        if (tune and tiling is None) else None
+    fixed = fixed_tiling(ctx, tcm, prec, L, tiling) if tiling else None
     pb = tcm.pack_batch(systems, ia, ib, il, s.R0, rotB=s.rotB)
     E = torch.empty(k, dtype=torch.float64, device="cuda")
     st = torch.empty(k, dtype=torch.int32, device="cuda")
@@ -577,8 +593,8 @@ def bench_config2(torch, tcm, synth, autotune, timer, stream, prec, peak_fp32, p
            "contract_roofline": {"bound": "fp64", "achieved": con, "peak": peak_fp64, "unit": "G FP64 op/s",
                                  "frac": con / peak_fp64, "launch_ms": con_launch_ms,
                                  "algorithmic_fp64_per_energy": contract_fp64_ops(L)},
-           "tiling": {"atoms_per_lane": tuned.best[L][0], "ctas_per_sm": tuned.best[L][1], "kmax": tuned.best[L][2],
-                      "chunks": ctx.tcm_ctx_get_chunking_l(L)[1]} if tuned else "default"}
+           "tiling": ({"atoms_per_lane": tuned.best[L][0], "ctas_per_sm": tuned.best[L][1], "kmax": tuned.best[L][2],
+                       "chunks": ctx.tcm_ctx_get_chunking_l(L)[1]} if tuned else (fixed or "default"))}
     # B's moments rotated from a cache (Wigner rotation in the contraction kernel) instead of
     # recomputed from its atoms: moments of A and B once, outside the timed steps
     mA = ctx.tcm_moments(A, L, precision=prec)
@@ -794,7 +810,7 @@ def run_only(args):
     if args.only == "protein_pes_scan":
         rec = bench_config2(torch, tcm, synth, autotune, Timer(torch, stream), stream, prec,
                             n_sm * FP32_LANES_PER_SM * smx * 1e6 / 1e12, n_sm * FP64_PER_SM_CLK * smx * 1e6 / 1e9,
-                            n_sm, smx, steps=args.steps, tune=not args.no_autotune)
+                            n_sm, smx, steps=args.steps, tune=not args.no_autotune, tiling=args.tiling)
     else:
         rec = bench_config3(torch, tcm, synth, stream, prec, tune=not args.no_autotune)
     print(json.dumps({args.only: rec}), flush=True)

@@ -61,32 +61,31 @@ constexpr int kLowComps = (kLowLmax + 1) * (kLowLmax + 1);
 __device__ void low_degrees(const MomJob& job, const double* __restrict__ syspart, double* s_low) {
   if (threadIdx.x < kLowSums) s_low[threadIdx.x] = __ldcg(syspart + (long long)job.low_base * kSysPart + kSysPartLow + threadIdx.x);
   __syncthreads();
-  if (threadIdx.x != 0) return;
+  const int k = threadIdx.x;  // packed output slot, one thread each
+  if (k >= (job.L + 1) * (job.L + 1) || k >= kLowComps) return;
   const double* R = job.rot;
   const double P[3] = {s_low[1], s_low[2], s_low[3]};
   const double T[3][3] = {{s_low[4], s_low[5], s_low[6]}, {s_low[5], s_low[7], s_low[8]}, {s_low[6], s_low[8], s_low[9]}};
-  double Pr[3], RT[3][3], Tr[3][3];
-  for (int a = 0; a < 3; ++a) {
-    Pr[a] = R[3 * a] * P[0] + R[3 * a + 1] * P[1] + R[3 * a + 2] * P[2];
-    for (int b = 0; b < 3; ++b) RT[a][b] = R[3 * a] * T[0][b] + R[3 * a + 1] * T[1][b] + R[3 * a + 2] * T[2][b];
-  }
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) Tr[a][b] = RT[a][0] * R[3 * b] + RT[a][1] * R[3 * b + 1] + RT[a][2] * R[3 * b + 2];
+  auto pr = [&](int a) { return R[3 * a] * P[0] + R[3 * a + 1] * P[1] + R[3 * a + 2] * P[2]; };  // (R P)_a
+  auto tr = [&](int a, int b) {  // (R T R^T)_ab
+    double s = 0.0;
+    for (int i = 0; i < 3; ++i) s += R[3 * a + i] * (T[i][0] * R[3 * b] + T[i][1] * R[3 * b + 1] + T[i][2] * R[3 * b + 2]);
+    return s;
+  };
   const double r2 = 0.70710678118654752440, s32 = 1.22474487139158904910, s38 = 0.61237243569579452455;
-  double* o = job.out;
-  o[0] = s_low[0];
-  if (job.L >= 1) {
-    o[1] = Pr[2];
-    o[2] = -r2 * Pr[0];
-    o[3] = -r2 * Pr[1];
+  double v;
+  switch (k) {
+    case 0: v = s_low[0]; break;
+    case 1: v = pr(2); break;
+    case 2: v = -r2 * pr(0); break;
+    case 3: v = -r2 * pr(1); break;
+    case 4: v = tr(2, 2) - 0.5 * (tr(0, 0) + tr(1, 1)); break;
+    case 5: v = -s32 * tr(0, 2); break;
+    case 6: v = -s32 * tr(1, 2); break;
+    case 7: v = s38 * (tr(0, 0) - tr(1, 1)); break;
+    default: v = s32 * tr(0, 1); break;
   }
-  if (job.L >= 2) {
-    o[4] = Tr[2][2] - 0.5 * (Tr[0][0] + Tr[1][1]);
-    o[5] = -s32 * Tr[0][2];
-    o[6] = -s32 * Tr[1][2];
-    o[7] = s38 * (Tr[0][0] - Tr[1][1]);
-    o[8] = s32 * Tr[0][1];
-  }
+  job.out[k] = v;
 }
 
 // a3: one CTA per moment job.  Threads walk the (chunk, slot) entries of the job's partial
