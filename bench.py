@@ -414,7 +414,7 @@ def run_ours(args, rank, world, dist):
         # the moment pass's warp tiles, grid and L-chunking chosen by the library's autotuner on a
         # sample of this batch's own items, before any timed step
         tuned = autotune.tune(ctx, systems, ia, ib, il, s.R0, rotB=s.rotB, precision=prec, reps=2,
-                              max_items_per_l=512, atoms_per_lane=(32, 64, 96, 128, 256))
+                              max_items_per_l=512, atoms_per_lane=(32, 64, 96, 128, 256, 512))
         tiling = {"lmax": L, "atoms_per_lane": tuned.best[L][0], "ctas_per_sm": tuned.best[L][1],
                   "kmax": tuned.best[L][2], "chunks": ctx.tcm_ctx_get_chunking_l(L)[1],
                   "tuned_on": "512 of the 10,000 orientations",

@@ -365,11 +365,12 @@ __global__ void __launch_bounds__(kSysThreads, 3) k_sys_radius_low(const SysJob*
 }  // namespace
 
 int sys_tile_atoms(long long n) {
-  // 128-atom tiles (4 per lane, one batch of loads) up to 32,768 atoms, then doubling up to
-  // 1,024 above 131,072: at most 256 tiles per system below 262,144 atoms, enough warps for the
-  // GPU even for a single system, few enough partial rows for the largest
-  long long t = 128;
-  while (t < 1024 && t * 256 < n) t *= 2;
+  // 256-atom tiles (8 per lane) up to 32,768 atoms, 512 up to 65,536, 1,024 above: enough warps
+  // for the GPU even for a single system, few enough partial rows for the largest (128-atom
+  // tiles were tried: their per-tile reductions cost more on a batch of many systems than the
+  // extra warps gained on a pair of 20,000-atom systems)
+  long long t = 256;
+  while (t < 1024 && t * 128 < n) t *= 2;
   return (int)t;
 }
 

@@ -33,8 +33,8 @@ constexpr int kNaTilesPerChunk = (int)(kNaMaxAtoms / kNaTileAtoms);  // 64
 constexpr int kNaMaxChunks = 10;                                     // most chunks of any (precision, Lmax)
 constexpr int kNaPartialDoubles = kNaTilesPerChunk * 800;            // max over plans of chunks * kmax = 800
 constexpr int kNaMaxTiles = kNaTilesPerChunk * kNaMaxChunks;
-// system-pass rows: sys_tile_atoms gives at most 256 tiles up to 262,144 atoms (1,024-atom tiles
-// above 131,072), plus the sum row
+// system-pass rows: sys_tile_atoms gives at most 128 tiles up to 65,536 atoms and 1,024-atom tiles
+// above (256 for the largest request), plus the sum row
 constexpr int kNaSysTiles = (int)((kNaMaxAtoms + 1023) / 1024) + 1;
 constexpr int kNaCompTotal = 5525;  // sum over L = 0..24 of (L+1)^2
 
