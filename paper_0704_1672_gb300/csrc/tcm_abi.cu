@@ -83,6 +83,15 @@ struct Packer {
     size = off + std::max<size_t>(v.size() * sizeof(T), 1);
     return off;
   }
+  // two arrays of one type back to back (one device array), without concatenating them on the host
+  template <typename T>
+  size_t add2(const std::vector<T>& a, const std::vector<T>& b) {
+    const size_t off = align_up(size);
+    spans.push_back(Span{a.data(), a.size() * sizeof(T), off});
+    spans.push_back(Span{b.data(), b.size() * sizeof(T), off + a.size() * sizeof(T)});
+    size = off + std::max<size_t>((a.size() + b.size()) * sizeof(T), 1);
+    return off;
+  }
 };
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -268,14 +277,15 @@ double chunk_cost(int plan, int L, int chunk) {
 // grouped by chunk plan (one launch per plan present, usually one), one order over all degrees.  The tiles themselves are written on the device
 // (k_expand_tiles), so the host work is O(groups log groups).
 void build_tiles(int precision, Plan& P) {
-  // one 64-bit key per group: [degree (FP64) or chunk plan (mixed)] [largest cost first] [group
-  // index], so a plain sort of integers gives the order deterministically (ties in their
-  // planning order)
+  // one 32-bit key per group: [degree (FP64) or chunk plan (mixed), 5 bits] [largest cost first,
+  // 27 bits]; a stable sort keeps ties in their planning order, so the order is deterministic.
+  // The sort is a least-significant-digit radix sort (three passes of 11 bits): for the tens of
+  // thousands of groups of a large batch it takes a fraction of a comparison sort's time.
   struct Group {
     int job, chunk;
   };
   std::vector<Group> g;
-  std::vector<unsigned long long> key;
+  std::vector<uint32_t> key;
   g.reserve(P.jobs.size() * 2);
   key.reserve(P.jobs.size() * 2);
   const bool by_degree = precision == TCM_FP64;
@@ -284,25 +294,38 @@ void build_tiles(int precision, Plan& P) {
     const int nch = moments_nchunks(j.plan, j.L);
     for (int ch = 0; ch < nch; ++ch) {
       const double cost = chunk_cost(j.plan, j.L, ch) * (double)j.atoms_per_tile;
-      const unsigned long long cq = (unsigned long long)std::min(cost, 134217727.0);  // 27 bits
-      key.push_back(((unsigned long long)(by_degree ? j.L : j.plan - 1) << 59) | ((134217727ull - cq) << 32) |
-                    (unsigned long long)g.size());
+      const uint32_t cq = (uint32_t)std::min(cost, 134217727.0);  // 27 bits
+      key.push_back(((uint32_t)(by_degree ? j.L : j.plan - 1) << 27) | (134217727u - cq));
       g.push_back(Group{ji, ch});
     }
   }
-  std::sort(key.begin(), key.end());
+  const size_t n = key.size();
+  std::vector<uint32_t> order(n), k2(n), o2(n);
+  for (size_t i = 0; i < n; ++i) order[i] = (uint32_t)i;
+  for (int shift = 0; shift < 32; shift += 11) {
+    uint32_t count[2049] = {};
+    for (size_t i = 0; i < n; ++i) ++count[((key[i] >> shift) & 2047u) + 1];
+    for (int b = 0; b < 2048; ++b) count[b + 1] += count[b];
+    for (size_t i = 0; i < n; ++i) {
+      const uint32_t d = (key[i] >> shift) & 2047u;
+      k2[count[d]] = key[i];
+      o2[count[d]++] = order[i];
+    }
+    key.swap(k2);
+    order.swap(o2);
+  }
   P.groups.clear();
-  P.groups.reserve(g.size());
+  P.groups.reserve(n);
   int first = 0;
   size_t gi = 0;
   for (int L = 0; L <= kLmaxMax; ++L) {
     P.tile_begin[L] = first;
-    for (; gi < key.size(); ++gi) {
-      const Group& gr = g[key[gi] & 0xffffffffull];
+    for (; gi < n; ++gi) {
+      const Group& gr = g[order[gi]];
       if ((by_degree ? P.jobs[gr.job].L : P.jobs[gr.job].plan - 1) != L) break;
-      const int n = P.jobs[gr.job].tiles_per_chunk;
-      P.groups.push_back(MomGroup{gr.job, gr.chunk, n, first});
-      first += n;
+      const int nt = P.jobs[gr.job].tiles_per_chunk;
+      P.groups.push_back(MomGroup{gr.job, gr.chunk, nt, first});
+      first += nt;
     }
   }
   P.tile_begin[kLmaxMax + 1] = first;
@@ -1000,14 +1023,12 @@ int energy_batch(tcm_ctx_t c, int n_systems, const tcm_system* systems, int64_t 
     if (d.jobA <= -2) d.jobA = n_computed + (-2 - d.jobA);
     if (d.jobB <= -2) d.jobB = n_computed + (-2 - d.jobB);
   }
-  std::vector<MomJob> all_jobs = P.jobs;
-  all_jobs.insert(all_jobs.end(), cached.begin(), cached.end());
   int Lmax_items = 0;
   for (int64_t k = 0; k < n_items; ++k) Lmax_items = std::max(Lmax_items, (int)items[k].lmax);
   std::vector<SysGeom> geoms(std::max(n_systems, 1));
   for (int s = 0; s < n_systems; ++s) geoms[s] = host_geom(systems[s]);
   Packer pk;
-  const size_t o_geo = pk.add(geoms), o_job = pk.add(all_jobs), o_tile = pk.add(P.groups), o_sj = pk.add(S.jobs),
+  const size_t o_geo = pk.add(geoms), o_job = pk.add2(P.jobs, cached), o_tile = pk.add(P.groups), o_sj = pk.add(S.jobs),
                o_it = pk.add(pd), o_rot = pk.add(rots);
   // every buffer the launches touch is sized before anything is queued (no reallocation
   // may happen while a graph is being captured)
