@@ -702,13 +702,20 @@ int rotate_smem_bytes(int L) {
   return (2 * nq + 3 * (L + 1)) * (int)sizeof(double2) + dpi2_off(L + 1) * (int)sizeof(double);
 }
 
+// The dynamic shared-memory limit of a kernel: above 48 KB of dynamic plus static shared memory
+// a launch needs the raised limit.  These kernels hold at most 8 KB of static shared memory, so
+// the limit is set whenever the dynamic part passes 40 KB (on every such launch: the attribute
+// is per device, and a call costs far less than the kernels it precedes).
+template <typename F>
+int raise_smem_limit(F kernel, int dyn) {
+  if (dyn <= 40 * 1024) return 0;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess ? 0 : -1;
+}
+
 int launch_rotate_moments(const RotDesc* sets, int n_sets, int Lmax_sets, const double* ztab, cudaStream_t s) {
   if (n_sets <= 0) return 0;
   const int smem = rotate_smem_bytes(Lmax_sets);
-  if (smem > 48 * 1024) {
-    if (cudaFuncSetAttribute(k_rotate_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-      return -1;
-  }
+  if (raise_smem_limit(k_rotate_moments, smem) != 0) return -1;
   k_rotate_moments<<<n_sets, contract_threads(Lmax_sets, n_sets), smem, s>>>(sets, ztab);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
@@ -728,16 +735,12 @@ int launch_contract(const PairDesc* items, int n_items, int Lmax_items, const Mo
   const int smem = contract_smem_bytes(Lmax_items);
   const int nt = contract_threads(Lmax_items, n_items);
   if (G) {
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_contract<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-      return -1;
+    if (raise_smem_limit(k_contract<true>, smem) != 0) return -1;
     if (launch_pdl(k_contract<true>, dim3(n_items), dim3(nt), smem, s, items, jobs, geoms, ztab, rots, E, status, G) !=
         cudaSuccess)
       return -1;
   } else {
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_contract<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-      return -1;
+    if (raise_smem_limit(k_contract<false>, smem) != 0) return -1;
     if (launch_pdl(k_contract<false>, dim3(n_items), dim3(nt), smem, s, items, jobs, geoms, ztab, rots, E, status,
                    (double*)nullptr) != cudaSuccess)
       return -1;

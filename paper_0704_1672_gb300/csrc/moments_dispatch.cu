@@ -34,12 +34,17 @@ namespace {
 struct ChunkTables {
   int nch[kNumPlans][kLmaxMax + 1];
   int m0[kNumPlans][kLmaxMax + 1][kLmaxMax + 2];
+  double cost[kNumPlans][kLmaxMax + 1][kLmaxMax + 1];
   ChunkTables() {
     for (int pi = 0; pi < kNumPlans; ++pi) {
       const int kmax = plan_kmax(pi);
       for (int L = 0; L <= kLmaxMax; ++L) {
         nch[pi][L] = plan_nch(L, kmax);
         for (int c = 0; c <= nch[pi][L]; ++c) m0[pi][L][c] = plan_m0(L, kmax, nch[pi][L], c);
+        // relative cost of one atom of a chunk: its accumulators, the seed power u^m0 and the
+        // per-atom set-up
+        for (int c = 0; c < nch[pi][L]; ++c)
+          cost[pi][L][c] = 1.25 * chunk_off(L, m0[pi][L][c], m0[pi][L][c + 1]) + 4.0 * m0[pi][L][c] + 30.0;
       }
     }
   }
@@ -53,6 +58,8 @@ const ChunkTables& chunk_tables() {
 int moments_nchunks(int plan, int L) { return chunk_tables().nch[plan][L]; }
 
 int moments_chunk_m0(int plan, int L, int chunk) { return chunk_tables().m0[plan][L][chunk]; }
+
+const double* moments_chunk_costs(int plan, int L) { return chunk_tables().cost[plan][L]; }
 
 void finalize_tables(std::vector<int>& imap_off, std::vector<int>& imap, std::vector<double>& fmap) {
   const int N = kLmaxMax + 1;

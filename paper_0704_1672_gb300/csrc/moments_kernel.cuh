@@ -553,7 +553,7 @@ int launch_moments_t(const MomJob* jobs, const MomTile* tiles, int n_tiles, int*
                      const SysGeom* geoms, double* partials, int grid, cudaStream_t s) {
   constexpr int smem = (kThreads / 32) * (LK >= 0 ? Plan<T, (LK >= 0 ? LK : 0), KM>::max_nacc() : KM) *
                        MomTraits<T>::stride * (int)sizeof(T);
-  if (smem > 48 * 1024) {
+  if (smem > 40 * 1024) {  // with the kernel's static shared memory (under 1 KB) it may pass 48 KB
     if (cudaFuncSetAttribute(k_moments<T, LK, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return -1;
   }

@@ -56,10 +56,29 @@ __device__ __forceinline__ FF ff_sub_split(float x, float hi, float lo) {
 }
 
 // |x - c|^2 in float from the exact difference d (each coordinate rounded once): within about
-// 3 x 2^-24 of the exact value.  Both scans of the radius use this same expression.
+// 3 x 2^-24 of the exact value.  The first scan of the radius filter takes this from the
+// differences it forms for the low-degree sums anyway.
 __device__ __forceinline__ float r2_float(const FF* d) {
   const float x = d[0].h + d[0].l, y = d[1].h + d[1].l, z = d[2].h + d[2].l;
   return __fmaf_rn(x, x, __fmaf_rn(y, y, z * z));
+}
+
+// |x - c|^2 in plain float, d_k = (x_k - c_hi,k) - c_lo,k: each difference within 2^-23 of its
+// value, the square within about 7 x 2^-24 (4.2e-7).  The second scan of the radius filter uses
+// this cheaper form; with the first scan's 1.8e-7 the two stay far inside the filter's 4e-6
+// margin, so the atom of the exact maximum is always among the candidates.
+__device__ __forceinline__ float r2_plain(const float4& v, const float* chi, const float* clo) {
+  const float x = (v.x - chi[0]) - clo[0], y = (v.y - chi[1]) - clo[1], z = (v.z - chi[2]) - clo[2];
+  return __fmaf_rn(x, x, __fmaf_rn(y, y, z * z));
+}
+
+// Product of a float q (exact) and an FF value: the exact product of the high parts plus q times
+// the low part.
+__device__ __forceinline__ FF ff_mul_f(float q, FF b) {
+  const float p = q * b.h;
+  float e = __fmaf_rn(q, b.h, -p);
+  e = __fmaf_rn(q, b.l, e);
+  return FF{p, e};
 }
 
 __device__ __forceinline__ void ff_warp_sum(float& s, float& e) {
@@ -68,6 +87,39 @@ __device__ __forceinline__ void ff_warp_sum(float& s, float& e) {
     const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
     const float e2 = __shfl_xor_sync(0xffffffffu, e, o);
     ff_acc(s, e, FF{s2, e2});
+  }
+}
+
+// Reduce-scatter of N float-float sums over the 32 lanes of a warp: at each level (lane offset
+// O = 16, 8, ..., 1) a lane keeps the first ceil(n/2) of its n sums if its O bit is clear, the
+// rest (padded with zeros) if it is set, and adds in its partner's values of the sums it keeps,
+// so each level moves half the values of the previous one (one butterfly per sum would move all
+// of them at every level).  A fixed pattern: the same inputs give the same sums in every run.
+// For N = 10, lane l ends with the whole of sum 5 b4 + 3 b3 + 2 b2 + b1 in (s[0], e[0]), where
+// b_i is bit i of l, if bit l of kRs10Lanes is set (ten lanes; the others hold zeros).
+constexpr unsigned kRs10Lanes = 0x05150515u;
+template <int N, int O>
+__device__ __forceinline__ void ff_reduce_scatter(float* s, float* e, int lane) {
+  if constexpr (O > 0) {
+    constexpr int K = (N + 1) / 2;
+    const bool hi = (lane & O) != 0;
+    float ns[K], ne[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const float gs = K + j < N ? s[K + j] : 0.f, ge = K + j < N ? e[K + j] : 0.f;
+      const float send_s = hi ? s[j] : gs, send_e = hi ? e[j] : ge;
+      float a = hi ? gs : s[j], b = hi ? ge : e[j];
+      const float rs = __shfl_xor_sync(0xffffffffu, send_s, O), re = __shfl_xor_sync(0xffffffffu, send_e, O);
+      ff_acc(a, b, FF{rs, re});
+      ns[j] = a;
+      ne[j] = b;
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      s[j] = ns[j];
+      e[j] = ne[j];
+    }
+    ff_reduce_scatter<K, O / 2>(s, e, lane);
   }
 }
 
@@ -152,9 +204,20 @@ __device__ __forceinline__ bool last_tile(int* ticket, int n_tiles, int lane) {
 // work is short, so a lane must keep several loads in flight to cover the memory latency).
 constexpr int kSysBatch = 4;
 
-__device__ __forceinline__ void low_accumulate(float* s, float* e, FF q, const FF* d) {
-  ff_acc(s[0], e[0], q);
-  const FF qd0 = ff_mul(q, d[0]), qd1 = ff_mul(q, d[1]), qd2 = ff_mul(q, d[2]);
+template <typename Q>
+__device__ __forceinline__ FF q_times(Q q, FF d);
+template <>
+__device__ __forceinline__ FF q_times<FF>(FF q, FF d) { return ff_mul(q, d); }
+template <>
+__device__ __forceinline__ FF q_times<float>(float q, FF d) { return ff_mul_f(q, d); }
+__device__ __forceinline__ FF as_ff(FF q) { return q; }
+__device__ __forceinline__ FF as_ff(float q) { return FF{q, 0.f}; }
+
+// q is a float (float records: the charge is exact) or an FF pair (double records).
+template <typename Q>
+__device__ __forceinline__ void low_accumulate(float* s, float* e, Q q, const FF* d) {
+  ff_acc(s[0], e[0], as_ff(q));
+  const FF qd0 = q_times(q, d[0]), qd1 = q_times(q, d[1]), qd2 = q_times(q, d[2]);
   ff_acc(s[1], e[1], qd0);
   ff_acc(s[2], e[2], qd1);
   ff_acc(s[3], e[3], qd2);
@@ -271,7 +334,7 @@ __global__ void __launch_bounds__(kSysThreads, 3) k_sys_radius_low(const SysJob*
         const FF d[3] = {ff_sub_split(v[u].x, chi[0], clo[0]), ff_sub_split(v[u].y, chi[1], clo[1]),
                          ff_sub_split(v[u].z, chi[2], clo[2])};
         if (i + 32 * u < i1) mf = fmaxf(mf, r2_float(d));
-        if (j.need_low) low_accumulate(s, e, FF{v[u].w, 0.f}, d);  // padding atoms carry q = 0
+        if (j.need_low) low_accumulate(s, e, v[u].w, d);  // padding atoms carry q = 0
       }
     }
     // the exact radius: only atoms within a relative 4e-6 of the tile's float maximum can hold
@@ -283,12 +346,7 @@ __global__ void __launch_bounds__(kSysThreads, 3) k_sys_radius_low(const SysJob*
       for (long long i0w = i0; i0w < i1; i0w += 32) {  // warp-uniform trip count
         const long long i = i0w + lane;
         bool cand = false;
-        if (i < i1) {
-          const float4 v = __ldg(X + i);
-          const FF d[3] = {ff_sub_split(v.x, chi[0], clo[0]), ff_sub_split(v.y, chi[1], clo[1]),
-                           ff_sub_split(v.z, chi[2], clo[2])};
-          cand = r2_float(d) >= thr;
-        }
+        if (i < i1) cand = r2_plain(__ldg(X + i), chi, clo) >= thr;
         // the candidates one at a time, in a loop whose trip count is the warp's candidate count:
         // a predicated double block would occupy GB300's 1/64-rate FP64 pipe for every atom
         unsigned m = __ballot_sync(0xffffffffu, cand);
@@ -330,13 +388,11 @@ __global__ void __launch_bounds__(kSysThreads, 3) k_sys_radius_low(const SysJob*
   rmax = warp_max_d(rmax);
   double* row = part + (long long)(j.tile_base + tl.t) * kSysPart;
   if (j.need_low) {
-#pragma unroll
-    for (int k = 0; k < kLowSums; ++k) ff_warp_sum(s[k], e[k]);
-    if (lane < 2 * kLowSums) {  // lane 2k writes the hi part of sum k, lane 2k + 1 its lo part
-      float v = 0.f;
-#pragma unroll
-      for (int k = 0; k < kLowSums; ++k) v = (lane == 2 * k) ? s[k] : ((lane == 2 * k + 1) ? e[k] : v);
-      reinterpret_cast<float*>(row)[kRowLow + lane] = v;
+    static_assert(kLowSums == 10, "the lane map of the reduce-scatter is for ten sums");
+    ff_reduce_scatter<kLowSums, 16>(s, e, lane);
+    if ((kRs10Lanes >> lane) & 1u) {  // the lane holding sum k writes its (hi, lo) pair
+      const int k = 5 * ((lane >> 4) & 1) + 3 * ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
+      reinterpret_cast<float2*>(reinterpret_cast<float*>(row) + kRowLow)[k] = make_float2(s[0], e[0]);
     }
   }
   if (lane == 0) row[kSysPartR2] = rmax;

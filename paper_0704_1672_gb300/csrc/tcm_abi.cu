@@ -267,10 +267,6 @@ void plan_job(tcm_ctx* c, int precision, MomJob& j, int& next_id) {
   next_id += nch * (int)tpc;
 }
 
-double chunk_cost(int plan, int L, int chunk) {
-  const int m0 = moments_chunk_m0(plan, L, chunk), m1 = moments_chunk_m0(plan, L, chunk + 1);
-  return 1.25 * chunk_off(L, m0, m1) + 4.0 * m0 + 30.0;
-}
 
 // The (job, chunk) groups in decreasing order of their tiles' cost (largest first, so the
 // persistent warps finish together).  FP64: grouped by degree (one launch per degree); mixed:
@@ -292,8 +288,9 @@ void build_tiles(int precision, Plan& P) {
   for (int ji = 0; ji < (int)P.jobs.size(); ++ji) {
     const MomJob& j = P.jobs[ji];
     const int nch = moments_nchunks(j.plan, j.L);
+    const double* cc = moments_chunk_costs(j.plan, j.L);
     for (int ch = 0; ch < nch; ++ch) {
-      const double cost = chunk_cost(j.plan, j.L, ch) * (double)j.atoms_per_tile;
+      const double cost = cc[ch] * (double)j.atoms_per_tile;
       const uint32_t cq = (uint32_t)std::min(cost, 134217727.0);  // 27 bits
       key.push_back(((uint32_t)(by_degree ? j.L : j.plan - 1) << 27) | (134217727u - cq));
       g.push_back(Group{ji, ch});

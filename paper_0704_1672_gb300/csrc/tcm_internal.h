@@ -264,6 +264,7 @@ int launch_expand_tiles(const MomGroup* groups, int n_groups, const MomJob* jobs
                         int n_sjobs, SysTile* t1, SysTile* t2, cudaStream_t s);
 int moments_nchunks(int plan, int L);
 int moments_chunk_m0(int plan, int L, int chunk);  // first column of a chunk (chunk = nch: L + 1)
+const double* moments_chunk_costs(int plan, int L);  // relative cost per atom of each chunk
 // Host: the inverse component maps of every plan and their factors F_lm (imap_off has
 // kNumPlans (kLmaxMax + 2) entries, plan by plan, each block ending with its total).
 void finalize_tables(std::vector<int>& imap_off, std::vector<int>& imap, std::vector<double>& fmap);
