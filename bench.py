@@ -637,7 +637,7 @@ def bench_config3(torch, tcm, synth, stream, prec, calls=3, tune=True):
                     for i in range(len(b.L))))
     ctx = tcm.Context(lmax_cap=24, stream=stream)
     tuned = autotune.tune(ctx, T, b.pair_a, b.pair_b, b.L, b.R0, rotB=b.rotB, precision=prec, reps=2,
-                          max_items_per_l=256, atoms_per_lane=(32, 64, 128)) if tune else None
+                          max_items_per_l=256) if tune else None
     E = torch.empty(len(b.L), dtype=torch.float64, device="cuda")
     st = torch.empty(len(b.L), dtype=torch.int32, device="cuda")
     rng = np.random.default_rng(99)
