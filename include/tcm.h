@@ -172,8 +172,9 @@ int tcm_ctx_get_chunking_l(tcm_ctx_t ctx, int lmax, int* kmax, int* n_chunks);
 
 /* CUDA-graph replay of tcm_energy_batch.  A call's launch sequence (tile list, centres and
  * radii, low-degree sums, the moment pass -- one launch over all degrees per chunk budget
- * present in TCM_MIXED, one per degree in TCM_FP64 --, finalisation, contraction) is captured into a graph and replayed by
- * later calls with the same launch shapes and buffers (item count, job and tile counts,
+ * present in TCM_MIXED, one per degree in TCM_FP64 --, finalisation, contraction) is
+ * captured into a graph and replayed by later calls with the same launch shapes, settings
+ * and buffers (item count, job and tile counts, tiling and chunking,
  * output pointers); the descriptors are uploaded per call, so the orientations, pairs and
  * systems may change.  mode 0: launch kernel by kernel; mode 1 (default): capture a shape
  * when two calls in a row have it (a stream of changing shapes launches directly instead of
