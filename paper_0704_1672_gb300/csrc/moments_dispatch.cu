@@ -137,7 +137,6 @@ __global__ void __launch_bounds__(256) k_expand_tiles(const MomGroup* __restrict
                                                       const MomJob* __restrict__ jobs, MomTile* __restrict__ tiles,
                                                       const SysJob* __restrict__ sjobs, int n_sjobs,
                                                       SysTile* __restrict__ t1, SysTile* __restrict__ t2) {
-  pdl_trigger();  // the system pass may be scheduled now; it waits for this grid before reading
   const int g = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (g < n_groups) {

@@ -233,8 +233,6 @@ __global__ void __launch_bounds__(kSysThreads) k_sys_centroid(const SysJob* __re
                                                               const SysTile* __restrict__ tiles, int n_tiles,
                                                               double* __restrict__ part, int* __restrict__ tickets,
                                                               SysGeom* __restrict__ geoms) {
-  pdl_wait();     // the tile lists are written
-  pdl_trigger();  // pass 2 may be scheduled; it waits for this grid before reading
   const int w = blockIdx.x * kSysWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (w >= n_tiles) return;
@@ -308,13 +306,12 @@ __global__ void __launch_bounds__(kSysThreads, 3) k_sys_radius_low(const SysJob*
                                                                 const SysTile* __restrict__ tiles, int n_tiles,
                                                                 double* __restrict__ part, int* __restrict__ tickets,
                                                                 SysGeom* __restrict__ geoms) {
-  pdl_wait();     // the tile lists and the centroids of pass 1 are complete
-  pdl_trigger();  // the moment pass may be scheduled; it waits for this grid before reading
   const int w = blockIdx.x * kSysWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (w >= n_tiles) return;
   const SysTile tl = tiles[w];
   const SysJob j = jobs[tl.job];
+  pdl_wait();  // the centroids of pass 1 are complete
   const SysGeom g = geoms[j.geom];
   const long long i0 = (long long)tl.t * j.atoms_per_tile;
   const long long i1 = min(j.n, i0 + (long long)j.atoms_per_tile);
@@ -435,9 +432,10 @@ int sys_tile_atoms(long long n) {
 
 int launch_sys(const SysJob* jobs, const SysTile* t1, int n1, const SysTile* t2, int n2, double* part, int* tickets,
                SysGeom* geoms, cudaStream_t s) {
-  if (n1 > 0 && launch_pdl(k_sys_centroid, dim3((n1 + kSysWarps - 1) / kSysWarps), dim3(kSysThreads), 0, s, jobs, t1,
-                           n1, part, tickets, geoms) != cudaSuccess)
-    return -1;
+  if (n1 > 0) {
+    k_sys_centroid<<<(n1 + kSysWarps - 1) / kSysWarps, kSysThreads, 0, s>>>(jobs, t1, n1, part, tickets, geoms);
+    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  }
   if (n2 > 0 && launch_pdl(k_sys_radius_low, dim3((n2 + kSysWarps - 1) / kSysWarps), dim3(kSysThreads), 0, s, jobs,
                            t2, n2, part, tickets, geoms) != cudaSuccess)
     return -1;

@@ -222,12 +222,10 @@ constexpr int kSysPart = kSysPartLow + kLowSums;
 
 // Programmatic dependent launch: a kernel launched with programmatic stream serialization
 // is set up while its predecessor drains; pdl_wait() blocks until the predecessor grid has
-// completed and its memory is visible (a no-op for an ordinary launch).  The tile lists, the
-// system pass and the finalisation issue griddepcontrol.launch_dependents (pdl_trigger) early,
-// so that the next launch is set up while they run (the system-pass kernels only after their
-// own wait, so that nothing a later kernel reads before its wait is still being written); the
-// moment kernel does not: dependent CTAs made resident before its tail had drained slowed the
-// replayed step down (0.372 ms against 0.325 ms).
+// completed and its memory is visible (a no-op for an ordinary launch).  Only the finalisation
+// issues griddepcontrol.launch_dependents (pdl_trigger), so that the contraction's CTAs set up
+// their tables while the last finalisation CTAs run; dependent CTAs made resident before the
+// moment kernel's tail had drained slowed the replayed step down (0.372 ms against 0.325 ms).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
