@@ -504,6 +504,7 @@ def run_ours(args, rank, world, dist):
         extras["uneven_pairs"] = bench_config3(torch, tcm, synth, stream, prec)
         fp64_plain = plain_fp64_config4(ctx, tcm, torch, A, B, s, n_orient=8)
         extras["fp64_plain_gpu"] = fp64_plain
+        extras["single_pair"] = bench_config1(torch, tcm, synth)
         if not args.no_serve:
             extras["serving"] = bench_serving(torch, tcm, synth, args.serve_seconds, dev, args.no_clocks)
         if not args.no_pes_grid:
@@ -544,6 +545,48 @@ def fixed_tiling(ctx, tcm, prec, L, spec):
     if prec != tcm.TCM_FP64:
         ctx.tcm_ctx_set_chunking_l(L, km)
     return {"lmax": L, "atoms_per_lane": apl, "ctas_per_sm": cps, "kmax": km, "how": "given (--tiling), not tuned"}
+
+
+def bench_config1(torch, tcm, synth, reps=200):
+    """The single pair (2 x 200 charges, Lmax = 10), one energy per call, each call synchronised:
+    the plain FP64 path (tcm_moments of both systems, then tcm_energy) and one-item
+    tcm_energy_batch calls in FP64 and mixed precision.  Latencies are host wall times per call
+    (the work is microseconds; launch and synchronisation dominate)."""
+    s = synth.single_pair_sphere()
+    A = torch.tensor(s.A, dtype=torch.float64, device="cuda")
+    B = torch.tensor(s.B, dtype=torch.float64, device="cuda")
+    Af, Bf = A.float(), B.float()
+    ctx = tcm.Context(lmax_cap=s.L)
+    R0 = np.asarray(s.R0, dtype=np.float64).reshape(1, 3)
+
+    def plain():
+        mA = ctx.tcm_moments(A, s.L, precision=tcm.TCM_FP64)
+        mB = ctx.tcm_moments(B, s.L, precision=tcm.TCM_FP64)
+        return ctx.tcm_energy(mA, mB, R0[0], s.L)
+
+    def batched(prec, X, Y):
+        def run():
+            E, _ = ctx.tcm_energy_batch([(X, None, None), (Y, None, None)], [0], [1], [s.L], R0, precision=prec)
+            return float(E[0])  # device -> host read: the call is synchronised
+        return run
+
+    out = {}
+    for name, fn in (("fp64_plain", plain), ("fp64_batched", batched(tcm.TCM_FP64, A, B)),
+                     ("mixed_batched", batched(tcm.TCM_MIXED, Af, Bf))):
+        for _ in range(10):
+            fn()
+        torch.cuda.synchronize()
+        lat = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            lat.append((time.perf_counter() - t0) * 1e3)
+        lat.sort()
+        out[name] = {"latency_ms_p50": lat[len(lat) // 2], "latency_ms_p99": lat[int(0.99 * (len(lat) - 1))],
+                     "energies_per_s": 1e3 / (sum(lat) / len(lat))}
+    ctx.close()
+    out["workload"] = "single pair: 2 x 200 charges in r = 10 A spheres, R0 = 40 A, Lmax = 10, one energy per call"
+    return out
 
 
 def bench_config2(torch, tcm, synth, autotune, timer, stream, prec, peak_fp32, peak_fp64, n_sm, smx, steps=200,
