@@ -88,6 +88,13 @@ def test_tune_picks_the_fastest_per_degree_and_applies_it():
     assert ctx.calls == 4 * len(autotune.candidates(tcm.TCM_MIXED))
 
 
+def test_choose_prefers_larger_tiles_within_one_percent():
+    t = {(64, 2, 160): 1.000, (128, 2, 160): 1.005, (256, 2, 160): 1.012, (512, 1, 160): 1.008, (32, 3, 96): 0.999}
+    assert autotune.choose(t) == (512, 1, 160)          # 1.008 <= 1.01 * 0.999: the largest tiles within 1 %
+    assert autotune.choose(t, tol=0.0) == (32, 3, 96)   # the fastest alone
+    assert autotune.choose({}) is None
+
+
 def test_fp64_candidates_keep_the_double_budget():
     c = autotune.candidates(tcm.TCM_FP64, (32, 64), (1, 2, 3))
     assert c == [(32, 1, 80), (32, 2, 80), (64, 1, 80), (64, 2, 80)]
@@ -138,7 +145,7 @@ def test_tuned_uneven_batch_matches_oracle():
         assert sorted(res.best) == [8, 12, 16, 24]
         for Ldeg, best in res.best.items():
             assert autotune.get_setting(ctx, tcm.TCM_MIXED, Ldeg) == best
-            assert res.timings[Ldeg][best] == min(res.timings[Ldeg].values())
+            assert res.timings[Ldeg][best] <= 1.01 * min(res.timings[Ldeg].values())
         print({Ldeg: (best, round(res.timings[Ldeg][best], 4)) for Ldeg, best in res.best.items()})
         E, st = ctx.tcm_energy_batch(T, a, b, L, R0, rotB=rot)
         torch.cuda.synchronize()
