@@ -8,9 +8,9 @@ For every degree present in the batch, the items of that degree (at most ``max_i
 them) form a sub-batch; each candidate setting (atoms per lane, CTAs per SM, kmax) is applied
 with ``tcm_ctx_set_tiling_l`` and ``tcm_ctx_set_chunking_l``, the sub-batch is run once untimed
 and ``reps`` times timed, and the median time of the moment phase (the library's CUDA-event
-phase profile: the moment kernels of that degree, nothing else) is kept.  The fastest candidate,
-or among those within 1 % of it the one with the largest warp tiles (``choose``), is applied to
-the context and returned.  Results can be saved to a JSON file keyed by device
+phase profile: the moment kernels of that degree, nothing else) is kept.  The fastest candidate
+(when the sub-batch is a sample of the degree's items: among those within 1 % of it, the one
+with the largest warp tiles; ``choose``) is applied to the context and returned.  Results can be saved to a JSON file keyed by device
 name, library build and precision, and loaded into a later context.
 
 The tiling and the chunking change only the order in which atom contributions are summed, so
@@ -88,7 +88,8 @@ def choose(timings: dict, tol=0.01):
     the largest warp tiles (atoms per lane; ties: the first in candidate order).  Larger tiles
     mean fewer partial rows for the finalisation to read, which a sampled sub-batch
     under-represents: on the large assembly 256 and 512 atoms per lane time within 0.1 % on 512
-    orientations, and 512 is 1.4 % faster on all 10,000."""
+    orientations, and 512 is 1.4 % faster on all 10,000.  ``tune`` passes tol = 0.01 when it
+    timed a sample of a degree's items and 0 when it timed all of them."""
     if not timings:
         return None
     best_ms = min(timings.values())
@@ -151,7 +152,10 @@ def tune(ctx, systems, a, b, lmax, R0, rotB=None, precision=None, atoms_per_lane
         for cand in candidates(precision, atoms_per_lane, ctas_per_sm, kmax):
             set_setting(ctx, precision, L, cand)
             t[cand] = measure(L, run) if measure else moment_phase_ms(ctx, run, reps)
-        best = choose(t) or default
+        # a sub-batch that leaves out items of this degree under-represents the partial rows that
+        # larger tiles save: then prefer them within 1 %; the whole batch is timed as it is
+        subsampled = len(idx) < int(np.count_nonzero(lmax == L))
+        best = choose(t, tol=0.01 if subsampled else 0.0) or default
         set_setting(ctx, precision, L, best)
         res.best[L] = best
         res.timings[L] = t

@@ -95,6 +95,21 @@ def test_choose_prefers_larger_tiles_within_one_percent():
     assert autotune.choose({}) is None
 
 
+def test_larger_tiles_preferred_only_when_the_degree_was_sampled():
+    def landscape(L, apl, cps, km):
+        return {256: 1.000, 512: 1.005}.get(apl, 2.0) + (0.0 if (cps, km) == (2, 160) else 1.0)
+
+    rng = np.random.default_rng(3)
+    k = 10
+    R0 = rng.normal(size=(k, 3)) + 50.0
+    for cap, want in ((4, 512), (512, 256)):  # 4 of the 10 items: a sample; 512: all of them
+        ctx = FakeCtx()
+        res = autotune.tune(ctx, systems(2), np.zeros(k, int), np.ones(k, int), np.full(k, 24), R0,
+                            precision=tcm.TCM_MIXED, max_items_per_l=cap, atoms_per_lane=(64, 256, 512),
+                            measure=lambda L, run: (run(), landscape(L, *ctx.setting(tcm.TCM_MIXED, L)))[1])
+        assert res.best[24] == (want, 2, 160), (cap, res.best)
+
+
 def test_fp64_candidates_keep_the_double_budget():
     c = autotune.candidates(tcm.TCM_FP64, (32, 64), (1, 2, 3))
     assert c == [(32, 1, 80), (32, 2, 80), (64, 1, 80), (64, 2, 80)]
